@@ -1,0 +1,687 @@
+/*
+ * FP64 CPU oracle for the lattice Boltzmann + raspberry-coupling step.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this file's library. It shares no code,
+ * header, table or constant generator with the CUDA library: every table
+ * here is built from its own definition.
+ *
+ * It is written to be read against Ustach & Faller, "The Raspberry model for
+ * protein-like particles" (arXiv:1604.01829):
+ *   - Sec. 1.1: LB as streaming along discrete velocity links plus a
+ *     collision that relaxes towards a Maxwell-Boltzmann equilibrium, either
+ *     on one time scale (BGK) or mode by mode (multiple relaxation times);
+ *     optional thermal noise ("stochastic or deterministic"); boundary nodes
+ *     reflect the populations that stream into them (bounce-back).
+ *   - Sec. 1.1, Eq. (latticeboltzmannfriction): bead force
+ *     F = -xi_bead (v - u(r,t)) + f_s, u interpolated between the nearest
+ *     grid points, f_s obeying fluctuation-dissipation.
+ *   - Sec. 1.2 and Sec. 2.3: the raspberry is a rigid body; beads are virtual
+ *     sites of the centre-of-mass particle; bead forces and torques act on
+ *     it; translation by velocity Verlet, rotation by a quaternion.
+ *   - Sec. 2.3: pore boundary nodes sit half a grid spacing outside the wall.
+ * Points the paper leaves open are taken as follows (each reading is also
+ * listed with the design notes):
+ *   D3Q19 lattice; second-order equilibrium; Guo forcing with
+ *   u = (j + F/2)/rho; orthogonal moment basis (Dunweg-Schiller-Ladd
+ *   polynomials), m* = m_eq + g_k (m - m_eq) + (1+g_k)/2 S_k; fluctuating
+ *   modes with amplitude sqrt(3 rho kT b_k (1-g_k^2)); Philox4x32-10
+ *   uniform variates of unit variance; trilinear interpolation between the
+ *   8 nodes surrounding a bead and the transposed spread of -F; node centres
+ *   at integer+1/2; a node is a wall node when its centre lies at distance
+ *   >= R from the pore axis.
+ *
+ * Deliberately plain: two population arrays and push streaming, the MRT
+ * collision as explicit 19x19 matrix products with the inverse found by
+ * Gauss-Jordan elimination, nested loops over beads and corners.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NQ 19
+
+/* ---------------------------------------------------------------- lattice */
+
+/* D3Q19 velocities: rest, 6 axis links, 12 face diagonals, each diagonal
+ * followed by its opposite (Sec. 1.1 "discrete velocity links"). */
+static const int CV[NQ][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double WQ[NQ];
+static int OPP[NQ];
+static double MM[NQ][NQ];   /* moment matrix M[k][i] = e_k(c_i)          */
+static double MINV[NQ][NQ]; /* its inverse by Gauss-Jordan elimination   */
+static double BK[NQ];       /* b_k = sum_i w_i e_k(c_i)^2                */
+static int tables_ready = 0;
+
+/* Moment polynomials e_k(c) of the orthogonal D3Q19 basis. */
+static double basis_poly(int k, const int c[3])
+{
+    double x = c[0], y = c[1], z = c[2];
+    double c2 = x * x + y * y + z * z;
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return c2 - 1.0;
+    case 5: return 3.0 * x * x - c2;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return y * z;
+    case 9: return z * x;
+    case 10: return (3.0 * c2 - 5.0) * x;
+    case 11: return (3.0 * c2 - 5.0) * y;
+    case 12: return (3.0 * c2 - 5.0) * z;
+    case 13: return (y * y - z * z) * x;
+    case 14: return (z * z - x * x) * y;
+    case 15: return (x * x - y * y) * z;
+    case 16: return 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+    case 17: return (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+    case 18: return (2.0 * c2 - 3.0) * (y * y - z * z);
+    }
+    return 0.0;
+}
+
+/* Plain Gauss-Jordan inversion with partial pivoting; returns 0 on success. */
+static int invert(int n, const double *a, double *inv)
+{
+    double *m = (double *)malloc(sizeof(double) * n * 2 * n);
+    if (!m) return -1;
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c)
+            m[r * 2 * n + c] = c < n ? a[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(m[r * 2 * n + col]) > fabs(m[piv * 2 * n + col])) piv = r;
+        if (fabs(m[piv * 2 * n + col]) < 1e-14) { free(m); return -1; }
+        if (piv != col)
+            for (int c = 0; c < 2 * n; ++c) {
+                double t = m[col * 2 * n + c];
+                m[col * 2 * n + c] = m[piv * 2 * n + c];
+                m[piv * 2 * n + c] = t;
+            }
+        double d = m[col * 2 * n + col];
+        for (int c = 0; c < 2 * n; ++c) m[col * 2 * n + c] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            double fct = m[r * 2 * n + col];
+            if (fct == 0.0) continue;
+            for (int c = 0; c < 2 * n; ++c) m[r * 2 * n + c] -= fct * m[col * 2 * n + c];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) inv[r * n + c] = m[r * 2 * n + n + c];
+    free(m);
+    return 0;
+}
+
+static void init_tables(void)
+{
+    if (tables_ready) return;
+    for (int i = 0; i < NQ; ++i) {
+        int c2 = CV[i][0] * CV[i][0] + CV[i][1] * CV[i][1] + CV[i][2] * CV[i][2];
+        WQ[i] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        for (int j = 0; j < NQ; ++j)
+            if (CV[j][0] == -CV[i][0] && CV[j][1] == -CV[i][1] && CV[j][2] == -CV[i][2])
+                OPP[i] = j;
+    }
+    for (int k = 0; k < NQ; ++k) {
+        BK[k] = 0.0;
+        for (int i = 0; i < NQ; ++i) {
+            MM[k][i] = basis_poly(k, CV[i]);
+            BK[k] += WQ[i] * MM[k][i] * MM[k][i];
+        }
+    }
+    invert(NQ, &MM[0][0], &MINV[0][0]);
+    tables_ready = 1;
+}
+
+/* ----------------------------------------------------------------- Philox */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+ * 32x32->64 multiplications with the round key bumped by the Weyl
+ * constants between rounds. */
+static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform variate of zero mean and unit variance from 32 random bits:
+ * u = (x + 1/2) 2^-32 in (0,1), xi = sqrt(12) (u - 1/2). */
+static double unit_uniform(uint32_t x)
+{
+    double u = ((double)x + 0.5) * (1.0 / 4294967296.0);
+    return sqrt(12.0) * (u - 0.5);
+}
+
+/* ------------------------------------------------------------- parameters */
+
+typedef struct {
+    int nx, ny, nz;
+    int collision;          /* 0 BGK, 1 MRT */
+    double tau;             /* BGK relaxation time */
+    double gamma_shear, gamma_bulk, gamma_odd, gamma_even; /* MRT: m* - m_eq = g (m - m_eq) */
+    double rho0;
+    double kT;              /* thermal energy (MRT only) */
+    double gamma_bead;      /* xi_bead of Eq. (latticeboltzmannfriction) */
+    uint64_t seed;
+    uint32_t instance;      /* third Philox counter word */
+    double body_force[3];   /* uniform force density on the fluid */
+    int compensate_force;   /* add -sum(F_ext)/N_fluid to the fluid */
+} orc_params;
+
+typedef struct {
+    int nbodies;
+    const int *bead_start;  /* nbodies + 1 offsets into the bead arrays */
+    const double *s;        /* body-frame bead offsets, 3 per bead */
+    double *X, *V, *q, *w;  /* per body: COM (3), velocity (3), quaternion w,x,y,z (4), body-frame omega (3) */
+    double *F_last;         /* per body: lab-frame total force of the previous step (3) */
+    double *T_last;         /* per body: body-frame total torque of the previous step (3) */
+    const double *mass;     /* per body (1) */
+    const double *inertia;  /* per body, principal moments (3) */
+    const double *F_ext;    /* per body, lab frame (3) */
+    const double *T_ext;    /* per body, lab frame (3) */
+    const int *fixed;       /* per body: 1 = kinematics held, not integrated */
+    double *F_bead;         /* out: lab-frame force on each bead (3 per bead) */
+    double *F_tot, *T_tot;  /* out: per body, lab-frame total force and torque (3, 3) */
+} orc_bodies;
+
+static size_t nidx(const orc_params *p, int x, int y, int z)
+{
+    return (size_t)x + (size_t)p->nx * ((size_t)y + (size_t)p->ny * (size_t)z);
+}
+
+static int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+
+/* Second-order equilibrium (Sec. 1.1 "Maxwell-Boltzmann" relaxation target). */
+static void equilibrium(double rho, const double u[3], double feq[NQ])
+{
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < NQ; ++i) {
+        double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+        feq[i] = WQ[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+/* Guo source term s_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F */
+static void guo_source(const double u[3], const double F[3], double s[NQ])
+{
+    for (int i = 0; i < NQ; ++i) {
+        double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+        double t = 0.0;
+        for (int a = 0; a < 3; ++a) t += (3.0 * (CV[i][a] - u[a]) + 9.0 * cu * CV[i][a]) * F[a];
+        s[i] = WQ[i] * t;
+    }
+}
+
+static double mode_rate(const orc_params *p, int k)
+{
+    if (k < 4) return 0.0;              /* conserved: rate is irrelevant */
+    if (k == 4) return p->gamma_bulk;
+    if (k <= 9) return p->gamma_shear;
+    if (k <= 15) return p->gamma_odd;
+    return p->gamma_even;
+}
+
+/* Collision of one node (Sec. 1.1). f: pre-collision populations, F: force
+ * density on the node, fout: post-collision populations. */
+static void collide_node(const orc_params *p, const double f[NQ], const double F[3],
+                         uint32_t node_id, uint32_t step, double fout[NQ])
+{
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < NQ; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) j[a] += CV[i][a] * f[i];
+    }
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
+    double feq[NQ], s[NQ];
+    equilibrium(rho, u, feq);
+    guo_source(u, F, s);
+
+    if (p->collision == 0) {
+        /* BGK: relax every population on the single time scale tau. */
+        for (int i = 0; i < NQ; ++i)
+            fout[i] = f[i] - (f[i] - feq[i]) / p->tau + (1.0 - 0.5 / p->tau) * s[i];
+        return;
+    }
+
+    /* MRT: m = M f, relax each mode towards M f_eq with its own rate. */
+    double m[NQ], meq[NQ], S[NQ], ms[NQ];
+    for (int k = 0; k < NQ; ++k) {
+        m[k] = meq[k] = S[k] = 0.0;
+        for (int i = 0; i < NQ; ++i) {
+            m[k] += MM[k][i] * f[i];
+            meq[k] += MM[k][i] * feq[i];
+            S[k] += MM[k][i] * s[i];
+        }
+    }
+    for (int k = 0; k < NQ; ++k) {
+        double g = mode_rate(p, k);
+        ms[k] = meq[k] + g * (m[k] - meq[k]) + 0.5 * (1.0 + g) * S[k];
+    }
+    if (p->kT > 0.0) {
+        /* Fluctuating modes: the 15 non-conserved moments get noise of
+         * variance mu b_k (1 - g_k^2), mu = 3 rho kT, so that their
+         * stationary variance is mu b_k. */
+        uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+        uint32_t r[16];
+        for (int call = 0; call < 4; ++call) {
+            uint32_t ctr[4] = {node_id, step, p->instance, (uint32_t)call};
+            philox4x32_10(ctr, key, &r[4 * call]);
+        }
+        double mu = 3.0 * rho * p->kT;
+        for (int k = 4; k < NQ; ++k) {
+            double g = mode_rate(p, k);
+            ms[k] += sqrt(mu * BK[k] * (1.0 - g * g)) * unit_uniform(r[k - 4]);
+        }
+    }
+    for (int i = 0; i < NQ; ++i) {
+        fout[i] = 0.0;
+        for (int k = 0; k < NQ; ++k) fout[i] += MINV[i][k] * ms[k];
+    }
+}
+
+/* Hamilton rotation matrix of the unit quaternion q = (w, x, y, z):
+ * lab vector = R body vector. */
+static void rotation(const double q[4], double R[3][3])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - z * w);
+    R[0][2] = 2.0 * (x * z + y * w);
+    R[1][0] = 2.0 * (x * y + z * w);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - x * w);
+    R[2][0] = 2.0 * (x * z - y * w);
+    R[2][1] = 2.0 * (y * z + x * w);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static void quat_mul(const double a[4], const double b[4], double o[4])
+{
+    double r[4];
+    r[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    r[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    r[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    r[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    memcpy(o, r, sizeof r);
+}
+
+static void cross(const double a[3], const double b[3], double o[3])
+{
+    double r[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    memcpy(o, r, sizeof r);
+}
+
+/* Half kicks of the body-frame angular velocity by Euler's equations,
+ * I dw/dt = T - w x (I w), over dt/2. The kick before the drift is explicit
+ * in w; the kick after it is implicit (fixed-point iteration), so that the
+ * pair of half kicks around each step boundary is the trapezoidal rule and
+ * the rotation integrator is second order and time-symmetric, the property
+ * of the velocity-Verlet rotation schemes cited in Sec. 2.3. */
+static void euler_half_kick(double w[3], const double I[3], const double T[3])
+{
+    double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]}, wxIw[3];
+    cross(w, Iw, wxIw);
+    for (int a = 0; a < 3; ++a) w[a] += 0.5 * (T[a] - wxIw[a]) / I[a];
+}
+
+#define IMPLICIT_KICK_ITERS 6
+
+static void euler_half_kick_implicit(double w[3], const double I[3], const double T[3])
+{
+    double w0[3] = {w[0], w[1], w[2]};
+    for (int it = 0; it < IMPLICIT_KICK_ITERS; ++it) {
+        double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]}, wxIw[3];
+        cross(w, Iw, wxIw);
+        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * (T[a] - wxIw[a]) / I[a];
+    }
+}
+
+/* ------------------------------------------------------------- public API */
+
+int orc_init_tables(void) { init_tables(); return 0; }
+
+void orc_lattice(int *c, double *w, int *opp)
+{
+    init_tables();
+    for (int i = 0; i < NQ; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = CV[i][a];
+        w[i] = WQ[i];
+        opp[i] = OPP[i];
+    }
+}
+
+void orc_mrt_tables(double *M, double *Minv, double *b)
+{
+    init_tables();
+    for (int k = 0; k < NQ; ++k) {
+        b[k] = BK[k];
+        for (int i = 0; i < NQ; ++i) {
+            M[k * NQ + i] = MM[k][i];
+            Minv[k * NQ + i] = MINV[k][i];
+        }
+    }
+}
+
+void orc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    philox4x32_10(ctr, key, out);
+}
+
+double orc_unit_uniform(uint32_t x) { return unit_uniform(x); }
+
+void orc_equilibrium(double rho, const double *u, double *feq)
+{
+    init_tables();
+    equilibrium(rho, u, feq);
+}
+
+void orc_collide_node(const orc_params *p, const double *f, const double *F,
+                      uint32_t node_id, uint32_t step, double *fout)
+{
+    init_tables();
+    collide_node(p, f, F, node_id, step, fout);
+}
+
+void orc_rotation(const double *q, double *R9)
+{
+    double R[3][3];
+    rotation(q, R);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) R9[3 * a + b] = R[a][b];
+}
+
+void orc_quat_mul(const double *a, const double *b, double *o) { quat_mul(a, b, o); }
+
+/* Cylindrical pore (Sec. 2.3): the axis runs along `axis` through the box
+ * centre; a node whose centre (integer + 1/2) lies at distance >= R from the
+ * axis is a wall (boundary) node, so that along a lattice direction the first
+ * wall node sits half a grid spacing outside a wall of radius R. */
+void orc_pore_mask(int nx, int ny, int nz, double R, int axis, unsigned char *mask)
+{
+    int n[3] = {nx, ny, nz};
+    int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+    double c1 = 0.5 * n[a1], c2 = 0.5 * n[a2];
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int r[3] = {x, y, z};
+                double d1 = r[a1] + 0.5 - c1, d2 = r[a2] + 0.5 - c2;
+                mask[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)] =
+                    (d1 * d1 + d2 * d2 >= R * R) ? 1 : 0;
+            }
+}
+
+/* Populations at rest: f_i = w_i rho0 on every node. f is [19][N]. */
+void orc_init(const orc_params *p, double *f)
+{
+    init_tables();
+    size_t N = (size_t)p->nx * p->ny * p->nz;
+    for (int i = 0; i < NQ; ++i)
+        for (size_t n = 0; n < N; ++n) f[(size_t)i * N + n] = WQ[i] * p->rho0;
+}
+
+/* Mass and momentum of the fluid nodes: out = {sum f, sum c_x f, sum c_y f,
+ * sum c_z f}. Neumaier-compensated sums over the nodes, so that the
+ * conservation checks see the step's own round-off and not the reduction's. */
+static void kadd(double *s, double *c, double v)
+{
+    double t = *s + v;
+    if (fabs(*s) >= fabs(v)) *c += (*s - t) + v;
+    else *c += (v - t) + *s;
+    *s = t;
+}
+
+void orc_moments_sum(const orc_params *p, const double *f, const unsigned char *mask, double *out)
+{
+    init_tables();
+    size_t N = (size_t)p->nx * p->ny * p->nz;
+    double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    for (size_t n = 0; n < N; ++n) {
+        if (mask && mask[n]) continue;
+        for (int i = 0; i < NQ; ++i) {
+            double v = f[(size_t)i * N + n];
+            kadd(&s[0], &c[0], v);
+            for (int a = 0; a < 3; ++a)
+                if (CV[i][a]) kadd(&s[a + 1], &c[a + 1], CV[i][a] * v);
+        }
+    }
+    for (int a = 0; a < 4; ++a) out[a] = s[a] + c[a];
+}
+
+/* Node density and velocity u = (j + F/2)/rho for every node (F may be NULL). */
+void orc_node_velocity(const orc_params *p, const double *f, const double *F, double *rho, double *u)
+{
+    init_tables();
+    size_t N = (size_t)p->nx * p->ny * p->nz;
+    for (size_t n = 0; n < N; ++n) {
+        double r = 0.0, j[3] = {0, 0, 0};
+        for (int i = 0; i < NQ; ++i) {
+            double v = f[(size_t)i * N + n];
+            r += v;
+            for (int a = 0; a < 3; ++a) j[a] += CV[i][a] * v;
+        }
+        rho[n] = r;
+        for (int a = 0; a < 3; ++a)
+            u[3 * n + a] = (j[a] + (F ? 0.5 * (p->body_force[a] + F[(size_t)a * N + n]) : 0.0)) / r;
+    }
+}
+
+/*
+ * One full step. f: [19][N] pre-collision populations (updated in place to
+ * the next pre-collision populations). mask: N bytes, 1 = wall node (NULL =
+ * none). Fnode: [3][N] bead force density spread onto the nodes by the
+ * previous step (read for the bead velocity interpolation, then replaced by
+ * this step's). b: bodies (NULL or nbodies == 0 for a plain fluid step).
+ * step: the step index, second Philox counter word.
+ *
+ * Order within the step:
+ *  1. bodies: first half kick with last step's force/torque, drift
+ *     (velocity Verlet for the COM; quaternion rotated by the half-step
+ *     body-frame angular velocity), Sec. 2.3;
+ *  2. virtual sites r_b = X + R(q) s_b, v_b = V + omega x (r_b - X), Sec. 1.2;
+ *  3. bead coupling, Eq. (latticeboltzmannfriction): trilinear u at r_b from
+ *     the 8 surrounding nodes, F_b = -gamma (v_b - u) + f_s, -w_j F_b spread
+ *     onto the same nodes, F and T summed onto the body (Sec. 2.3);
+ *  4. collision of every fluid node with the force g + spread force;
+ *  5. push streaming; a population streaming into a wall node returns to
+ *     its origin in the opposite direction (halfway bounce-back, Sec. 1.1);
+ *  6. bodies: second half kick with this step's force and torque.
+ * Returns 0, or -1 on bad input.
+ */
+int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *Fnode,
+             orc_bodies *b, int64_t step)
+{
+    init_tables();
+    if (p->collision == 0 && p->kT > 0.0) return -1;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const uint32_t step32 = (uint32_t)step;
+    const int nbodies = b ? b->nbodies : 0;
+
+    size_t nfluid = 0;
+    for (size_t n = 0; n < N; ++n) nfluid += (mask && mask[n]) ? 0 : 1;
+
+    /* uniform force density on the fluid */
+    double g[3];
+    for (int a = 0; a < 3; ++a) g[a] = p->body_force[a];
+    if (p->compensate_force && nfluid > 0)
+        for (int bi = 0; bi < nbodies; ++bi)
+            if (!b->fixed[bi])
+                for (int a = 0; a < 3; ++a) g[a] -= b->F_ext[3 * bi + a] / (double)nfluid;
+
+    double *Fnew = (double *)calloc(3 * N, sizeof(double));
+    double *fpost = (double *)malloc(sizeof(double) * NQ * N);
+    if (!Fnew || !fpost) { free(Fnew); free(fpost); return -1; }
+
+    /* 1. first half kick and drift */
+    for (int bi = 0; bi < nbodies; ++bi) {
+        if (b->fixed[bi]) continue;
+        double M = b->mass[bi];
+        double *X = &b->X[3 * bi], *V = &b->V[3 * bi], *q = &b->q[4 * bi], *w = &b->w[3 * bi];
+        for (int a = 0; a < 3; ++a) {
+            V[a] += 0.5 * b->F_last[3 * bi + a] / M;
+            X[a] += V[a];
+        }
+        euler_half_kick(w, &b->inertia[3 * bi], &b->T_last[3 * bi]);
+        double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (wn > 0.0) {
+            double h = 0.5 * wn;
+            double dq[4] = {cos(h), sin(h) * w[0] / wn, sin(h) * w[1] / wn, sin(h) * w[2] / wn};
+            quat_mul(q, dq, q);
+        }
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int a = 0; a < 4; ++a) q[a] /= qn;
+    }
+
+    /* 2.-3. virtual sites and coupling */
+    for (int bi = 0; bi < nbodies; ++bi) {
+        double R[3][3];
+        rotation(&b->q[4 * bi], R);
+        const double *X = &b->X[3 * bi], *V = &b->V[3 * bi], *wb = &b->w[3 * bi];
+        double wl[3];
+        for (int a = 0; a < 3; ++a) wl[a] = R[a][0] * wb[0] + R[a][1] * wb[1] + R[a][2] * wb[2];
+        double Ft[3] = {0, 0, 0}, Tt[3] = {0, 0, 0};
+        for (int k = b->bead_start[bi]; k < b->bead_start[bi + 1]; ++k) {
+            const double *s = &b->s[3 * k];
+            double rel[3], r[3], v[3], wxr[3];
+            for (int a = 0; a < 3; ++a) rel[a] = R[a][0] * s[0] + R[a][1] * s[1] + R[a][2] * s[2];
+            for (int a = 0; a < 3; ++a) r[a] = X[a] + rel[a];
+            cross(wl, rel, wxr);
+            for (int a = 0; a < 3; ++a) v[a] = V[a] + wxr[a];
+
+            /* the 8 nodes around r; node centres at integer + 1/2 */
+            int base[3];
+            double frac[3];
+            for (int a = 0; a < 3; ++a) {
+                double t = r[a] - 0.5;
+                double fl = floor(t);
+                base[a] = (int)fl;
+                frac[a] = t - fl;
+            }
+            double ub[3] = {0, 0, 0};
+            size_t node[8];
+            double wgt[8];
+            int fluid[8];
+            for (int cidx = 0; cidx < 8; ++cidx) {
+                int o[3] = {cidx & 1, (cidx >> 1) & 1, (cidx >> 2) & 1};
+                double wt = 1.0;
+                for (int a = 0; a < 3; ++a) wt *= o[a] ? frac[a] : 1.0 - frac[a];
+                int xx = wrap(base[0] + o[0], nx), yy = wrap(base[1] + o[1], ny), zz = wrap(base[2] + o[2], nz);
+                size_t n = nidx(p, xx, yy, zz);
+                node[cidx] = n;
+                wgt[cidx] = wt;
+                fluid[cidx] = !(mask && mask[n]);
+                if (!fluid[cidx]) continue; /* wall nodes carry u = 0 */
+                double rho = 0.0, j[3] = {0, 0, 0};
+                for (int i = 0; i < NQ; ++i) {
+                    double fv = f[(size_t)i * N + n];
+                    rho += fv;
+                    for (int a = 0; a < 3; ++a) j[a] += CV[i][a] * fv;
+                }
+                for (int a = 0; a < 3; ++a)
+                    ub[a] += wt * (j[a] + 0.5 * (g[a] + Fnode[(size_t)a * N + n])) / rho;
+            }
+            double Fb[3];
+            double fs[3] = {0, 0, 0};
+            if (p->kT > 0.0 && p->gamma_bead > 0.0) {
+                uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+                uint32_t ctr[4] = {(uint32_t)k, step32, p->instance, 4u};
+                uint32_t rr[4];
+                philox4x32_10(ctr, key, rr);
+                double amp = sqrt(2.0 * p->kT * p->gamma_bead);
+                for (int a = 0; a < 3; ++a) fs[a] = amp * unit_uniform(rr[a]);
+            }
+            for (int a = 0; a < 3; ++a) Fb[a] = -p->gamma_bead * (v[a] - ub[a]) + fs[a];
+            for (int cidx = 0; cidx < 8; ++cidx) {
+                if (!fluid[cidx]) continue; /* momentum into a wall node is taken by the wall */
+                for (int a = 0; a < 3; ++a) Fnew[(size_t)a * N + node[cidx]] -= wgt[cidx] * Fb[a];
+            }
+            double tq[3];
+            cross(rel, Fb, tq);
+            for (int a = 0; a < 3; ++a) {
+                b->F_bead[3 * k + a] = Fb[a];
+                Ft[a] += Fb[a];
+                Tt[a] += tq[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            b->F_tot[3 * bi + a] = Ft[a] + b->F_ext[3 * bi + a];
+            b->T_tot[3 * bi + a] = Tt[a] + b->T_ext[3 * bi + a];
+        }
+    }
+
+    /* 4. collision */
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t n = nidx(p, x, y, z);
+                if (mask && mask[n]) {
+                    for (int i = 0; i < NQ; ++i) fpost[(size_t)i * N + n] = f[(size_t)i * N + n];
+                    continue;
+                }
+                double fl[NQ], fo[NQ], F[3];
+                for (int i = 0; i < NQ; ++i) fl[i] = f[(size_t)i * N + n];
+                for (int a = 0; a < 3; ++a) F[a] = g[a] + Fnew[(size_t)a * N + n];
+                collide_node(p, fl, F, (uint32_t)n, step32, fo);
+                for (int i = 0; i < NQ; ++i) fpost[(size_t)i * N + n] = fo[i];
+            }
+
+    /* 5. push streaming with halfway bounce-back; wall nodes keep their values */
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t n = nidx(p, x, y, z);
+                if (mask && mask[n]) continue;
+                for (int i = 0; i < NQ; ++i) {
+                    size_t to = nidx(p, wrap(x + CV[i][0], nx), wrap(y + CV[i][1], ny), wrap(z + CV[i][2], nz));
+                    if (mask && mask[to])
+                        f[(size_t)OPP[i] * N + n] = fpost[(size_t)i * N + n];
+                    else
+                        f[(size_t)i * N + to] = fpost[(size_t)i * N + n];
+                }
+            }
+
+    /* 6. second half kick */
+    for (int bi = 0; bi < nbodies; ++bi) {
+        double R[3][3];
+        rotation(&b->q[4 * bi], R);
+        double Tb[3];
+        const double *Tl = &b->T_tot[3 * bi];
+        for (int a = 0; a < 3; ++a) Tb[a] = R[0][a] * Tl[0] + R[1][a] * Tl[1] + R[2][a] * Tl[2];
+        for (int a = 0; a < 3; ++a) {
+            b->F_last[3 * bi + a] = b->F_tot[3 * bi + a];
+            b->T_last[3 * bi + a] = Tb[a];
+        }
+        if (b->fixed[bi]) continue;
+        for (int a = 0; a < 3; ++a) b->V[3 * bi + a] += 0.5 * b->F_tot[3 * bi + a] / b->mass[bi];
+        euler_half_kick_implicit(&b->w[3 * bi], &b->inertia[3 * bi], Tb);
+    }
+
+    memcpy(Fnode, Fnew, sizeof(double) * 3 * N);
+    free(Fnew);
+    free(fpost);
+    return 0;
+}
