@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Throughput of the LB + raspberry-coupling step on the GB300.
+
+One step = one pass of the whole hot path over the lattice: bodies half-kick
+and drift, virtual sites, bead coupling (interpolate, drag, spread, reduce),
+fused collide-and-stream with bounce-back, bodies second half-kick.
+
+Default workload: 256^3 periodic D3Q19 box, MRT (nu = 0.016) with thermal
+fluctuations (kT = 1e-4, Philox noise), populations stored in FP32 as
+deviations from w_i rho0, 64 prolate ellipsoidal raspberries (aspect 2-4,
+semi-axes 2-8, 1 bead per unit area, ~23k beads) at seeded positions and
+orientations. Inputs are synthetic and seeded; the state (1.27 GB of
+populations) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = "ellipsoids64_256^3_mrt_kT_fp32"
+METRIC = "MLUPS incl. coupling (D3Q19 MRT + fluctuations + raspberry coupling)"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d and d[k]:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lb_fluid.cu", "lb_device.cuh", "lb_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1604_01829_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_key):
+    """DRAM bytes per launch of the collide kernel from the committed ncu
+    summary, or None if none exists or the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(workload_key)
+        if not e or e.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(precision):
+    from paper_1604_01829_gb300 import workloads as W
+    return W.ellipsoids_256(precision=precision)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_1604_01829_gb300 import build, lb
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier_max(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def measure(precision, steps, warmup, with_clocks):
+        w = build_workload(precision)
+        stream = torch.cuda.Stream()
+        L = lb.from_workload(w, stream=stream.cuda_stream)
+        N = w.nodes
+        L.lb_step(warmup)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if with_clocks else None
+        if clocks:
+            clocks.start()
+        L.lb_set_timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lb_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, klaunch = L.lb_kernel_time()
+        L.lb_set_timing(False)
+        clk = clocks.stop() if clocks else None
+        if dist is not None:
+            dist.barrier()
+        ms_max = barrier_max(ms)
+        m, p = L.lb_conservation()   # raises on non-finite state
+        res = dict(ms=ms_max, kernel_ms=kms / max(klaunch, 1), launches=klaunch, nodes=N,
+                   nbeads=w.nbeads, nbodies=len(w.bodies), clocks=clk, L=L, w=w)
+        return res
+
+    main = measure(32, args.steps, args.warmup, True)
+    N = main["nodes"]
+    K = args.steps
+    value = N * K * ws / (main["ms"] * 1e-3) / 1e6
+    peak, peak_kind = measured_peak()
+    bytes_per_node = 2 * 19 * 4
+    achieved = bytes_per_node * N / (main["kernel_ms"] * 1e-3) / 1e9
+    traffic = ncu_traffic(WORKLOAD)
+
+    # end to end through the C ABI with host buffers: per step the host sets
+    # the external forces of every body (H2D) and reads every body's force
+    # and torque back (D2H)
+    L, w = main["L"], main["w"]
+    nb = len(w.bodies)
+    Fext = np.zeros(3 * nb)
+    Text = np.zeros(3 * nb)
+    Fout = np.zeros(3 * nb)
+    Tout = np.zeros(3 * nb)
+    e2e_steps = max(10, min(K, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.lb_set_external_forces(Fext, Text)
+        L.lb_step(1)
+        L.lb_forces_all(Fout, Tout)
+    t1 = time.perf_counter()
+    e2e_ms = barrier_max((t1 - t0) * 1e3 / e2e_steps)
+    e2e_value = N * ws / (e2e_ms * 1e-3) / 1e6
+    main["L"].close()
+    del main["L"]
+
+    # FP64 populations on the same workload (the metric compares FP32 and FP64)
+    k64 = max(3, K // 2)
+    fp64 = measure(64, k64, max(3, args.warmup // 2), False)
+    fp64_value = fp64["nodes"] * k64 * ws / (fp64["ms"] * 1e-3) / 1e6
+    fp64_ach = 2 * 19 * 8 * fp64["nodes"] / (fp64["kernel_ms"] * 1e-3) / 1e9
+    fp64["L"].close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": round(value, 1),
+            "unit": "MLUPS",
+            "n_gpus": ws,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": round(main["ms"] / K, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded ellipsoidal raspberries, Philox thermal noise)",
+            "config": {"workload": WORKLOAD, "lattice": [256, 256, 256], "collision": "MRT",
+                       "kT": 1e-4, "nu": 0.016, "bodies": main["nbodies"], "beads": main["nbeads"],
+                       "storage": "fp32 deviation f - w rho0", "l2": "state 1.27 GB > L2, no flush",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": "k_collide_stream<float,MRT,noise>",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "bytes_per_node": bytes_per_node,
+                         "kernel_ms": round(main["kernel_ms"], 5),
+                         "traffic": traffic},
+            "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "steps": e2e_steps,
+                    "h2d_bytes_per_step": 2 * 3 * 8 * nb, "d2h_bytes_per_step": 2 * 3 * 8 * nb},
+            "gpu_launches": 5 * K + 1,
+            "fp64": {"value": round(fp64_value, 1), "unit": "MLUPS", "steps": k64,
+                     "ms_per_step": round(fp64["ms"] / k64, 4),
+                     "kernel_achieved_gbs": round(fp64_ach, 1),
+                     "frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8},
+            "clocks": main["clocks"],
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def oracle_sample(seconds):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    a 64^3 periodic box (1/64 of the lattice) with the same physics, holding
+    the first ellipsoid of the workload (about the full box's nodes-per-bead
+    ratio), run for as many steps as fit in ~`seconds`."""
+    from oracle import oracle as O
+    from paper_1604_01829_gb300 import workloads as W
+    w = W.ellipsoids_256(n_bodies=1, L=64, precision=64)
+    p = w.params
+    o = O.OracleLB(64, 64, 64, **{k: p[k] for k in ("collision", "gamma_shear", "gamma_bulk", "gamma_odd",
+                                                      "gamma_even", "rho0", "kT", "gamma_bead", "seed")})
+    b = w.bodies[0]
+    o.add_raspberry(b.beads, b.X, b.q, b.mass, b.inertia)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    n = max(1, int(seconds / per) - 1)
+    o.step(n)
+    t2 = time.perf_counter()
+    steps = n + 1
+    mlups = w.nodes * steps / (t2 - t0) / 1e6
+    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"64^3 periodic box, MRT + fluctuations, 1 ellipsoid ({w.nbeads} beads), {steps} steps, "
+                      f"{t2 - t0:.1f} s, single thread"}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle on a bounded sample, K timed steps."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1604_01829_gb300 import workloads as W
+    w = W.ellipsoids_256(n_bodies=1, L=64, precision=64)
+    p = w.params
+    o = O.OracleLB(64, 64, 64, **{k: p[k] for k in ("collision", "gamma_shear", "gamma_bulk", "gamma_odd",
+                                                      "gamma_even", "rho0", "kT", "gamma_bead", "seed")})
+    b = w.bodies[0]
+    o.add_raspberry(b.beads, b.X, b.q, b.mass, b.inertia)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    t1 = time.perf_counter()
+    v = w.nodes * args.steps / (t1 - t0) / 1e6
+    sample = f"64^3 periodic box (1/64 of the 256^3 lattice), MRT + fluctuations, 1 ellipsoid, {args.steps} steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round((t1 - t0) * 1e3 / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * lb.h - C ABI of the GB300 lattice Boltzmann + raspberry-colloid library.
+ *
+ * The library advances a D3Q19 lattice Boltzmann fluid coupled by point
+ * friction to rigid "raspberry" colloids, the method of Ustach & Faller,
+ * "The Raspberry model for protein-like particles: ellipsoids and confinement
+ * in cylindrical pores" (arXiv:1604.01829):
+ *   - fluid: streaming along the discrete velocity links and a collision that
+ *     relaxes towards equilibrium on one time scale (BGK) or mode by mode
+ *     (multiple relaxation times), deterministic or with thermal noise;
+ *     boundary nodes reflect what streams into them (Sec. 1.1);
+ *   - coupling: each bead feels F = -gamma (v - u(r,t)) + f_s with u
+ *     interpolated from the nearest nodes, Eq. (latticeboltzmannfriction)
+ *     in Sec. 1.1; -F goes back to the same nodes;
+ *   - bodies: beads are virtual sites of a rigid body whose centre of mass
+ *     moves by velocity Verlet and whose orientation is a quaternion
+ *     (Sec. 1.2, Sec. 2.3);
+ *   - pores: cylindrical walls with boundary nodes half a grid spacing
+ *     outside the wall (Sec. 2.3).
+ *
+ * Units: lattice units throughout (grid spacing 1, time step 1, fluid mass
+ * per node rho0). Node (x, y, z), 0 <= x < nx etc., has its centre at
+ * (x + 1/2, y + 1/2, z + 1/2) and linear index x + nx (y + ny z).
+ * Populations are exchanged as double arrays [19][N] in the velocity order
+ * of lb_lattice().
+ *
+ * Conventions: every call returns an lb_status; none aborts, prints or
+ * throws. Inputs are copied (the caller keeps ownership of its buffers);
+ * outputs go to caller-owned buffers. Pointer arguments are HOST pointers
+ * unless the name says otherwise. The library owns all device memory it
+ * allocates; lb_destroy frees it. A handle is not thread-safe: one host
+ * thread at a time per handle. Device work is issued on the stream given at
+ * creation (or a private stream); calls that return data to the host
+ * synchronise that stream.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx *lb_handle;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,      /* invalid argument or unsupported combination   */
+    LB_ERR_OOM = 2,      /* device or host allocation failed              */
+    LB_ERR_CUDA = 3,     /* a CUDA call failed (message in lb_last_error) */
+    LB_ERR_UNSTABLE = 4, /* non-finite mass or momentum detected          */
+    LB_ERR_TIMEOUT = 5,  /* a bounded device wait ran out                 */
+    LB_ERR_STATE = 6     /* call not valid in the current state           */
+} lb_status;
+
+typedef struct {
+    int nx, ny, nz;          /* lattice size, each >= 2                              */
+    int precision;           /* 64: FP64 populations; 32: FP32 populations stored as
+                                f_i - w_i rho0 (compute in FP32, bodies and
+                                reductions in FP64)                                  */
+    int collision;           /* 0: BGK (Sec. 1.1 single time scale); 1: MRT          */
+    double tau;              /* BGK relaxation time (> 1/2)                          */
+    double gamma_shear;      /* MRT: non-equilibrium part of each mode is multiplied */
+    double gamma_bulk;       /*   by its rate per step, m* - m_eq = g (m - m_eq);     */
+    double gamma_odd;        /*   |g| < 1. Shear: g = (6 nu - 1)/(6 nu + 1).          */
+    double gamma_even;       /*   odd / even: kinetic (ghost) modes.                  */
+    double rho0;             /* reference density (> 0)                              */
+    double kT;               /* thermal energy; > 0 enables fluctuating MRT modes
+                                and bead noise (MRT only)                            */
+    double gamma_bead;       /* bead friction gamma of Eq. (latticeboltzmannfriction),
+                                lattice units (>= 0)                                 */
+    unsigned long long seed; /* Philox4x32-10 key                                    */
+    unsigned int instance;   /* third Philox counter word (independent replicas)     */
+    double body_force[3];    /* uniform force density on every fluid node            */
+    int compensate_force;    /* 1: add -sum(F_ext of free bodies)/N_fluid to the
+                                fluid so the total momentum stays constant           */
+    int md_substeps;         /* MD steps per LB step; only 1 is supported            */
+} lb_params;
+
+/* Creates a lattice with every population at rest, f_i = w_i rho0.
+ * cuda_stream: a cudaStream_t to issue work on, or NULL for a private stream.
+ * On success *out holds the new handle. Errors: LB_ERR_ARG (bad params),
+ * LB_ERR_OOM, LB_ERR_CUDA (no device, launch failure). */
+lb_status lb_create(const lb_params *params, void *cuda_stream, lb_handle *out);
+
+/* Frees all device and host memory of the handle. NULL is accepted. */
+lb_status lb_destroy(lb_handle h);
+
+/* Cylindrical pore (Sec. 2.3): wall along `axis` (0 x, 1 y, 2 z) through the
+ * box centre; a node whose centre lies at distance >= radius from the axis is
+ * a boundary node, so the first boundary node along a lattice direction sits
+ * half a grid spacing outside the wall. Populations streaming into boundary
+ * nodes return to their origin reversed (halfway bounce-back). Only before
+ * the first lb_step. Errors: LB_ERR_ARG, LB_ERR_STATE. */
+lb_status lb_set_pore(lb_handle h, double radius, int axis);
+
+/* Adds a rigid raspberry (Sec. 1.2): nbeads body-frame bead offsets
+ * beads_body_xyz[3*nbeads] relative to the centre of mass X[3], orientation
+ * q[4] = (w, x, y, z) (normalised by the library), mass and principal
+ * moments inertia[3] (body axes = principal axes), constant external force
+ * F_ext[3] and torque T_ext[3] (lab frame, may be NULL = 0). fixed = 1 holds
+ * the body's position, orientation and velocities (a fixed colloid in flow).
+ * *body_id receives the body index (0, 1, ...). Only before the first lb_step.
+ * Errors: LB_ERR_ARG, LB_ERR_STATE. */
+lb_status lb_add_raspberry(lb_handle h, const double *beads_body_xyz, int nbeads,
+                           const double X[3], const double q[4], double mass,
+                           const double inertia[3], const double F_ext[3],
+                           const double T_ext[3], int fixed, int *body_id);
+
+/* Sets the kinematic state of a body: centre X, velocity V, orientation q,
+ * body-frame angular velocity w (any pointer may be NULL = unchanged). */
+lb_status lb_set_body_state(lb_handle h, int body_id, const double X[3], const double V[3],
+                            const double q[4], const double w[3]);
+
+/* Replaces the external forces and torques of the first nbodies bodies from
+ * F_ext[3*nbodies], T_ext[3*nbodies] (lab frame; T_ext may be NULL = 0). */
+lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, const double *T_ext);
+
+/* Advances nsteps LB steps. One step: (1) bodies half-kick and drift,
+ * (2) virtual sites, (3) bead coupling with trilinear interpolation and
+ * spread, (4) fused collision + in-place streaming with halfway
+ * bounce-back, (5) bodies second half-kick. Asynchronous on the handle's
+ * stream. Errors: LB_ERR_ARG (nsteps < 0), LB_ERR_CUDA. */
+lb_status lb_step(lb_handle h, int nsteps);
+
+/* Total force F[3] and torque T[3] (lab frame, about the centre of mass) on
+ * body_id from the last step: sum of bead forces plus F_ext / T_ext, the
+ * quantity of Eq. (stokesflow). per_bead_xyz (may be NULL) receives the
+ * 3*nbeads bead forces of that body. Synchronises. */
+lb_status lb_forces(lb_handle h, int body_id, double F[3], double T[3], double *per_bead_xyz);
+
+/* F[3*nbodies], T[3*nbodies] for the first nbodies bodies. Synchronises. */
+lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T);
+
+/* Body state X[3], V[3], q[4], body-frame w[3] (any may be NULL). */
+lb_status lb_get_body(lb_handle h, int body_id, double X[3], double V[3], double q[4], double w[3]);
+
+/* Pre-collision populations of the current step as double [19][N]
+ * (n == 19*N). Boundary-node entries are unspecified. Synchronises. */
+lb_status lb_get_populations(lb_handle h, double *host, size_t n);
+
+/* Replaces the pre-collision populations of the current step. */
+lb_status lb_set_populations(lb_handle h, const double *host, size_t n);
+
+/* Pre-collision populations of `count` nodes given by linear index
+ * nodes[count] into out[19*count] (node-major). Synchronises. */
+lb_status lb_sample_populations(lb_handle h, const long long *nodes, int count, double *out);
+
+/* Bead force density spread onto the nodes by the last step (the force the
+ * last collision used, without body_force), as double [3][N]. */
+lb_status lb_get_node_force(lb_handle h, double *host, size_t n);
+
+/* Fluid mass sum f and momentum sum c f of the pre-collision populations,
+ * reduced in FP64. Returns LB_ERR_UNSTABLE if either is not finite. */
+lb_status lb_conservation(lb_handle h, double *mass, double mom[3]);
+
+typedef struct {
+    long long nodes, fluid_nodes, step;
+    int nbodies, nbeads, precision;
+    size_t device_bytes;
+} lb_info_t;
+
+lb_status lb_info(lb_handle h, lb_info_t *info);
+
+/* Kernel timing: when on, CUDA events bracket every launch of the fused
+ * collide-and-stream kernel on the handle's stream. lb_kernel_time returns
+ * (synchronising) the summed device time in ms and the number of timed
+ * launches since the last call, then resets the counters. */
+lb_status lb_set_timing(lb_handle h, int on);
+lb_status lb_kernel_time(lb_handle h, double *total_ms, long long *launches);
+
+/* Message of the last failed call on h (or of the last failed lb_create when
+ * h is NULL). Owned by the library, valid until the next call. */
+const char *lb_last_error(lb_handle h);
+const char *lb_status_string(lb_status s);
+
+/* Host-only: the velocity set c[19*3], weights w[19] and opposite-link table
+ * opp[19] the library uses. Needs no GPU. Returns 19. */
+int lb_lattice(int *c, double *w, int *opp);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

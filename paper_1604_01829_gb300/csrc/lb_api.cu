@@ -1,0 +1,694 @@
+// C ABI (include/lb.h) and host runtime: parameter validation, device
+// memory, the per-step launch sequence, population and force I/O, kernel
+// timing. Every entry point returns an lb_status and never throws.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+using lbk::Body;
+
+struct lb_ctx {
+    lb_params p{};
+    lbk::Geom g{};
+    bool fp32 = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *f = nullptr;
+    double *gforce = nullptr;               // device (3)
+    unsigned long long *step_dev = nullptr; // device step counter
+    long long step = 0;                     // host mirror
+    long long nfluid = 0;
+    double sig[15] = {};
+    // bead force fields (double buffered) and their 4x4x4 tile flags
+    double *Fbuf[2] = {nullptr, nullptr};
+    unsigned char *tiles[2] = {nullptr, nullptr};
+    int ntx = 0, nty = 0, ntz = 0;
+    // bodies
+    std::vector<Body> hb;
+    std::vector<double> hs;
+    std::vector<int> hbody_of;
+    std::vector<int> bead_start{0};
+    Body *db = nullptr;
+    double *ds = nullptr;
+    int *dbody_of = nullptr;
+    double *dFbead = nullptr;
+    bool uploaded = false;
+    // reductions
+    double *partials = nullptr;
+    double *out4 = nullptr;
+    int red_blocks = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // pairs
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    long long timed_n = 0;
+    dim3 block{128, 1, 1};
+    size_t dev_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lb_status fail(lb_ctx *h, lb_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx *h, cudaError_t e, const char *where) {
+    return fail(h, LB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(h, call)                                                  \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);          \
+    } while (0)
+
+template <typename P>
+lb_status dev_alloc(lb_ctx *h, P **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(h, LB_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+    h->dev_bytes += bytes;
+    return LB_OK;
+}
+
+double nodes_of(const lb_ctx *h) { return (double)h->g.N; }
+
+void compute_gforce(const lb_ctx *h, double g[3]) {
+    for (int a = 0; a < 3; ++a) g[a] = h->p.body_force[a];
+    if (h->p.compensate_force && h->nfluid > 0)
+        for (const Body &b : h->hb)
+            if (!b.fixed)
+                for (int a = 0; a < 3; ++a) g[a] -= b.F_ext[a] / (double)h->nfluid;
+}
+
+lb_status upload_gforce(lb_ctx *h) {
+    static thread_local double g[3];
+    compute_gforce(h, g);
+    LB_CUDA(h, cudaMemcpyAsync(h->gforce, g, sizeof(g), cudaMemcpyHostToDevice, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+long long count_fluid(const lb_ctx *h) {
+    if (h->g.pore_axis < 0) return h->g.N;
+    const int ax = h->g.pore_axis;
+    const int na = ax == 0 ? h->g.ny : h->g.nx;
+    const int nb = ax == 2 ? h->g.ny : h->g.nz;
+    const int nl = ax == 0 ? h->g.nx : (ax == 1 ? h->g.ny : h->g.nz);
+    long long c = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < na; ++a) {
+            const long long da = 2LL * a + 1 - na, db = 2LL * b + 1 - nb;
+            if (da * da + db * db < h->g.pore_t) ++c;
+        }
+    return c * nl;
+}
+
+lb_status upload_bodies(lb_ctx *h) {
+    if (h->uploaded) return LB_OK;
+    const int nb = (int)h->hb.size();
+    const int nbeads = (int)h->hbody_of.size();
+    if (nb > 0) {
+        lb_status s;
+        if ((s = dev_alloc(h, &h->db, sizeof(Body) * nb)) != LB_OK) return s;
+        if ((s = dev_alloc(h, &h->ds, sizeof(double) * 3 * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
+        if ((s = dev_alloc(h, &h->dbody_of, sizeof(int) * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
+        if ((s = dev_alloc(h, &h->dFbead, sizeof(double) * 3 * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
+        LB_CUDA(h, cudaMemcpyAsync(h->db, h->hb.data(), sizeof(Body) * nb, cudaMemcpyHostToDevice, h->stream));
+        if (nbeads > 0) {
+            LB_CUDA(h, cudaMemcpyAsync(h->ds, h->hs.data(), sizeof(double) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
+            LB_CUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
+        }
+        LB_CUDA(h, cudaMemsetAsync(h->dFbead, 0, sizeof(double) * 3 * (size_t)std::max(nbeads, 1), h->stream));
+        const size_t fbytes = sizeof(double) * 3 * (size_t)h->g.N;
+        const size_t tbytes = (size_t)h->ntx * h->nty * h->ntz;
+        for (int k = 0; k < 2; ++k) {
+            if ((s = dev_alloc(h, &h->Fbuf[k], fbytes)) != LB_OK) return s;
+            if ((s = dev_alloc(h, &h->tiles[k], tbytes)) != LB_OK) return s;
+            LB_CUDA(h, cudaMemsetAsync(h->Fbuf[k], 0, fbytes, h->stream));
+            LB_CUDA(h, cudaMemsetAsync(h->tiles[k], 0, tbytes, h->stream));
+        }
+    }
+    lb_status s = upload_gforce(h);
+    if (s != LB_OK) return s;
+    h->uploaded = true;
+    return LB_OK;
+}
+
+// refresh the host mirror of the bodies from the device
+lb_status pull_bodies(lb_ctx *h) {
+    if (!h->uploaded || h->hb.empty()) return LB_OK;
+    LB_CUDA(h, cudaMemcpyAsync(h->hb.data(), h->db, sizeof(Body) * h->hb.size(), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status push_bodies(lb_ctx *h) {
+    if (!h->uploaded || h->hb.empty()) return LB_OK;
+    LB_CUDA(h, cudaMemcpyAsync(h->db, h->hb.data(), sizeof(Body) * h->hb.size(), cudaMemcpyHostToDevice, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status check_handle(lb_ctx *h) {
+    if (!h) return fail(nullptr, LB_ERR_ARG, "null handle");
+    return LB_OK;
+}
+
+lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
+    lbk::FluidArgs a{};
+    a.g = h->g;
+    a.f = h->f;
+    a.rho0 = h->p.rho0;
+    a.omega = 1.0 / h->p.tau;
+    a.gs = h->p.gamma_shear;
+    a.gb = h->p.gamma_bulk;
+    a.go = h->p.gamma_odd;
+    a.ge = h->p.gamma_even;
+    for (int k = 0; k < 15; ++k) a.sig[k] = h->sig[k];
+    a.gforce = h->gforce;
+    const bool bodies = !h->hb.empty() && !h->hbody_of.empty();
+    a.Fn = bodies ? h->Fbuf[cur] : nullptr;
+    a.tiles = bodies ? h->tiles[cur] : nullptr;
+    a.ntx = h->ntx;
+    a.nty = h->nty;
+    a.key0 = (uint32_t)h->p.seed;
+    a.key1 = (uint32_t)(h->p.seed >> 32);
+    a.instance = h->p.instance;
+    a.step_base = h->step_dev;
+    a.step_off = step_off;
+    return a;
+}
+
+lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
+    const bool noise = h->p.collision == 1 && h->p.kT > 0.0;
+    if (h->timing) {
+        if (h->ev_used + 2 > h->ev.size()) {
+            if (h->ev.size() >= 8192) {
+                // fold the recorded pairs into the totals to bound the event pool
+                LB_CUDA(h, cudaStreamSynchronize(h->stream));
+                for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+                    float ms = 0.f;
+                    LB_CUDA(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+                    h->timed_ms += ms;
+                    h->timed_n += 1;
+                }
+                h->ev_used = 0;
+            } else {
+                for (int k = 0; k < 256; ++k) {
+                    cudaEvent_t e;
+                    LB_CUDA(h, cudaEventCreate(&e));
+                    h->ev.push_back(e);
+                }
+            }
+        }
+        LB_CUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
+    }
+    cudaError_t e = lbk::launch_collide_stream(a, h->fp32, h->p.collision, noise, odd, h->block, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "collide_stream launch");
+    if (h->timing) {
+        LB_CUDA(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+        h->ev_used += 2;
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lb_status_string(lb_status s) {
+    switch (s) {
+    case LB_OK: return "ok";
+    case LB_ERR_ARG: return "invalid argument";
+    case LB_ERR_OOM: return "out of memory";
+    case LB_ERR_CUDA: return "CUDA error";
+    case LB_ERR_UNSTABLE: return "non-finite mass or momentum";
+    case LB_ERR_TIMEOUT: return "device wait timed out";
+    case LB_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *lb_last_error(lb_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int lb_lattice(int *c, double *w, int *opp) {
+    for (int i = 0; i < 19; ++i) {
+        if (c) { c[3 * i] = lbk::cx(i); c[3 * i + 1] = lbk::cy(i); c[3 * i + 2] = lbk::cz(i); }
+        if (w) w[i] = lbk::wq(i);
+        if (opp) opp[i] = lbk::opp(i);
+    }
+    return 19;
+}
+
+lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
+    if (!p || !out) return fail(nullptr, LB_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (p->nx < 2 || p->ny < 2 || p->nz < 2) return fail(nullptr, LB_ERR_ARG, "lattice sizes must be >= 2");
+    const double N = (double)p->nx * p->ny * p->nz;
+    if (N > 2.0e9) return fail(nullptr, LB_ERR_ARG, "lattice too large (node count must fit 31 bits)");
+    if (p->precision != 32 && p->precision != 64) return fail(nullptr, LB_ERR_ARG, "precision must be 32 or 64");
+    if (p->collision != 0 && p->collision != 1) return fail(nullptr, LB_ERR_ARG, "collision must be 0 (BGK) or 1 (MRT)");
+    if (p->collision == 0 && !(p->tau > 0.5)) return fail(nullptr, LB_ERR_ARG, "BGK needs tau > 1/2");
+    if (p->collision == 1) {
+        const double r[4] = {p->gamma_shear, p->gamma_bulk, p->gamma_odd, p->gamma_even};
+        for (double v : r)
+            if (!(v > -1.0 && v < 1.0)) return fail(nullptr, LB_ERR_ARG, "MRT rates must lie in (-1, 1)");
+    }
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return fail(nullptr, LB_ERR_ARG, "rho0 must be > 0");
+    if (!(p->kT >= 0.0) || !std::isfinite(p->kT)) return fail(nullptr, LB_ERR_ARG, "kT must be >= 0");
+    if (p->kT > 0.0 && p->collision == 0)
+        return fail(nullptr, LB_ERR_ARG, "thermal noise needs MRT collision (BGK has no separate non-conserved modes)");
+    if (!(p->gamma_bead >= 0.0) || !std::isfinite(p->gamma_bead)) return fail(nullptr, LB_ERR_ARG, "gamma_bead must be >= 0");
+    if (p->md_substeps != 1 && p->md_substeps != 0) return fail(nullptr, LB_ERR_ARG, "md_substeps must be 1");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->body_force[a])) return fail(nullptr, LB_ERR_ARG, "body_force must be finite");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, LB_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+
+    lb_ctx *h = new (std::nothrow) lb_ctx();
+    if (!h) return fail(nullptr, LB_ERR_OOM, "host allocation failed");
+    h->p = *p;
+    h->p.md_substeps = 1;
+    h->fp32 = p->precision == 32;
+    h->g.nx = p->nx; h->g.ny = p->ny; h->g.nz = p->nz;
+    h->g.N = (long long)p->nx * p->ny * p->nz;
+    h->g.pore_axis = -1;
+    h->g.pore_t = 0;
+    h->g.pore_in = 0;
+    h->nfluid = h->g.N;
+    h->ntx = (p->nx + 3) / 4; h->nty = (p->ny + 3) / 4; h->ntz = (p->nz + 3) / 4;
+    // noise amplitudes per mode (divided by sqrt(rho)): sqrt(3 kT b_k (1 - g_k^2))
+    if (p->collision == 1 && p->kT > 0.0) {
+        const double b[15] = {2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 2.0 / 3, 2.0 / 3, 2.0 / 3,
+                              2.0 / 9, 2.0 / 9, 2.0 / 9, 2.0, 4.0 / 3, 4.0 / 9};
+        for (int k = 0; k < 15; ++k) {
+            const int mode = k + 4;
+            const double gk = mode == 4 ? p->gamma_bulk : (mode <= 9 ? p->gamma_shear : (mode <= 15 ? p->gamma_odd : p->gamma_even));
+            h->sig[k] = std::sqrt(3.0 * p->kT * b[k] * (1.0 - gk * gk));
+        }
+    }
+    // block shape: x fastest, 128 threads
+    int bx = ((p->nx + 31) / 32) * 32;
+    if (bx > 128) bx = 128;
+    h->block = dim3(bx, 128 / bx, 1);
+
+    if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+    else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { lb_status s = cuda_fail(nullptr, e, "cudaStreamCreate"); delete h; return s; }
+        h->own_stream = true;
+    }
+    const size_t es = h->fp32 ? 4 : 8;
+    lb_status s;
+    if ((s = dev_alloc(h, &h->f, es * 19 * (size_t)h->g.N)) != LB_OK ||
+        (s = dev_alloc(h, &h->gforce, 3 * sizeof(double))) != LB_OK ||
+        (s = dev_alloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK) {
+        g_create_error = h->err;
+        lb_destroy(h);
+        return s;
+    }
+    h->red_blocks = 1024;
+    if ((s = dev_alloc(h, &h->partials, sizeof(double) * 4 * h->red_blocks)) != LB_OK ||
+        (s = dev_alloc(h, &h->out4, sizeof(double) * 4)) != LB_OK) {
+        g_create_error = h->err;
+        lb_destroy(h);
+        return s;
+    }
+    e = cudaMemsetAsync(h->step_dev, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = lbk::launch_init(h->f, h->fp32, h->g.N, p->rho0, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "lb_create init");
+        lb_destroy(h);
+        return LB_ERR_CUDA;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_handle h) {
+    if (!h) return LB_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void *bufs[] = {h->f, h->gforce, h->step_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
+                    h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return LB_OK;
+}
+
+lb_status lb_set_pore(lb_handle h, double radius, int axis) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (h->step > 0 || h->uploaded) return fail(h, LB_ERR_STATE, "lb_set_pore must come before the first lb_step");
+    if (axis < 0 || axis > 2) return fail(h, LB_ERR_ARG, "axis must be 0, 1 or 2");
+    if (!(radius > 0.0) || !std::isfinite(radius)) return fail(h, LB_ERR_ARG, "radius must be > 0");
+    // wall iff d^2 >= R^2 with d the node-centre distance; in doubled
+    // coordinates 4 d^2 is an integer, so the test is 4 d^2 >= ceil(4 R^2)
+    const double t = std::ceil(4.0 * (radius * radius));
+    h->g.pore_axis = axis;
+    h->g.pore_t = (long long)t;
+    const double inner = std::sqrt(t) - 2.0 * std::sqrt(2.0) - 0.01;
+    h->g.pore_in = inner > 0 ? (long long)std::floor(inner * inner) : 0;
+    h->nfluid = count_fluid(h);
+    // populations of new wall nodes are never read; nothing else changes
+    return LB_OK;
+}
+
+lb_status lb_add_raspberry(lb_handle h, const double *beads, int nbeads, const double X[3], const double q[4],
+                           double mass, const double inertia[3], const double F_ext[3], const double T_ext[3],
+                           int fixed, int *body_id) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (h->uploaded) return fail(h, LB_ERR_STATE, "bodies must be added before the first lb_step");
+    if (nbeads < 0 || (nbeads > 0 && !beads) || !X || !q || !inertia)
+        return fail(h, LB_ERR_ARG, "bad raspberry arguments");
+    if (!(mass > 0.0) || !(inertia[0] > 0 && inertia[1] > 0 && inertia[2] > 0))
+        return fail(h, LB_ERR_ARG, "mass and inertia must be positive");
+    const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(qn > 0.0) || !std::isfinite(qn)) return fail(h, LB_ERR_ARG, "quaternion must be non-zero");
+    for (int k = 0; k < 3 * nbeads; ++k)
+        if (!std::isfinite(beads[k])) return fail(h, LB_ERR_ARG, "non-finite bead offset");
+    Body b{};
+    for (int a = 0; a < 3; ++a) {
+        b.X[a] = X[a];
+        b.I[a] = inertia[a];
+        b.F_ext[a] = F_ext ? F_ext[a] : 0.0;
+        b.T_ext[a] = T_ext ? T_ext[a] : 0.0;
+    }
+    for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
+    b.mass = mass;
+    b.fixed = fixed ? 1 : 0;
+    const int id = (int)h->hb.size();
+    h->hb.push_back(b);
+    for (int k = 0; k < 3 * nbeads; ++k) h->hs.push_back(beads[k]);
+    for (int k = 0; k < nbeads; ++k) h->hbody_of.push_back(id);
+    h->bead_start.push_back((int)h->hbody_of.size());
+    if (body_id) *body_id = id;
+    return LB_OK;
+}
+
+lb_status lb_set_body_state(lb_handle h, int id, const double X[3], const double V[3], const double q[4],
+                            const double w[3]) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (id < 0 || id >= (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body id");
+    lb_status s = pull_bodies(h);
+    if (s != LB_OK) return s;
+    Body &b = h->hb[id];
+    for (int a = 0; a < 3; ++a) {
+        if (X) b.X[a] = X[a];
+        if (V) b.V[a] = V[a];
+        if (w) b.w[a] = w[a];
+    }
+    if (q) {
+        const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        if (!(qn > 0.0)) return fail(h, LB_ERR_ARG, "quaternion must be non-zero");
+        for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
+    }
+    return push_bodies(h);
+}
+
+lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, const double *T_ext) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (nbodies < 0 || nbodies > (int)h->hb.size() || (nbodies > 0 && !F_ext))
+        return fail(h, LB_ERR_ARG, "bad external force arguments");
+    for (int b = 0; b < nbodies; ++b)
+        for (int a = 0; a < 3; ++a) {
+            h->hb[b].F_ext[a] = F_ext[3 * b + a];
+            h->hb[b].T_ext[a] = T_ext ? T_ext[3 * b + a] : 0.0;
+        }
+    if (!h->uploaded || nbodies == 0) return LB_OK;
+    // strided copies straight into the device body records
+    LB_CUDA(h, cudaMemcpy2DAsync(&h->db[0].F_ext[0], sizeof(Body), F_ext, 3 * sizeof(double), 3 * sizeof(double),
+                                 nbodies, cudaMemcpyHostToDevice, h->stream));
+    if (T_ext)
+        LB_CUDA(h, cudaMemcpy2DAsync(&h->db[0].T_ext[0], sizeof(Body), T_ext, 3 * sizeof(double), 3 * sizeof(double),
+                                     nbodies, cudaMemcpyHostToDevice, h->stream));
+    else
+        for (int b = 0; b < nbodies; ++b)
+            LB_CUDA(h, cudaMemsetAsync(&h->db[b].T_ext[0], 0, 3 * sizeof(double), h->stream));
+    if (h->p.compensate_force) {
+        static thread_local double g[3];
+        compute_gforce(h, g);
+        LB_CUDA(h, cudaMemcpyAsync(h->gforce, g, sizeof(g), cudaMemcpyHostToDevice, h->stream));
+    }
+    return LB_OK;
+}
+
+lb_status lb_step(lb_handle h, int nsteps) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (nsteps < 0) return fail(h, LB_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return LB_OK;
+    lb_status s = upload_bodies(h);
+    if (s != LB_OK) return s;
+    const int nb = (int)h->hb.size();
+    const int nbeads = (int)h->hbody_of.size();
+    const bool coupled = nb > 0 && nbeads > 0;
+    for (int k = 0; k < nsteps; ++k) {
+        const bool odd = (h->step & 1) != 0;
+        const int cur = (int)(h->step & 1), prev = cur ^ 1;
+        if (nb > 0) {
+            cudaError_t e = lbk::launch_kick_drift(h->db, nb, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "kick_drift launch");
+        }
+        if (coupled) {
+            cudaError_t e = lbk::launch_clear_tiles(h->Fbuf[cur], h->tiles[cur], h->g, h->ntx, h->nty, h->ntz, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "clear_tiles launch");
+            lbk::CoupleArgs c{};
+            c.g = h->g;
+            c.f = h->f;
+            c.fp32 = h->fp32;
+            c.odd = odd;
+            c.rho0 = h->p.rho0;
+            c.gamma = h->p.gamma_bead;
+            c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
+            c.gforce = h->gforce;
+            c.Fprev = h->Fbuf[prev];
+            c.Fcur = h->Fbuf[cur];
+            c.tiles_cur = h->tiles[cur];
+            c.ntx = h->ntx;
+            c.nty = h->nty;
+            c.s = h->ds;
+            c.bead_body = h->dbody_of;
+            c.bodies = h->db;
+            c.F_bead = h->dFbead;
+            c.nbeads = nbeads;
+            c.key0 = (uint32_t)h->p.seed;
+            c.key1 = (uint32_t)(h->p.seed >> 32);
+            c.instance = h->p.instance;
+            c.step_base = h->step_dev;
+            c.step_off = (uint32_t)k;
+            e = lbk::launch_couple(c, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
+        }
+        s = timed_collide(h, fluid_args(h, cur, (uint32_t)k), odd);
+        if (s != LB_OK) return s;
+        if (nb > 0) {
+            cudaError_t e = lbk::launch_kick2(h->db, nb, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
+        }
+        ++h->step;
+    }
+    cudaError_t e = lbk::launch_advance(h->step_dev, (unsigned)nsteps, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "advance launch");
+    return LB_OK;
+}
+
+lb_status lb_forces(lb_handle h, int id, double F[3], double T[3], double *per_bead) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (id < 0 || id >= (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body id");
+    if (!h->uploaded) {
+        for (int a = 0; a < 3; ++a) {
+            if (F) F[a] = 0.0;
+            if (T) T[a] = 0.0;
+        }
+        if (per_bead)
+            std::memset(per_bead, 0, sizeof(double) * 3 * (h->bead_start[id + 1] - h->bead_start[id]));
+        return LB_OK;
+    }
+    if (F) LB_CUDA(h, cudaMemcpyAsync(F, &h->db[id].F_tot[0], 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (T) LB_CUDA(h, cudaMemcpyAsync(T, &h->db[id].T_tot[0], 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    const int b0 = h->bead_start[id], b1 = h->bead_start[id + 1];
+    if (per_bead && b1 > b0)
+        LB_CUDA(h, cudaMemcpyAsync(per_bead, h->dFbead + 3 * (size_t)b0, sizeof(double) * 3 * (b1 - b0),
+                                   cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (nbodies < 0 || nbodies > (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body count");
+    if (nbodies == 0) return LB_OK;
+    if (!h->uploaded) {
+        if (F) std::memset(F, 0, sizeof(double) * 3 * nbodies);
+        if (T) std::memset(T, 0, sizeof(double) * 3 * nbodies);
+        return LB_OK;
+    }
+    if (F) LB_CUDA(h, cudaMemcpy2DAsync(F, 3 * sizeof(double), &h->db[0].F_tot[0], sizeof(Body), 3 * sizeof(double),
+                                        nbodies, cudaMemcpyDeviceToHost, h->stream));
+    if (T) LB_CUDA(h, cudaMemcpy2DAsync(T, 3 * sizeof(double), &h->db[0].T_tot[0], sizeof(Body), 3 * sizeof(double),
+                                        nbodies, cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_body(lb_handle h, int id, double X[3], double V[3], double q[4], double w[3]) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (id < 0 || id >= (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body id");
+    lb_status s = pull_bodies(h);
+    if (s != LB_OK) return s;
+    const Body &b = h->hb[id];
+    for (int a = 0; a < 3; ++a) {
+        if (X) X[a] = b.X[a];
+        if (V) V[a] = b.V[a];
+        if (w) w[a] = b.w[a];
+    }
+    if (q)
+        for (int a = 0; a < 4; ++a) q[a] = b.q[a];
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_handle h, double *host, size_t n) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!host || n != 19 * (size_t)h->g.N) return fail(h, LB_ERR_ARG, "buffer must hold 19*N doubles");
+    double *tmp = nullptr;
+    lb_status s = dev_alloc(h, &tmp, sizeof(double) * n);
+    if (s != LB_OK) return s;
+    h->dev_bytes -= sizeof(double) * n;
+    cudaError_t e = lbk::launch_gather(h->f, h->fp32, h->g, (h->step & 1) != 0, h->p.rho0, tmp, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_get_populations");
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_handle h, const double *host, size_t n) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!host || n != 19 * (size_t)h->g.N) return fail(h, LB_ERR_ARG, "buffer must hold 19*N doubles");
+    double *tmp = nullptr;
+    lb_status s = dev_alloc(h, &tmp, sizeof(double) * n);
+    if (s != LB_OK) return s;
+    h->dev_bytes -= sizeof(double) * n;
+    cudaError_t e = cudaMemcpyAsync(tmp, host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = lbk::launch_scatter(h->f, h->fp32, h->g, (h->step & 1) != 0, h->p.rho0, tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_set_populations");
+    return LB_OK;
+}
+
+lb_status lb_sample_populations(lb_handle h, const long long *nodes, int count, double *out) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (count < 0 || (count > 0 && (!nodes || !out))) return fail(h, LB_ERR_ARG, "bad sample arguments");
+    if (count == 0) return LB_OK;
+    for (int k = 0; k < count; ++k)
+        if (nodes[k] < 0 || nodes[k] >= h->g.N) return fail(h, LB_ERR_ARG, "node index out of range");
+    long long *dn = nullptr;
+    double *dout = nullptr;
+    lb_status s = dev_alloc(h, &dn, sizeof(long long) * count);
+    if (s != LB_OK) return s;
+    h->dev_bytes -= sizeof(long long) * count;
+    s = dev_alloc(h, &dout, sizeof(double) * 19 * count);
+    if (s != LB_OK) { cudaFree(dn); return s; }
+    h->dev_bytes -= sizeof(double) * 19 * count;
+    cudaError_t e = cudaMemcpyAsync(dn, nodes, sizeof(long long) * count, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = lbk::launch_sample(h->f, h->fp32, h->g, (h->step & 1) != 0, h->p.rho0, dn, count, dout, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * 19 * count, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dn);
+    cudaFree(dout);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_sample_populations");
+    return LB_OK;
+}
+
+lb_status lb_get_node_force(lb_handle h, double *host, size_t n) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!host || n != 3 * (size_t)h->g.N) return fail(h, LB_ERR_ARG, "buffer must hold 3*N doubles");
+    if (!h->Fbuf[0] || h->step == 0) {
+        std::memset(host, 0, sizeof(double) * n);
+        return LB_OK;
+    }
+    const int last = (int)((h->step - 1) & 1);
+    LB_CUDA(h, cudaMemcpyAsync(host, h->Fbuf[last], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_conservation(lb_handle h, double *mass, double mom[3]) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    double o[4];
+    cudaError_t e = lbk::launch_moments(h->f, h->fp32, h->g, (h->step & 1) != 0, h->partials, h->red_blocks,
+                                        h->out4, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(o, h->out4, sizeof(o), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_conservation");
+    if (h->fp32) o[0] += h->p.rho0 * (double)h->nfluid;
+    if (mass) *mass = o[0];
+    if (mom)
+        for (int a = 0; a < 3; ++a) mom[a] = o[a + 1];
+    for (double v : o)
+        if (!std::isfinite(v)) return fail(h, LB_ERR_UNSTABLE, "non-finite mass or momentum");
+    return LB_OK;
+}
+
+lb_status lb_info(lb_handle h, lb_info_t *info) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!info) return fail(h, LB_ERR_ARG, "null info");
+    info->nodes = h->g.N;
+    info->fluid_nodes = h->nfluid;
+    info->step = h->step;
+    info->nbodies = (int)h->hb.size();
+    info->nbeads = (int)h->hbody_of.size();
+    info->precision = h->fp32 ? 32 : 64;
+    info->device_bytes = h->dev_bytes;
+    return LB_OK;
+}
+
+lb_status lb_set_timing(lb_handle h, int on) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    h->timing = on != 0;
+    return LB_OK;
+}
+
+lb_status lb_kernel_time(lb_handle h, double *total_ms, long long *launches) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        LB_CUDA(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+        h->timed_ms += ms;
+        h->timed_n += 1;
+    }
+    h->ev_used = 0;
+    if (total_ms) *total_ms = h->timed_ms;
+    if (launches) *launches = h->timed_n;
+    h->timed_ms = 0.0;
+    h->timed_n = 0;
+    return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Device-side building blocks of the LB + raspberry-coupling step (sm_103a).
+//
+// D3Q19 velocity set, Philox4x32-10, node indexing with periodic wrap, the
+// analytic cylindrical-pore wall test and the parity-aware population access
+// of the in-place (AA) streaming pattern.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbk {
+
+// ----------------------------------------------------------------- lattice
+// D3Q19 (Sec. 1.1 "discrete velocity links"): 0 rest; 1-6 axis links
+// +x -x +y -y +z -z; 7-18 face diagonals, each followed by its opposite:
+// (+x+y)(-x-y) (+x-y)(-x+y) (+x+z)(-x-z) (+x-z)(-x+z) (+y+z)(-y-z) (+y-z)(-y+z).
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+// opposite link: odd i pairs with i + 1
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double wq(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Zero-mean unit-variance uniform variate from 32 random bits:
+// sqrt(12) ((x + 1/2) 2^-32 - 1/2).
+__device__ __forceinline__ double unit_uniform_d(uint32_t x) {
+    return 3.4641016151377544 * (((double)x + 0.5) * 2.3283064365386963e-10 - 0.5);
+}
+__device__ __forceinline__ float unit_uniform_f(uint32_t x) {
+    // (x - 2^31 + 1/2) 2^-32 with one integer-to-float conversion
+    return 3.4641016151377544f * (((float)(int32_t)(x ^ 0x80000000u) + 0.5f) * 2.3283064365386963e-10f);
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+    int nx, ny, nz;
+    long long N;        // nodes = stride between population planes
+    int pore_axis;      // -1: periodic box without walls
+    long long pore_t;   // wall iff (2a+1-na)^2 + (2b+1-nb)^2 >= pore_t (a, b: coordinates across the axis)
+    long long pore_in;  // below this the node and all its neighbours are fluid
+};
+
+__device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ long long nidx(const Geom &g, int x, int y, int z) {
+    return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+}
+
+// squared doubled distance from the pore axis of the node centre
+__device__ __forceinline__ long long pore_r2(const Geom &g, int x, int y, int z) {
+    int a, b, na, nb;
+    if (g.pore_axis == 0) { a = y; b = z; na = g.ny; nb = g.nz; }
+    else if (g.pore_axis == 1) { a = x; b = z; na = g.nx; nb = g.nz; }
+    else { a = x; b = y; na = g.nx; nb = g.ny; }
+    const long long da = 2 * a + 1 - na, db = 2 * b + 1 - nb;
+    return da * da + db * db;
+}
+
+__device__ __forceinline__ bool is_wall(const Geom &g, int x, int y, int z) {
+    return g.pore_axis >= 0 && pore_r2(g, x, y, z) >= g.pore_t;
+}
+
+// Pre-collision population i of node (x,y,z) under the AA pattern.
+// Even step count: stored in place, A[i][n]. Odd step count: the neighbour
+// upstream holds it in the opposite slot, A[opp i][n - c_i]; if that
+// neighbour is a wall node the population bounced back into A[i][n].
+template <typename T>
+__device__ __forceinline__ T load_pre(const T *A, const Geom &g, int x, int y, int z, long long n,
+                                      int i, bool odd) {
+    if (!odd || i == 0) return A[(long long)i * g.N + n];
+    const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(y - cy(i), g.ny), zs = wrapm(z - cz(i), g.nz);
+    if (is_wall(g, xs, ys, zs)) return A[(long long)i * g.N + n];
+    return A[(long long)opp(i) * g.N + nidx(g, xs, ys, zs)];
+}
+
+// Store of population i so that the next load_pre returns it (inverse map).
+template <typename T>
+__device__ __forceinline__ void store_pre(T *A, const Geom &g, int x, int y, int z, long long n,
+                                          int i, bool odd, T v) {
+    if (!odd || i == 0) { A[(long long)i * g.N + n] = v; return; }
+    const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(y - cy(i), g.ny), zs = wrapm(z - cz(i), g.nz);
+    if (is_wall(g, xs, ys, zs)) { A[(long long)i * g.N + n] = v; return; }
+    A[(long long)opp(i) * g.N + nidx(g, xs, ys, zs)] = v;
+}
+
+// 4x4x4 tiles flag where bead forces were spread
+__device__ __forceinline__ long long tile_of(int x, int y, int z, int ntx, int nty) {
+    return (long long)(x >> 2) + (long long)ntx * ((long long)(y >> 2) + (long long)nty * (z >> 2));
+}
+
+}  // namespace lbk

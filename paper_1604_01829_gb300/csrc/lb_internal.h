@@ -1,0 +1,85 @@
+// Internal launch interface between the C-ABI runtime (lb_api.cu) and the
+// kernels (lb_fluid.cu, lb_bodies.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+// Everything the fused collide-and-stream kernel reads besides populations.
+struct FluidArgs {
+    Geom g;
+    void *f;                     // populations: double[19][N] (FP64) or float[19][N] deviations
+    double rho0;
+    double omega;                // BGK 1/tau
+    double gs, gb, go, ge;       // MRT rates (shear, bulk, odd ghost, even ghost)
+    double sig[15];              // noise amplitude of modes 4..18 divided by sqrt(rho)
+    const double *gforce;        // device: uniform force density (3)
+    const double *Fn;            // device: spread bead force [3][N] or nullptr
+    const unsigned char *tiles;  // device: 4x4x4 tile flags of Fn or nullptr
+    int ntx, nty;
+    uint32_t key0, key1, instance;
+    const unsigned long long *step_base;  // device step counter of the first step of this launch group
+    uint32_t step_off;
+};
+
+// Rigid bodies (FP64, array of structs; few bodies, one thread each).
+struct Body {
+    double X[3], V[3], q[4], w[3];   // centre, velocity, orientation (w,x,y,z), body-frame omega
+    double F_last[3], T_last[3];     // last step: lab-frame force, body-frame torque
+    double F_ext[3], T_ext[3];       // lab frame
+    double F_tot[3], T_tot[3];       // last step: lab-frame totals (beads + external)
+    double acc[6];                   // bead force / torque accumulators of the running step
+    double R[9];                     // rotation of the running step (row-major, lab = R body)
+    double wl[3];                    // lab-frame omega of the running step
+    double mass, I[3];
+    int fixed, pad;
+};
+
+struct CoupleArgs {
+    Geom g;
+    const void *f;               // populations (pre-collision of this step)
+    bool fp32;                   // deviation storage
+    bool odd;                    // parity of the step count
+    double rho0;
+    double gamma;
+    double noise_amp;            // sqrt(2 kT gamma), 0 = off
+    const double *gforce;        // uniform force density (3)
+    const double *Fprev;         // [3][N] spread force of the previous step
+    double *Fcur;                // [3][N] spread force of this step (zero on entry)
+    unsigned char *tiles_cur;    // flags of Fcur
+    int ntx, nty;
+    const double *s;             // body-frame bead offsets [3*nbeads]
+    const int *bead_body;        // body index of each bead
+    Body *bodies;
+    double *F_bead;              // out: bead forces [3*nbeads]
+    int nbeads;
+    uint32_t key0, key1, instance;
+    const unsigned long long *step_base;
+    uint32_t step_off;
+};
+
+// launchers (return the launch error)
+cudaError_t launch_init(void *f, bool fp32, long long N, double rho0, cudaStream_t s);
+cudaError_t launch_collide_stream(const FluidArgs &a, bool fp32, int collision, bool noise, bool odd,
+                                  dim3 block, cudaStream_t s);
+cudaError_t launch_gather(const void *f, bool fp32, const Geom &g, bool odd, double rho0, double *out,
+                          cudaStream_t s);
+cudaError_t launch_scatter(void *f, bool fp32, const Geom &g, bool odd, double rho0, const double *in,
+                           cudaStream_t s);
+cudaError_t launch_sample(const void *f, bool fp32, const Geom &g, bool odd, double rho0,
+                          const long long *nodes, int count, double *out, cudaStream_t s);
+cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, double *partials,
+                           int nblocks, double *out4, cudaStream_t s);
+cudaError_t launch_advance(unsigned long long *step, unsigned int by, cudaStream_t s);
+
+cudaError_t launch_kick_drift(Body *b, int nbodies, cudaStream_t s);
+cudaError_t launch_clear_tiles(double *F, unsigned char *tiles, const Geom &g, int ntx, int nty, int ntz,
+                               cudaStream_t s);
+cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
+cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s);
+
+}  // namespace lbk

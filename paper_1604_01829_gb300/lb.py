@@ -1,0 +1,270 @@
+"""Python binding of the C ABI in include/lb.h (argument marshalling only).
+
+Every step of the LB + coupling path runs in the CUDA library
+``_lib/liblbrasp.so``; this module only converts numpy arrays to pointers and
+lb_status codes to exceptions. There is no fallback: if the library has not
+been built (``paper_1604_01829_gb300.build.build()``) or no GPU is present,
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbrasp.so")
+
+LB_OK, LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_UNSTABLE, LB_ERR_TIMEOUT, LB_ERR_STATE = range(7)
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_llp = C.POINTER(C.c_longlong)
+
+
+class lb_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("precision", C.c_int), ("collision", C.c_int),
+                ("tau", C.c_double),
+                ("gamma_shear", C.c_double), ("gamma_bulk", C.c_double),
+                ("gamma_odd", C.c_double), ("gamma_even", C.c_double),
+                ("rho0", C.c_double), ("kT", C.c_double), ("gamma_bead", C.c_double),
+                ("seed", C.c_ulonglong), ("instance", C.c_uint),
+                ("body_force", C.c_double * 3),
+                ("compensate_force", C.c_int), ("md_substeps", C.c_int)]
+
+
+class lb_info_t(C.Structure):
+    _fields_ = [("nodes", C.c_longlong), ("fluid_nodes", C.c_longlong), ("step", C.c_longlong),
+                ("nbodies", C.c_int), ("nbeads", C.c_int), ("precision", C.c_int),
+                ("device_bytes", C.c_size_t)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (argtypes)
+_SIGS = {
+    "lb_create": [C.POINTER(lb_params), C.c_void_p, C.POINTER(C.c_void_p)],
+    "lb_destroy": [C.c_void_p],
+    "lb_set_pore": [C.c_void_p, C.c_double, C.c_int],
+    "lb_add_raspberry": [C.c_void_p, _dp, C.c_int, _dp, _dp, C.c_double, _dp, _dp, _dp, C.c_int, _ip],
+    "lb_set_body_state": [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp],
+    "lb_set_external_forces": [C.c_void_p, C.c_int, _dp, _dp],
+    "lb_step": [C.c_void_p, C.c_int],
+    "lb_forces": [C.c_void_p, C.c_int, _dp, _dp, _dp],
+    "lb_forces_all": [C.c_void_p, C.c_int, _dp, _dp],
+    "lb_get_body": [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp],
+    "lb_get_populations": [C.c_void_p, _dp, C.c_size_t],
+    "lb_set_populations": [C.c_void_p, _dp, C.c_size_t],
+    "lb_sample_populations": [C.c_void_p, _llp, C.c_int, _dp],
+    "lb_get_node_force": [C.c_void_p, _dp, C.c_size_t],
+    "lb_conservation": [C.c_void_p, _dp, _dp],
+    "lb_info": [C.c_void_p, C.POINTER(lb_info_t)],
+    "lb_set_timing": [C.c_void_p, C.c_int],
+    "lb_kernel_time": [C.c_void_p, _dp, _llp],
+}
+
+# every symbol include/lb.h declares
+EXPORTS = sorted(list(_SIGS) + ["lb_last_error", "lb_status_string", "lb_lattice"])
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library {LIB_PATH} is missing: build it with "
+                    "paper_1604_01829_gb300.build.build() (nvcc, sm_103a)")
+            L = C.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.lb_last_error.argtypes = [C.c_void_p]
+            L.lb_last_error.restype = C.c_char_p
+            L.lb_status_string.argtypes = [C.c_int]
+            L.lb_status_string.restype = C.c_char_p
+            L.lb_lattice.argtypes = [_ip, _dp, _ip]
+            L.lb_lattice.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(h, status):
+    if status != LB_OK:
+        L = load()
+        msg = L.lb_last_error(h).decode() if L.lb_last_error(h) else ""
+        raise LBError(status, msg or L.lb_status_string(status).decode())
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _vec(v, n):
+    if v is None:
+        return None
+    a = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} values")
+    return a
+
+
+def lb_lattice():
+    c = np.zeros(57, np.int32)
+    w = np.zeros(19)
+    opp = np.zeros(19, np.int32)
+    load().lb_lattice(c.ctypes.data_as(_ip), _d(w), opp.ctypes.data_as(_ip))
+    return c.reshape(19, 3), w, opp
+
+
+def make_params(nx, ny, nz, precision=64, collision=0, tau=1.0, gamma_shear=0.0, gamma_bulk=0.0,
+                gamma_odd=0.0, gamma_even=0.0, rho0=1.0, kT=0.0, gamma_bead=0.0, seed=0,
+                instance=0, body_force=(0.0, 0.0, 0.0), compensate_force=0, md_substeps=1):
+    return lb_params(nx, ny, nz, precision, collision, tau, gamma_shear, gamma_bulk, gamma_odd,
+                     gamma_even, rho0, kT, gamma_bead, seed, instance,
+                     (C.c_double * 3)(*body_force), compensate_force, md_substeps)
+
+
+class LB:
+    """One lattice (handle) of the CUDA library; method names follow lb.h."""
+
+    def __init__(self, nx, ny, nz, stream=None, **kw):
+        L = load()
+        self.p = make_params(nx, ny, nz, **kw)
+        self.N = nx * ny * nz
+        h = C.c_void_p()
+        st = L.lb_create(C.byref(self.p), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != LB_OK:
+            raise LBError(st, L.lb_last_error(None).decode())
+        self.h = h
+        self.bead_counts = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # set-up --------------------------------------------------------------
+    def lb_set_pore(self, radius, axis=2):
+        _check(self.h, load().lb_set_pore(self.h, float(radius), int(axis)))
+
+    def lb_add_raspberry(self, beads, X, q=(1, 0, 0, 0), mass=1.0, inertia=(1, 1, 1),
+                         F_ext=None, T_ext=None, fixed=False):
+        b = np.ascontiguousarray(beads, dtype=np.float64).reshape(-1)
+        bid = C.c_int(-1)
+        _check(self.h, load().lb_add_raspberry(
+            self.h, _d(b), b.size // 3, _d(_vec(X, 3)), _d(_vec(q, 4)), float(mass),
+            _d(_vec(inertia, 3)), _d(_vec(F_ext, 3)), _d(_vec(T_ext, 3)), int(bool(fixed)),
+            C.byref(bid)))
+        self.bead_counts.append(b.size // 3)
+        return bid.value
+
+    def lb_set_body_state(self, body, X=None, V=None, q=None, w=None):
+        _check(self.h, load().lb_set_body_state(self.h, int(body), _d(_vec(X, 3)), _d(_vec(V, 3)),
+                                                _d(_vec(q, 4)), _d(_vec(w, 3))))
+
+    def lb_set_external_forces(self, F_ext, T_ext=None):
+        F = np.ascontiguousarray(F_ext, dtype=np.float64).reshape(-1)
+        T = None if T_ext is None else np.ascontiguousarray(T_ext, dtype=np.float64).reshape(-1)
+        _check(self.h, load().lb_set_external_forces(self.h, F.size // 3, _d(F), _d(T)))
+
+    # stepping ------------------------------------------------------------
+    def lb_step(self, n=1):
+        _check(self.h, load().lb_step(self.h, int(n)))
+
+    # results -------------------------------------------------------------
+    def lb_forces(self, body, per_bead=False):
+        F = np.zeros(3)
+        T = np.zeros(3)
+        pb = np.zeros(3 * self.bead_counts[body]) if per_bead else None
+        _check(self.h, load().lb_forces(self.h, int(body), _d(F), _d(T), _d(pb)))
+        return (F, T, pb.reshape(-1, 3)) if per_bead else (F, T)
+
+    def lb_forces_all(self, F=None, T=None):
+        n = len(self.bead_counts)
+        F = np.zeros(3 * n) if F is None else F
+        T = np.zeros(3 * n) if T is None else T
+        _check(self.h, load().lb_forces_all(self.h, n, _d(F), _d(T)))
+        return F, T
+
+    def lb_get_body(self, body):
+        X, V, q, w = np.zeros(3), np.zeros(3), np.zeros(4), np.zeros(3)
+        _check(self.h, load().lb_get_body(self.h, int(body), _d(X), _d(V), _d(q), _d(w)))
+        return dict(X=X, V=V, q=q, w=w)
+
+    def lb_get_populations(self):
+        out = np.zeros(19 * self.N)
+        _check(self.h, load().lb_get_populations(self.h, _d(out), out.size))
+        return out.reshape(19, self.N)
+
+    def lb_set_populations(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        _check(self.h, load().lb_set_populations(self.h, _d(a), a.size))
+
+    def lb_sample_populations(self, nodes):
+        nd = np.ascontiguousarray(nodes, dtype=np.int64).reshape(-1)
+        out = np.zeros(19 * nd.size)
+        _check(self.h, load().lb_sample_populations(self.h, nd.ctypes.data_as(_llp), nd.size, _d(out)))
+        return out.reshape(-1, 19)
+
+    def lb_get_node_force(self):
+        out = np.zeros(3 * self.N)
+        _check(self.h, load().lb_get_node_force(self.h, _d(out), out.size))
+        return out.reshape(3, self.N)
+
+    def lb_conservation(self):
+        m = C.c_double()
+        p = np.zeros(3)
+        _check(self.h, load().lb_conservation(self.h, C.byref(m), _d(p)))
+        return m.value, p
+
+    def lb_info(self):
+        i = lb_info_t()
+        _check(self.h, load().lb_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in lb_info_t._fields_}
+
+    def lb_set_timing(self, on=True):
+        _check(self.h, load().lb_set_timing(self.h, int(bool(on))))
+
+    def lb_kernel_time(self):
+        ms = C.c_double()
+        n = C.c_longlong()
+        _check(self.h, load().lb_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+
+def from_workload(w, stream=None, precision=None):
+    """Create an LB handle holding a workloads.Workload (pore and bodies)."""
+    kw = dict(w.params)
+    if precision is not None:
+        kw["precision"] = precision
+    lb = LB(w.nx, w.ny, w.nz, stream=stream, **kw)
+    if w.pore is not None:
+        lb.lb_set_pore(*w.pore)
+    for b in w.bodies:
+        lb.lb_add_raspberry(b.beads, b.X, b.q, b.mass, b.inertia, b.F_ext, b.T_ext, b.fixed)
+    return lb

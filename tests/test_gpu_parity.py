@@ -1,0 +1,150 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs, element by element.
+
+Tolerances (written here, derived in the design notes):
+  FP64 populations: |f_gpu - f_oracle| <= 1e-12 w_i rho0 after the stated
+  steps (summation order and FMA contraction differ; atomics reorder the
+  bead-force sums);
+  FP32 storage of f - w_i rho0: <= 2e-5 w_i rho0 (FP32 rounding of
+  deviations of order 1e-2 w_i rho0 over tens of steps).
+Sizes span several 4x4x4 force tiles and several thread blocks with a ragged
+tail in every direction; odd and even step counts exercise both AA parities.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import Pair, W19, perturbed_populations
+from paper_1604_01829_gb300 import workloads as Wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1604_01829_gb300 import build
+    build.build()
+
+
+MRT = dict(collision=1, gamma_shear=-0.45, gamma_bulk=-0.2, gamma_odd=0.3, gamma_even=-0.1)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("case", ["bgk", "mrt", "mrt_noise"])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_periodic_fluid(precision, case, steps):
+    nx, ny, nz = 37, 13, 10
+    params = dict(collision=0, tau=0.8) if case == "bgk" else dict(MRT)
+    if case == "mrt_noise":
+        params.update(kT=1e-4, seed=0xABCDEF0123)
+    params["body_force"] = (1e-5, -2e-5, 3e-6)
+    P = Pair(nx, ny, nz, precision=precision, **params)
+    P.set_populations(perturbed_populations(P.N, seed=3))
+    P.step(steps)
+    assert P.pop_error() <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("axis", [2, 0])
+def test_pore_bounce_back(precision, axis):
+    n_ax, n_cross = 9, 22
+    dims = [n_cross, n_cross, n_cross]
+    dims[axis] = n_ax
+    params = dict(MRT, body_force=tuple(1e-5 if a == axis else 0.0 for a in range(3)))
+    P = Pair(*dims, precision=precision, pore=(8.3, axis), **params)
+    P.set_populations(perturbed_populations(P.N, seed=5))
+    for _ in range(3):
+        P.step(3)
+        assert P.pop_error() <= TOL[precision]
+    mg, _ = P.gpu.lb_conservation()
+    mo, _ = P.orc.conservation()
+    assert abs(mg - mo) <= 1e-11 * mo
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_free_raspberry_periodic(precision):
+    L = 24
+    params = dict(collision=0, tau=0.9, gamma_bead=Wl.paper_gamma_to_lattice(200.0),
+                  compensate_force=1, body_force=(0, 2e-6, 0))
+    P = Pair(L, L, L + 3, precision=precision, **params)
+    P.set_populations(perturbed_populations(P.N, amp=0.005, u_amp=0.005, seed=7))
+    beads = Wl.sphere_raspberry(3.0)
+    q = [0.9, 0.2, -0.3, 0.1]
+    b = P.add_body(beads, [11.3, 12.7, 13.1], q, mass=113.0, inertia=(400, 420, 440),
+                   F_ext=(1e-3, 0, -5e-4), T_ext=(0, 1e-3, 0), V=(1e-3, -2e-3, 5e-4), w=(1e-3, 2e-3, -1e-3))
+    for k in range(4):
+        P.step(3 if k % 2 == 0 else 2)
+        assert P.pop_error() <= TOL[precision]
+        e = P.body_errors(b)
+        tb = 1e-11 if precision == 64 else 2e-5
+        assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb, e
+        assert e["X"] <= tb and e["V"] <= tb * 1e-2 and e["q"] <= tb and e["w"] <= tb * 1e-2, e
+    # spread force field of the last step
+    Fg = P.gpu.lb_get_node_force()
+    Fo = P.orc.Fnode.reshape(3, -1)
+    assert np.abs(Fg - Fo).max() <= (1e-12 if precision == 64 else 2e-5) * np.abs(Fo).max()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_raspberry_in_pore_with_noise(precision):
+    """Thermal MRT fluid, bead noise, a fixed sphere near the pore wall (some
+    corners are wall nodes) and a free ellipsoid."""
+    params = dict(MRT, kT=1e-4, seed=77, gamma_bead=Wl.paper_gamma_to_lattice(50.0))
+    P = Pair(26, 26, 20, precision=precision, pore=(11.0, 2), **params)
+    sph = Wl.sphere_raspberry(2.5)
+    P.add_body(sph, [13 + 7.2, 13.4, 6.0], fixed=True, V=(0, 0, 1e-3))
+    ell = Wl.ellipsoid_raspberry(4.0, 2.0, 2.0, seed=3)
+    P.add_body(ell, [11.5, 12.2, 14.7], [0.8, 0.1, 0.5, -0.2], mass=60.0, inertia=(30, 90, 90),
+               F_ext=(0, 0, 2e-3))
+    for _ in range(3):
+        P.step(3)
+        assert P.pop_error() <= TOL[precision]
+        for b in range(2):
+            e = P.body_errors(b)
+            tb = 1e-11 if precision == 64 else 5e-5
+            assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb, (b, e)
+
+
+def test_conservation_matches_oracle_and_is_exact():
+    params = dict(MRT, kT=1e-4, seed=5)
+    P = Pair(20, 18, 16, precision=64, **params)
+    P.set_populations(perturbed_populations(P.N, seed=9))
+    m0, p0 = P.gpu.lb_conservation()
+    mo, po = P.orc.conservation()
+    assert abs(m0 - mo) <= 1e-12 * mo and np.abs(p0 - po).max() <= 1e-12
+    P.step(11)
+    m1, p1 = P.gpu.lb_conservation()
+    assert abs(m1 - m0) <= 1e-12 * m0
+    assert np.abs(p1 - p0).max() <= 1e-13 * m0
+
+
+def test_sample_populations_matches_full_readback():
+    P = Pair(17, 9, 6, precision=32, **MRT)
+    P.set_populations(perturbed_populations(P.N, seed=2))
+    P.gpu.lb_step(3)
+    full = P.gpu.lb_get_populations()
+    idx = np.array([0, 5, P.N - 1, 123, 456])
+    s = P.gpu.lb_sample_populations(idx)
+    assert np.array_equal(s, full[:, idx].T)
+
+
+def test_errors_are_reported_not_raised_in_the_library():
+    from paper_1604_01829_gb300 import lb
+    with pytest.raises(lb.LBError) as ei:
+        lb.LB(8, 8, 8, collision=0, tau=0.4)
+    assert ei.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError):
+        lb.LB(8, 8, 8, collision=0, tau=1.0, kT=1e-4)
+    g = lb.LB(8, 8, 8)
+    with pytest.raises(lb.LBError) as ei:
+        g.lb_set_pore(3.0, axis=5)
+    assert ei.value.status == lb.LB_ERR_ARG
+    g.lb_step(1)
+    with pytest.raises(lb.LBError) as ei:
+        g.lb_set_pore(3.0, axis=2)
+    assert ei.value.status == lb.LB_ERR_STATE
+    with pytest.raises(lb.LBError):
+        g.lb_sample_populations([8 ** 3])
