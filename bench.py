@@ -131,9 +131,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+ARGS = None
+
+
 def build_workload(precision):
     from paper_1604_01829_gb300 import workloads as W
-    return W.ellipsoids_256(precision=precision)
+    L = ARGS.lattice if ARGS else 256
+    nb = ARGS.bodies if ARGS else 64
+    return W.ellipsoids_256(n_bodies=nb, L=L, precision=precision)
 
 
 def run_ours(args, ws, rank, local):
@@ -205,7 +210,7 @@ def run_ours(args, ws, rank, local):
     Text = np.zeros(3 * nb)
     Fout = np.zeros(3 * nb)
     Tout = np.zeros(3 * nb)
-    e2e_steps = max(10, min(K, 200))
+    e2e_steps = 0 if args.no_e2e else max(10, min(K, 200))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -213,17 +218,23 @@ def run_ours(args, ws, rank, local):
         L.lb_step(1)
         L.lb_forces_all(Fout, Tout)
     t1 = time.perf_counter()
-    e2e_ms = barrier_max((t1 - t0) * 1e3 / e2e_steps)
-    e2e_value = N * ws / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = barrier_max((t1 - t0) * 1e3 / max(e2e_steps, 1))
+    e2e_value = N * ws / (e2e_ms * 1e-3) / 1e6 if e2e_steps else None
     main["L"].close()
     del main["L"]
 
     # FP64 populations on the same workload (the metric compares FP32 and FP64)
-    k64 = max(3, K // 2)
-    fp64 = measure(64, k64, max(3, args.warmup // 2), False)
-    fp64_value = fp64["nodes"] * k64 * ws / (fp64["ms"] * 1e-3) / 1e6
-    fp64_ach = 2 * 19 * 8 * fp64["nodes"] / (fp64["kernel_ms"] * 1e-3) / 1e9
-    fp64["L"].close()
+    fp64_line = None
+    if not args.skip_fp64:
+        k64 = max(3, K // 4)
+        fp64 = measure(64, k64, 3, False)
+        fp64_value = fp64["nodes"] * k64 * ws / (fp64["ms"] * 1e-3) / 1e6
+        fp64_ach = 2 * 19 * 8 * fp64["nodes"] / (fp64["kernel_ms"] * 1e-3) / 1e9
+        fp64["L"].close()
+        fp64_line = {"value": round(fp64_value, 1), "unit": "MLUPS", "steps": k64,
+                     "ms_per_step": round(fp64["ms"] / k64, 4),
+                     "kernel_achieved_gbs": round(fp64_ach, 1),
+                     "frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -243,7 +254,9 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic (seeded ellipsoidal raspberries, Philox thermal noise)",
-            "config": {"workload": WORKLOAD, "lattice": [256, 256, 256], "collision": "MRT",
+            "config": {"workload": WORKLOAD if (args.lattice, args.bodies) == (256, 64)
+                       else f"ellipsoids{args.bodies}_{args.lattice}^3_mrt_kT_fp32",
+                       "lattice": [args.lattice] * 3, "collision": "MRT",
                        "kT": 1e-4, "nu": 0.016, "bodies": main["nbodies"], "beads": main["nbeads"],
                        "storage": "fp32 deviation f - w rho0", "l2": "state 1.27 GB > L2, no flush",
                        "parallelism": f"replicas x{ws}"},
@@ -253,13 +266,10 @@ def run_ours(args, ws, rank, local):
                          "bytes_per_node": bytes_per_node,
                          "kernel_ms": round(main["kernel_ms"], 5),
                          "traffic": traffic},
-            "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "steps": e2e_steps,
+            "e2e": {"value": None if e2e_value is None else round(e2e_value, 1), "unit": "MLUPS", "steps": e2e_steps,
                     "h2d_bytes_per_step": 2 * 3 * 8 * nb, "d2h_bytes_per_step": 2 * 3 * 8 * nb},
-            "gpu_launches": 5 * K + 1,
-            "fp64": {"value": round(fp64_value, 1), "unit": "MLUPS", "steps": k64,
-                     "ms_per_step": round(fp64["ms"] / k64, 4),
-                     "kernel_achieved_gbs": round(fp64_ach, 1),
-                     "frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8},
+            "gpu_launches": 3 * K + 2,
+            "fp64": fp64_line,
             "clocks": main["clocks"],
             "cpu_baseline": cpu,
         }
@@ -331,7 +341,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-population leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    ap.add_argument("--lattice", type=int, default=256, help="cubic lattice edge (profiling cases)")
+    ap.add_argument("--bodies", type=int, default=64, help="number of ellipsoids (profiling cases)")
     args = ap.parse_args()
+    global ARGS
+    ARGS = args
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()

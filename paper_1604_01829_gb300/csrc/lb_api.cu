@@ -21,6 +21,7 @@ struct lb_ctx {
     bool own_stream = false;
     void *f = nullptr;
     double *gforce = nullptr;               // device (3)
+    float *gforce_f = nullptr;              // device (3), FP32 copy
     unsigned long long *step_dev = nullptr; // device step counter
     long long step = 0;                     // host mirror
     long long nfluid = 0;
@@ -51,6 +52,8 @@ struct lb_ctx {
     long long timed_n = 0;
     dim3 block{128, 1, 1};
     size_t dev_bytes = 0;
+    double g_host[3] = {};
+    float gf_host[3] = {};
     std::string err;
 };
 
@@ -86,8 +89,6 @@ lb_status dev_alloc(lb_ctx *h, P **ptr, size_t bytes) {
     return LB_OK;
 }
 
-double nodes_of(const lb_ctx *h) { return (double)h->g.N; }
-
 void compute_gforce(const lb_ctx *h, double g[3]) {
     for (int a = 0; a < 3; ++a) g[a] = h->p.body_force[a];
     if (h->p.compensate_force && h->nfluid > 0)
@@ -96,10 +97,13 @@ void compute_gforce(const lb_ctx *h, double g[3]) {
                 for (int a = 0; a < 3; ++a) g[a] -= b.F_ext[a] / (double)h->nfluid;
 }
 
-lb_status upload_gforce(lb_ctx *h) {
-    static thread_local double g[3];
-    compute_gforce(h, g);
-    LB_CUDA(h, cudaMemcpyAsync(h->gforce, g, sizeof(g), cudaMemcpyHostToDevice, h->stream));
+// The uniform force density in FP64 and FP32, staged in host memory that
+// stays valid until the asynchronous copy has run.
+lb_status push_gforce(lb_ctx *h) {
+    compute_gforce(h, h->g_host);
+    for (int a = 0; a < 3; ++a) h->gf_host[a] = (float)h->g_host[a];
+    LB_CUDA(h, cudaMemcpyAsync(h->gforce, h->g_host, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    LB_CUDA(h, cudaMemcpyAsync(h->gforce_f, h->gf_host, 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
@@ -144,7 +148,7 @@ lb_status upload_bodies(lb_ctx *h) {
             LB_CUDA(h, cudaMemsetAsync(h->tiles[k], 0, tbytes, h->stream));
         }
     }
-    lb_status s = upload_gforce(h);
+    lb_status s = push_gforce(h);
     if (s != LB_OK) return s;
     h->uploaded = true;
     return LB_OK;
@@ -174,14 +178,22 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
     lbk::FluidArgs a{};
     a.g = h->g;
     a.f = h->f;
-    a.rho0 = h->p.rho0;
-    a.omega = 1.0 / h->p.tau;
-    a.gs = h->p.gamma_shear;
-    a.gb = h->p.gamma_bulk;
-    a.go = h->p.gamma_odd;
-    a.ge = h->p.gamma_even;
-    for (int k = 0; k < 15; ++k) a.sig[k] = h->sig[k];
+    a.pd.rho0 = h->p.rho0;
+    a.pd.omega = 1.0 / h->p.tau;
+    a.pd.gs = h->p.gamma_shear;
+    a.pd.gb = h->p.gamma_bulk;
+    a.pd.go = h->p.gamma_odd;
+    a.pd.ge = h->p.gamma_even;
+    for (int k = 0; k < 15; ++k) a.pd.sig[k] = h->sig[k];
+    a.pf.rho0 = (float)a.pd.rho0;
+    a.pf.omega = (float)a.pd.omega;
+    a.pf.gs = (float)a.pd.gs;
+    a.pf.gb = (float)a.pd.gb;
+    a.pf.go = (float)a.pd.go;
+    a.pf.ge = (float)a.pd.ge;
+    for (int k = 0; k < 15; ++k) a.pf.sig[k] = (float)a.pd.sig[k];
     a.gforce = h->gforce;
+    a.gforce_f = h->gforce_f;
     const bool bodies = !h->hb.empty() && !h->hbody_of.empty();
     a.Fn = bodies ? h->Fbuf[cur] : nullptr;
     a.tiles = bodies ? h->tiles[cur] : nullptr;
@@ -323,6 +335,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
     lb_status s;
     if ((s = dev_alloc(h, &h->f, es * 19 * (size_t)h->g.N)) != LB_OK ||
         (s = dev_alloc(h, &h->gforce, 3 * sizeof(double))) != LB_OK ||
+        (s = dev_alloc(h, &h->gforce_f, 3 * sizeof(float))) != LB_OK ||
         (s = dev_alloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK) {
         g_create_error = h->err;
         lb_destroy(h);
@@ -350,7 +363,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
 lb_status lb_destroy(lb_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void *bufs[] = {h->f, h->gforce, h->step_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
+    void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -448,11 +461,7 @@ lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, 
     else
         for (int b = 0; b < nbodies; ++b)
             LB_CUDA(h, cudaMemsetAsync(&h->db[b].T_ext[0], 0, 3 * sizeof(double), h->stream));
-    if (h->p.compensate_force) {
-        static thread_local double g[3];
-        compute_gforce(h, g);
-        LB_CUDA(h, cudaMemcpyAsync(h->gforce, g, sizeof(g), cudaMemcpyHostToDevice, h->stream));
-    }
+    if (h->p.compensate_force) return push_gforce(h);
     return LB_OK;
 }
 
@@ -469,12 +478,14 @@ lb_status lb_step(lb_handle h, int nsteps) {
         const bool odd = (h->step & 1) != 0;
         const int cur = (int)(h->step & 1), prev = cur ^ 1;
         if (nb > 0) {
-            cudaError_t e = lbk::launch_kick_drift(h->db, nb, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "kick_drift launch");
+            // previous step's second half kick (k > 0), this step's kick and
+            // drift, and the clearing of this step's spread-force tiles
+            cudaError_t e = lbk::launch_step_pre(h->db, nb, k > 0, coupled ? h->Fbuf[cur] : nullptr,
+                                                 coupled ? h->tiles[cur] : nullptr, h->g,
+                                                 coupled ? h->ntx : 0, h->nty, h->ntz, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
         }
         if (coupled) {
-            cudaError_t e = lbk::launch_clear_tiles(h->Fbuf[cur], h->tiles[cur], h->g, h->ntx, h->nty, h->ntz, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "clear_tiles launch");
             lbk::CoupleArgs c{};
             c.g = h->g;
             c.f = h->f;
@@ -499,16 +510,16 @@ lb_status lb_step(lb_handle h, int nsteps) {
             c.instance = h->p.instance;
             c.step_base = h->step_dev;
             c.step_off = (uint32_t)k;
-            e = lbk::launch_couple(c, h->stream);
+            cudaError_t e = lbk::launch_couple(c, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
         }
         s = timed_collide(h, fluid_args(h, cur, (uint32_t)k), odd);
         if (s != LB_OK) return s;
-        if (nb > 0) {
-            cudaError_t e = lbk::launch_kick2(h->db, nb, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
-        }
         ++h->step;
+    }
+    if (nb > 0) {
+        cudaError_t e = lbk::launch_kick2(h->db, nb, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
     }
     cudaError_t e = lbk::launch_advance(h->step_dev, (unsigned)nsteps, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "advance launch");

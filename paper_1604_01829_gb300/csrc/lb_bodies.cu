@@ -48,12 +48,27 @@ __device__ __forceinline__ void euler_half_implicit(double w[3], const double I[
     }
 }
 
+// Totals of a finished step, then its second half kick: V += F/(2M),
+// implicit Euler half kick of the body-frame omega.
+__device__ void kick2(Body &B) {
+    double Tb[3];
+    for (int a = 0; a < 3; ++a) {
+        B.F_tot[a] = B.acc[a] + B.F_ext[a];
+        B.T_tot[a] = B.acc[3 + a] + B.T_ext[a];
+    }
+    for (int a = 0; a < 3; ++a) Tb[a] = B.R[a] * B.T_tot[0] + B.R[3 + a] * B.T_tot[1] + B.R[6 + a] * B.T_tot[2];
+    for (int a = 0; a < 3; ++a) {
+        B.F_last[a] = B.F_tot[a];
+        B.T_last[a] = Tb[a];
+    }
+    if (B.fixed) return;
+    for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * B.F_tot[a] / B.mass;
+    euler_half_implicit(B.w, B.I, Tb);
+}
+
 // First half kick with last step's force and torque, then drift: X += V,
 // q <- q (x) exp(omega/2) with the half-step body-frame omega.
-__global__ void k_kick_drift(Body *bodies, int nb) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    Body &B = bodies[b];
+__device__ void kick_drift(Body &B) {
     if (!B.fixed) {
         for (int a = 0; a < 3; ++a) {
             B.V[a] += 0.5 * B.F_last[a] / B.mass;
@@ -80,9 +95,18 @@ __global__ void k_kick_drift(Body *bodies, int nb) {
     for (int a = 0; a < 6; ++a) B.acc[a] = 0.0;
 }
 
-// Zero the spread-force entries of every flagged 4x4x4 tile and clear the flag.
-__global__ void k_clear_tiles(double *F, unsigned char *tiles, Geom g, int ntx, int nty, int ntz) {
+// Step prologue in one launch: threads [0, nb) finish the previous step's
+// bodies (second half kick) if asked and start this step's (half kick,
+// drift, rotation); every thread also clears one flagged 4x4x4 tile of this
+// step's spread-force buffer.
+__global__ void k_step_pre(Body *bodies, int nb, int finish_prev, double *F, unsigned char *tiles, Geom g,
+                           int ntx, int nty, int ntz) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < nb) {
+        Body &B = bodies[t];
+        if (finish_prev) kick2(B);
+        kick_drift(B);
+    }
     const long long nt = (long long)ntx * nty * ntz;
     if (t >= nt || !tiles[t]) return;
     const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
@@ -105,13 +129,14 @@ __global__ void k_clear_tiles(double *F, unsigned char *tiles, Geom g, int ntx, 
     tiles[t] = 0;
 }
 
-template <typename T>
+// Pre-collision density and momentum of one node in the compute precision R.
+template <typename R, typename T>
 __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int y, int z, long long n,
-                                           bool odd, double rho0, double &rho, double j[3]) {
-    double s = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+                                           bool odd, R rho0, R &rho, R j[3]) {
+    R s = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const double v = (double)load_pre(A, g, x, y, z, n, i, odd);
+        const R v = (R)load_pre(A, g, x, y, z, n, i, odd);
         s += v;
         if (cx(i)) jx += cx(i) * v;
         if (cy(i)) jy += cy(i) * v;
@@ -121,130 +146,131 @@ __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int
     j[0] = jx; j[1] = jy; j[2] = jz;
 }
 
-// One thread per bead.
+// Eight lanes per bead, one per surrounding node: lane 0 of the group forms
+// the virtual site, every lane interpolates its node's velocity and spreads
+// its share of -F_b, the group reduces by shuffles. Node arithmetic runs in
+// the storage precision (FP32 deviations or FP64), bead and body sums in FP64.
 template <typename T>
 __global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.nbeads) return;
+    using R = T;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = t >> 3;
+    const int c = t & 7;
+    const int lane = threadIdx.x & 31;
+    const bool active = k < a.nbeads;
     const Geom &g = a.g;
     const T *A = static_cast<const T *>(a.f);
-    Body &B = a.bodies[a.bead_body[k]];
-    const double s[3] = {a.s[3 * k], a.s[3 * k + 1], a.s[3 * k + 2]};
-    double rel[3], r[3], v[3], wxr[3];
-    for (int c = 0; c < 3; ++c) rel[c] = B.R[3 * c] * s[0] + B.R[3 * c + 1] * s[1] + B.R[3 * c + 2] * s[2];
-    for (int c = 0; c < 3; ++c) r[c] = B.X[c] + rel[c];
-    cross3(B.wl, rel, wxr);
-    for (int c = 0; c < 3; ++c) v[c] = B.V[c] + wxr[c];
+    const int body = active ? a.bead_body[k] : -1;
 
-    // 8 surrounding nodes (centres at integer + 1/2), periodic
-    int base[3];
-    double fr[3];
-    for (int c = 0; c < 3; ++c) {
-        const double t = r[c] - 0.5;
-        const double fl = floor(t);
-        base[c] = (int)fl;
-        fr[c] = t - fl;
+    double rel[3] = {0, 0, 0}, r[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    if (active && c == 0) {
+        const Body &B = a.bodies[body];
+        const double s[3] = {a.s[3 * k], a.s[3 * k + 1], a.s[3 * k + 2]};
+        double wxr[3];
+        for (int q = 0; q < 3; ++q) rel[q] = B.R[3 * q] * s[0] + B.R[3 * q + 1] * s[1] + B.R[3 * q + 2] * s[2];
+        for (int q = 0; q < 3; ++q) r[q] = B.X[q] + rel[q];
+        cross3(B.wl, rel, wxr);
+        for (int q = 0; q < 3; ++q) v[q] = B.V[q] + wxr[q];
     }
+    for (int q = 0; q < 3; ++q) r[q] = __shfl_sync(0xffffffffu, r[q], 0, 8);
+
+    // this lane's node among the 8 around r (centres at integer + 1/2), periodic
+    const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
     const int n3[3] = {g.nx, g.ny, g.nz};
-    int cc[3][2];
-    for (int c = 0; c < 3; ++c) {
-        int b0 = base[c] % n3[c];
-        if (b0 < 0) b0 += n3[c];
-        cc[c][0] = b0;
-        cc[c][1] = b0 + 1 == n3[c] ? 0 : b0 + 1;
+    int xyz[3];
+    double wt = 1.0;
+    for (int q = 0; q < 3; ++q) {
+        const double tq = r[q] - 0.5;
+        const double fl = floor(tq);
+        const double fr = tq - fl;
+        int b0 = (int)fl % n3[q];
+        if (b0 < 0) b0 += n3[q];
+        xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
+        wt *= o[q] ? fr : 1.0 - fr;
     }
-    const double gx = a.gforce[0], gy = a.gforce[1], gz = a.gforce[2];
+    const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
+    const bool fluid = active && !is_wall(g, xyz[0], xyz[1], xyz[2]);
     double ub[3] = {0.0, 0.0, 0.0};
-    double wgt[8];
-    long long nn[8];
-    bool fl8[8];
-#pragma unroll
-    for (int ci = 0; ci < 8; ++ci) {
-        const int ox = ci & 1, oy = (ci >> 1) & 1, oz = (ci >> 2) & 1;
-        const double wt = (ox ? fr[0] : 1.0 - fr[0]) * (oy ? fr[1] : 1.0 - fr[1]) * (oz ? fr[2] : 1.0 - fr[2]);
-        const int x = cc[0][ox], y = cc[1][oy], z = cc[2][oz];
-        const long long n = nidx(g, x, y, z);
-        wgt[ci] = wt;
-        nn[ci] = n;
-        fl8[ci] = !is_wall(g, x, y, z);
-        if (!fl8[ci]) continue;             // wall nodes carry u = 0
-        double rho, j[3];
-        node_rho_j(A, g, x, y, z, n, a.odd, a.rho0, rho, j);
-        ub[0] += wt * (j[0] + 0.5 * (gx + a.Fprev[n])) / rho;
-        ub[1] += wt * (j[1] + 0.5 * (gy + a.Fprev[g.N + n])) / rho;
-        ub[2] += wt * (j[2] + 0.5 * (gz + a.Fprev[2 * g.N + n])) / rho;
+    if (fluid) {                         // wall nodes carry u = 0
+        R rho, j[3];
+        node_rho_j<R>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (R)a.rho0, rho, j);
+        const R ir = R(1) / rho;
+        const R ux = (j[0] + R(0.5) * (R)(a.gforce[0] + a.Fprev[n])) * ir;
+        const R uy = (j[1] + R(0.5) * (R)(a.gforce[1] + a.Fprev[g.N + n])) * ir;
+        const R uz = (j[2] + R(0.5) * (R)(a.gforce[2] + a.Fprev[2 * g.N + n])) * ir;
+        ub[0] = wt * (double)ux;
+        ub[1] = wt * (double)uy;
+        ub[2] = wt * (double)uz;
     }
-    double fs[3] = {0.0, 0.0, 0.0};
-    if (a.noise_amp > 0.0) {
-        const uint32_t step = (uint32_t)(*a.step_base) + a.step_off;
-        const uint4 rr = philox4x32_10(make_uint4((uint32_t)k, step, a.instance, 4u), make_uint2(a.key0, a.key1));
-        fs[0] = a.noise_amp * unit_uniform_d(rr.x);
-        fs[1] = a.noise_amp * unit_uniform_d(rr.y);
-        fs[2] = a.noise_amp * unit_uniform_d(rr.z);
+    for (int off = 1; off < 8; off <<= 1)
+        for (int q = 0; q < 3; ++q) ub[q] += __shfl_xor_sync(0xffffffffu, ub[q], off, 8);
+
+    // Eq. (latticeboltzmannfriction): F_b = -gamma (v - u(r)) + f_s
+    double Fb[3] = {0.0, 0.0, 0.0};
+    if (active && c == 0) {
+        double fs[3] = {0.0, 0.0, 0.0};
+        if (a.noise_amp > 0.0) {
+            const uint32_t step = (uint32_t)(*a.step_base) + a.step_off;
+            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k, step, a.instance, 4u), make_uint2(a.key0, a.key1));
+            fs[0] = a.noise_amp * unit_uniform_d(rr.x);
+            fs[1] = a.noise_amp * unit_uniform_d(rr.y);
+            fs[2] = a.noise_amp * unit_uniform_d(rr.z);
+        }
+        for (int q = 0; q < 3; ++q) Fb[q] = -a.gamma * (v[q] - ub[q]) + fs[q];
+        for (int q = 0; q < 3; ++q) a.F_bead[3 * k + q] = Fb[q];
     }
-    double Fb[3];
-    for (int c = 0; c < 3; ++c) Fb[c] = -a.gamma * (v[c] - ub[c]) + fs[c];
-    // spread -F_b with the interpolation weights; wall corners take nothing
-#pragma unroll
-    for (int ci = 0; ci < 8; ++ci) {
-        if (!fl8[ci]) continue;
-        const long long n = nn[ci];
-        atomicAdd(&a.Fcur[n], -wgt[ci] * Fb[0]);
-        atomicAdd(&a.Fcur[g.N + n], -wgt[ci] * Fb[1]);
-        atomicAdd(&a.Fcur[2 * g.N + n], -wgt[ci] * Fb[2]);
-        int x, y, z;
-        x = (int)(n % g.nx);
-        y = (int)((n / g.nx) % g.ny);
-        z = (int)(n / ((long long)g.nx * g.ny));
-        a.tiles_cur[tile_of(x, y, z, a.ntx, a.nty)] = 1;
+    for (int q = 0; q < 3; ++q) Fb[q] = __shfl_sync(0xffffffffu, Fb[q], 0, 8);
+
+    // spread -w F_b onto this lane's node; a wall node takes nothing
+    if (fluid) {
+        atomicAdd(&a.Fcur[n], -wt * Fb[0]);
+        atomicAdd(&a.Fcur[g.N + n], -wt * Fb[1]);
+        atomicAdd(&a.Fcur[2 * g.N + n], -wt * Fb[2]);
+        a.tiles_cur[tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty)] = 1;
     }
-    for (int c = 0; c < 3; ++c) a.F_bead[3 * k + c] = Fb[c];
-    double tq[3];
-    cross3(rel, Fb, tq);
-    for (int c = 0; c < 3; ++c) {
-        atomicAdd(&B.acc[c], Fb[c]);
-        atomicAdd(&B.acc[3 + c], tq[c]);
+
+    // force and torque on the body: sum the (up to 4) beads of this warp
+    // that belong to the warp's first body, atomics for the others
+    double FT[6] = {0, 0, 0, 0, 0, 0};
+    if (active && c == 0) {
+        double tq[3];
+        cross3(rel, Fb, tq);
+        for (int q = 0; q < 3; ++q) { FT[q] = Fb[q]; FT[3 + q] = tq[q]; }
     }
+    const int b_first = __shfl_sync(0xffffffffu, body, 0);
+    const bool lead = active && c == 0;
+    const bool same = lead && body == b_first;
+    double red[6];
+    for (int q = 0; q < 6; ++q) red[q] = same ? FT[q] : 0.0;
+    for (int q = 0; q < 6; ++q) {
+        red[q] += __shfl_xor_sync(0xffffffffu, red[q], 8);
+        red[q] += __shfl_xor_sync(0xffffffffu, red[q], 16);
+    }
+    if (lane == 0 && b_first >= 0)
+        for (int q = 0; q < 6; ++q) atomicAdd(&a.bodies[b_first].acc[q], red[q]);
+    if (lead && !same)
+        for (int q = 0; q < 6; ++q) atomicAdd(&a.bodies[body].acc[q], FT[q]);
 }
 
-// Totals, then the second half kick: V += F/(2M), implicit Euler half kick of w.
 __global__ void k_kick2(Body *bodies, int nb) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    Body &B = bodies[b];
-    double Tb[3];
-    for (int a = 0; a < 3; ++a) {
-        B.F_tot[a] = B.acc[a] + B.F_ext[a];
-        B.T_tot[a] = B.acc[3 + a] + B.T_ext[a];
-    }
-    for (int a = 0; a < 3; ++a) Tb[a] = B.R[a] * B.T_tot[0] + B.R[3 + a] * B.T_tot[1] + B.R[6 + a] * B.T_tot[2];
-    for (int a = 0; a < 3; ++a) {
-        B.F_last[a] = B.F_tot[a];
-        B.T_last[a] = Tb[a];
-    }
-    if (B.fixed) return;
-    for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * B.F_tot[a] / B.mass;
-    euler_half_implicit(B.w, B.I, Tb);
+    if (b < nb) kick2(bodies[b]);
 }
 
 }  // namespace
 
-cudaError_t launch_kick_drift(Body *b, int nbodies, cudaStream_t s) {
-    if (nbodies <= 0) return cudaSuccess;
-    k_kick_drift<<<(nbodies + 63) / 64, 64, 0, s>>>(b, nbodies);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_clear_tiles(double *F, unsigned char *tiles, const Geom &g, int ntx, int nty, int ntz,
-                               cudaStream_t s) {
+cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, double *F, unsigned char *tiles,
+                            const Geom &g, int ntx, int nty, int ntz, cudaStream_t s) {
     const long long nt = (long long)ntx * nty * ntz;
-    k_clear_tiles<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(F, tiles, g, ntx, nty, ntz);
+    const long long n = nt > nbodies ? nt : nbodies;
+    k_step_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, F, tiles, g, ntx,
+                                                           nty, ntz);
     return cudaGetLastError();
 }
 
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s) {
     if (a.nbeads <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((a.nbeads + 127) / 128);
+    const unsigned grid = (unsigned)((8LL * a.nbeads + 127) / 128);
     if (a.fp32) k_couple<float><<<grid, 128, 0, s>>>(a);
     else k_couple<double><<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();

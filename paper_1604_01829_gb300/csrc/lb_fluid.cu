@@ -24,9 +24,6 @@ namespace lbk {
 
 namespace {
 
-template <typename R>
-struct Pops { R v[19]; };
-
 // ---------------------------------------------------------------- collision
 // Post-collision populations of one node, in place. Force F = uniform + spread
 // bead force; u = (j + F/2) / rho (Guo forcing); MRT in the orthogonal
@@ -34,8 +31,8 @@ struct Pops { R v[19]; };
 // (3c^2-5)c, (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz, 3c^4-6c^2+1,
 // (2c^2-3)(3cx^2-c^2), (2c^2-3)(cy^2-cz^2), with norms b_k = sum w e_k^2.
 template <typename R, bool DEV, int COLL, bool NOISE>
-__device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const FluidArgs &a, uint32_t node,
-                                        uint32_t step) {
+__device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const CollParams<R> &a,
+                                        const FluidArgs &fa, uint32_t node, uint32_t step) {
     const R s1 = f[1] + f[2], d1 = f[1] - f[2];
     const R s3 = f[3] + f[4], d3 = f[3] - f[4];
     const R s5 = f[5] + f[6], d5 = f[5] - f[6];
@@ -49,11 +46,12 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Flui
     const R Sxy = s7 + s9, Sxz = s11 + s13, Syz = s15 + s17;
     const R Sd = Sxy + Sxz + Syz;
     const R m0 = f[0] + Sax + Sd;                      // rho, or rho - rho0 for deviations
-    const R rho = DEV ? (R)a.rho0 + m0 : m0;
+    const R rho = DEV ? a.rho0 + m0 : m0;
     const R jx = d1 + d7 + d9 + d11 + d13;
     const R jy = d3 + d7 - d9 + d15 + d17;
     const R jz = d5 + d11 - d13 + d15 - d17;
-    const R ir = R(1) / rho;
+    R ir;
+    if constexpr (sizeof(R) == 4) ir = __frcp_rn(rho); else ir = R(1) / rho;
     const R ux = (jx + R(0.5) * Fx) * ir;
     const R uy = (jy + R(0.5) * Fy) * ir;
     const R uz = (jz + R(0.5) * Fz) * ir;
@@ -63,7 +61,7 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Flui
 
     if (COLL == 0) {
         // BGK: f* = f - (f - f_eq)/tau + (1 - 1/(2 tau)) w [3(c-u) + 9 (c.u) c].F
-        const R om = (R)a.omega, h = R(1) - R(0.5) * om;
+        const R om = a.omega, h = R(1) - R(0.5) * om;
         const R base = DEV ? m0 : rho;                 // w rho (or w (rho - rho0)) coefficient of '1'
         const R k2 = R(1.5) * uu;
         // rest population
@@ -104,7 +102,7 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Flui
     R m18 = -(s3 - s5) + Sxy - Sxz;
 
     // equilibrium stress moments and Guo source moments
-    const R gb = (R)a.gb, gs = (R)a.gs, go = (R)a.go, ge = (R)a.ge;
+    const R gb = a.gb, gs = a.gs, go = a.go, ge = a.ge;
     const R hb = R(0.5) * (R(1) + gb), hs = R(0.5) * (R(1) + gs);
     {
         const R e4 = rho * uu;
@@ -123,30 +121,30 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Flui
 
     if (NOISE) {
         // 15 non-conserved modes, variance 3 rho kT b_k (1 - g_k^2)
-        const uint2 key = make_uint2(a.key0, a.key1);
-        const uint4 r0 = philox4x32_10(make_uint4(node, step, a.instance, 0u), key);
-        const uint4 r1 = philox4x32_10(make_uint4(node, step, a.instance, 1u), key);
-        const uint4 r2 = philox4x32_10(make_uint4(node, step, a.instance, 2u), key);
-        const uint4 r3 = philox4x32_10(make_uint4(node, step, a.instance, 3u), key);
+        const uint2 key = make_uint2(fa.key0, fa.key1);
+        const uint4 r0 = philox4x32_10(make_uint4(node, step, fa.instance, 0u), key);
+        const uint4 r1 = philox4x32_10(make_uint4(node, step, fa.instance, 1u), key);
+        const uint4 r2 = philox4x32_10(make_uint4(node, step, fa.instance, 2u), key);
+        const uint4 r3 = philox4x32_10(make_uint4(node, step, fa.instance, 3u), key);
         const R sr = sqrt(rho);
         auto xi = [](uint32_t v) -> R {
             if constexpr (sizeof(R) == 8) return unit_uniform_d(v); else return unit_uniform_f(v);
         };
-        m4 += sr * (R)a.sig[0] * xi(r0.x);
-        m5 += sr * (R)a.sig[1] * xi(r0.y);
-        m6 += sr * (R)a.sig[2] * xi(r0.z);
-        m7 += sr * (R)a.sig[3] * xi(r0.w);
-        m8 += sr * (R)a.sig[4] * xi(r1.x);
-        m9 += sr * (R)a.sig[5] * xi(r1.y);
-        m10 += sr * (R)a.sig[6] * xi(r1.z);
-        m11 += sr * (R)a.sig[7] * xi(r1.w);
-        m12 += sr * (R)a.sig[8] * xi(r2.x);
-        m13 += sr * (R)a.sig[9] * xi(r2.y);
-        m14 += sr * (R)a.sig[10] * xi(r2.z);
-        m15 += sr * (R)a.sig[11] * xi(r2.w);
-        m16 += sr * (R)a.sig[12] * xi(r3.x);
-        m17 += sr * (R)a.sig[13] * xi(r3.y);
-        m18 += sr * (R)a.sig[14] * xi(r3.z);
+        m4 += sr * a.sig[0] * xi(r0.x);
+        m5 += sr * a.sig[1] * xi(r0.y);
+        m6 += sr * a.sig[2] * xi(r0.z);
+        m7 += sr * a.sig[3] * xi(r0.w);
+        m8 += sr * a.sig[4] * xi(r1.x);
+        m9 += sr * a.sig[5] * xi(r1.y);
+        m10 += sr * a.sig[6] * xi(r1.z);
+        m11 += sr * a.sig[7] * xi(r1.w);
+        m12 += sr * a.sig[8] * xi(r2.x);
+        m13 += sr * a.sig[9] * xi(r2.y);
+        m14 += sr * a.sig[10] * xi(r2.z);
+        m15 += sr * a.sig[11] * xi(r2.w);
+        m16 += sr * a.sig[12] * xi(r3.x);
+        m17 += sr * a.sig[13] * xi(r3.y);
+        m18 += sr * a.sig[14] * xi(r3.z);
     }
 
     // back to populations: f*_i = w_i sum_k e_k(c_i) m*_k / b_k
@@ -210,7 +208,7 @@ __global__ void __launch_bounds__(128) k_collide_stream(const FluidArgs a) {
     if (x >= g.nx || y >= g.ny) return;
     T *A = static_cast<T *>(a.f);
     const long long N = g.N;
-    const long long n = nidx(g, x, y, z);
+    const unsigned n = (unsigned)x + (unsigned)g.nx * ((unsigned)y + (unsigned)g.ny * (unsigned)z);
 
     bool near_wall = false;
     if (PORE) {
@@ -219,31 +217,38 @@ __global__ void __launch_bounds__(128) k_collide_stream(const FluidArgs a) {
         near_wall = r2 >= g.pore_in;         // some neighbour may be a wall node
     }
 
-    // neighbour coordinates with periodic wrap
-    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-    auto X = [&](int d) { return d < 0 ? xm : (d > 0 ? xp : x); };
-    auto Y = [&](int d) { return d < 0 ? ym : (d > 0 ? yp : y); };
-    auto Z = [&](int d) { return d < 0 ? zm : (d > 0 ? zp : z); };
+    // neighbour offsets with periodic wrap: node = xo[dx] + yo[dy] + zo[dz]
+    // (32-bit; the node count is limited to 2^31 at creation)
+    const int nxy = g.nx * g.ny;
+    const int xo[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
+    const int yo[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.nx, y * g.nx, (y == g.ny - 1 ? 0 : y + 1) * g.nx};
+    const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * nxy, z * nxy, (z == g.nz - 1 ? 0 : z + 1) * nxy};
+    const unsigned N32 = (unsigned)N;
+    auto plane = [&](int i) { return A + (size_t)i * N32; };
 
     R f[19];
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = A[(long long)i * N + n];
+        for (int i = 0; i < 19; ++i) f[i] = plane(i)[n];
     } else {
         f[0] = A[n];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const int xs = X(-cx(i)), ys = Y(-cy(i)), zs = Z(-cz(i));
-            if (PORE && near_wall && pore_r2(g, xs, ys, zs) >= g.pore_t)
-                f[i] = A[(long long)i * N + n];
-            else
-                f[i] = A[(long long)opp(i) * N + nidx(g, xs, ys, zs)];
+            const unsigned src = (unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]);
+            if (PORE && near_wall) {
+                int xs = xo[1 - cx(i)], ys = (y - cy(i) + g.ny) % g.ny, zs = (z - cz(i) + g.nz) % g.nz;
+                if (pore_r2(g, xs, ys, zs) >= g.pore_t) { f[i] = plane(i)[n]; continue; }
+            }
+            f[i] = plane(opp(i))[src];
         }
     }
 
-    R Fx = (R)__ldg(a.gforce), Fy = (R)__ldg(a.gforce + 1), Fz = (R)__ldg(a.gforce + 2);
+    R Fx, Fy, Fz;
+    if constexpr (sizeof(R) == 4) {
+        Fx = __ldg(a.gforce_f); Fy = __ldg(a.gforce_f + 1); Fz = __ldg(a.gforce_f + 2);
+    } else {
+        Fx = __ldg(a.gforce); Fy = __ldg(a.gforce + 1); Fz = __ldg(a.gforce + 2);
+    }
     if (a.tiles && a.tiles[tile_of(x, y, z, a.ntx, a.nty)]) {
         Fx += (R)a.Fn[n];
         Fy += (R)a.Fn[N + n];
@@ -252,20 +257,22 @@ __global__ void __launch_bounds__(128) k_collide_stream(const FluidArgs a) {
     uint32_t step = 0;
     if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;
 
-    collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a, (uint32_t)n, step);
+    if constexpr (sizeof(R) == 4) collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pf, a, (uint32_t)n, step);
+    else collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pd, a, (uint32_t)n, step);
 
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) A[(long long)opp(i) * N + n] = f[i];
+        for (int i = 0; i < 19; ++i) plane(opp(i))[n] = f[i];
     } else {
         A[n] = f[0];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const int xd = X(cx(i)), yd = Y(cy(i)), zd = Z(cz(i));
-            if (PORE && near_wall && pore_r2(g, xd, yd, zd) >= g.pore_t)
-                A[(long long)opp(i) * N + n] = f[i];
-            else
-                A[(long long)i * N + nidx(g, xd, yd, zd)] = f[i];
+            const unsigned dst = (unsigned)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
+            if (PORE && near_wall) {
+                int xd = xo[1 + cx(i)], yd = (y + cy(i) + g.ny) % g.ny, zd = (z + cz(i) + g.nz) % g.nz;
+                if (pore_r2(g, xd, yd, zd) >= g.pore_t) { plane(opp(i))[n] = f[i]; continue; }
+            }
+            plane(i)[dst] = f[i];
         }
     }
 }

@@ -9,15 +9,24 @@
 
 namespace lbk {
 
+// Collision parameters in the compute precision of the kernel (the FP32
+// kernel gets them pre-rounded on the host, so it converts nothing).
+template <typename R>
+struct CollParams {
+    R rho0;
+    R omega;                     // BGK 1/tau
+    R gs, gb, go, ge;            // MRT rates (shear, bulk, odd ghost, even ghost)
+    R sig[15];                   // noise amplitude of modes 4..18 divided by sqrt(rho)
+};
+
 // Everything the fused collide-and-stream kernel reads besides populations.
 struct FluidArgs {
     Geom g;
     void *f;                     // populations: double[19][N] (FP64) or float[19][N] deviations
-    double rho0;
-    double omega;                // BGK 1/tau
-    double gs, gb, go, ge;       // MRT rates (shear, bulk, odd ghost, even ghost)
-    double sig[15];              // noise amplitude of modes 4..18 divided by sqrt(rho)
+    CollParams<double> pd;
+    CollParams<float> pf;
     const double *gforce;        // device: uniform force density (3)
+    const float *gforce_f;       // device: the same, rounded to FP32
     const double *Fn;            // device: spread bead force [3][N] or nullptr
     const unsigned char *tiles;  // device: 4x4x4 tile flags of Fn or nullptr
     int ntx, nty;
@@ -76,9 +85,8 @@ cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, do
                            int nblocks, double *out4, cudaStream_t s);
 cudaError_t launch_advance(unsigned long long *step, unsigned int by, cudaStream_t s);
 
-cudaError_t launch_kick_drift(Body *b, int nbodies, cudaStream_t s);
-cudaError_t launch_clear_tiles(double *F, unsigned char *tiles, const Geom &g, int ntx, int nty, int ntz,
-                               cudaStream_t s);
+cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, double *F, unsigned char *tiles,
+                            const Geom &g, int ntx, int nty, int ntz, cudaStream_t s);
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
 cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s);
 

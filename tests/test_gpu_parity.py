@@ -61,7 +61,8 @@ def test_pore_bounce_back(precision, axis):
         assert P.pop_error() <= TOL[precision]
     mg, _ = P.gpu.lb_conservation()
     mo, _ = P.orc.conservation()
-    assert abs(mg - mo) <= 1e-11 * mo
+    # FP32 deviations carry ~1e-7 relative rounding of O(1e-2) deviations
+    assert abs(mg - mo) <= (1e-11 if precision == 64 else 1e-8) * mo
 
 
 @pytest.mark.parametrize("precision", [64, 32])
