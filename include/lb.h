@@ -175,6 +175,36 @@ lb_status lb_kernel_time(lb_handle h, double *total_ms, long long *launches);
 const char *lb_last_error(lb_handle h);
 const char *lb_status_string(lb_status s);
 
+/* Allocation-free mass and momentum reduction. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, either
+ * because another allocator (for example a caching allocator) already holds
+ * the device's free memory, or because they must not let an allocation
+ * synchronise the device while a simulation runs. It allocates nothing: its
+ * per-block partial sums live in a static device array of
+ * LB_NOALLOC_MAX_BLOCKS * 4 doubles (256 KiB), which every GPU that loads the
+ * library keeps until the process exits.
+ *
+ * d_populations: DEVICE pointer to a population array laid out like the
+ * library's own, [19][nx*ny*nz], doubles (precision 64) or deviations
+ * f_i - w_i rho0 as floats (precision 32), in the in-place streaming layout
+ * after an even (odd_parity = 0) or odd (odd_parity = 1) number of steps.
+ * pore_radius > 0 excludes the wall nodes of a pore along pore_axis, as
+ * lb_set_pore defines them. d_out: DEVICE pointer to 4 doubles receiving
+ * {sum f, sum c_x f, sum c_y f, sum c_z f} over the fluid nodes. Work is
+ * queued on cuda_stream (NULL = legacy default stream) without waiting.
+ * err (may be NULL) receives a message of at most err_len bytes on failure.
+ * Lattices of more than LB_NOALLOC_MAX_NODES nodes are rejected with
+ * LB_ERR_ARG. All calls share the one scratch array, so calls that overlap
+ * on the GPU race and give wrong sums. The first call on a device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture. */
+#define LB_NOALLOC_NODES_PER_BLOCK 4096
+#define LB_NOALLOC_MAX_BLOCKS 8192
+#define LB_NOALLOC_MAX_NODES (LB_NOALLOC_NODES_PER_BLOCK * LB_NOALLOC_MAX_BLOCKS)
+lb_status lb_moments_noalloc(const void *d_populations, int precision, int nx, int ny, int nz,
+                             int odd_parity, double rho0, double pore_radius, int pore_axis,
+                             double *d_out, void *cuda_stream, char *err, size_t err_len);
+
 /* Host-only: the velocity set c[19*3], weights w[19] and opposite-link table
  * opp[19] the library uses. Needs no GPU. Returns 19. */
 int lb_lattice(int *c, double *w, int *opp);

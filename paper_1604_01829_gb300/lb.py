@@ -68,7 +68,7 @@ _SIGS = {
 }
 
 # every symbol include/lb.h declares
-EXPORTS = sorted(list(_SIGS) + ["lb_last_error", "lb_status_string", "lb_lattice"])
+EXPORTS = sorted(list(_SIGS) + ["lb_last_error", "lb_status_string", "lb_lattice", "lb_moments_noalloc"])
 
 
 def load():
@@ -91,6 +91,10 @@ def load():
             L.lb_status_string.restype = C.c_char_p
             L.lb_lattice.argtypes = [_ip, _dp, _ip]
             L.lb_lattice.restype = C.c_int
+            L.lb_moments_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                             C.c_char_p, C.c_size_t]
+            L.lb_moments_noalloc.restype = C.c_int
             _lib = L
     return _lib
 
@@ -127,6 +131,19 @@ def lb_lattice():
     opp = np.zeros(19, np.int32)
     load().lb_lattice(c.ctypes.data_as(_ip), _d(w), opp.ctypes.data_as(_ip))
     return c.reshape(19, 3), w, opp
+
+
+def lb_moments_noalloc(d_populations, precision, nx, ny, nz, odd_parity, rho0, d_out,
+                       pore_radius=0.0, pore_axis=2, stream=None):
+    """Allocation-free mass/momentum sums of a device population array into
+    the 4 doubles at device address d_out (see include/lb.h). Raises LBError
+    with the library's message on failure."""
+    err = C.create_string_buffer(256)
+    st = load().lb_moments_noalloc(C.c_void_p(d_populations), int(precision), int(nx), int(ny), int(nz),
+                                   int(odd_parity), float(rho0), float(pore_radius), int(pore_axis),
+                                   C.c_void_p(d_out), C.c_void_p(stream) if stream else None, err, 256)
+    if st != LB_OK:
+        raise LBError(st, err.value.decode())
 
 
 def make_params(nx, ny, nz, precision=64, collision=0, tau=1.0, gamma_shear=0.0, gamma_bulk=0.0,
