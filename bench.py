@@ -57,7 +57,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lb_fluid.cu", "lb_device.cuh", "lb_internal.h"):
+    for f in ("lb_fluid.cu", "lb_collide.cuh", "lb_device.cuh", "lb_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1604_01829_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -163,6 +163,14 @@ typedef struct {
 
 lb_status lb_info(lb_handle h, lb_info_t *info);
 
+/* Choice of the fused collide-and-stream kernel: variant 0 = automatic
+ * (currently the plain kernel, the faster one measured on GB300), 1 = plain
+ * per-thread loads, 2 = TMA-staged
+ * (FP32 storage, no pore, nx % 4 == 0, else LB_ERR_ARG). stages (0 = auto,
+ * 2-6) sets the depth of the shared-memory ring of row segments, ctas_per_sm
+ * (0 = auto) the persistent grid. Results do not depend on the choice. */
+lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_per_sm);
+
 /* Kernel timing: when on, CUDA events bracket every launch of the fused
  * collide-and-stream kernel on the handle's stream. lb_kernel_time returns
  * (synchronising) the summed device time in ms and the number of timed

@@ -23,6 +23,9 @@ struct lb_ctx {
     double *gforce = nullptr;               // device (3)
     float *gforce_f = nullptr;              // device (3), FP32 copy
     unsigned long long *step_dev = nullptr; // device step counter
+    int *err_dev = nullptr;                 // device error word of bounded waits
+    int cs_variant = 0;                     // collide kernel: 0 auto (plain), 1 plain, 2 TMA-staged
+    int tma_stages = 0, tma_ctas = 0;       // 0 = library default
     long long step = 0;                     // host mirror
     long long nfluid = 0;
     double sig[15] = {};
@@ -169,6 +172,15 @@ lb_status push_bodies(lb_ctx *h) {
     return LB_OK;
 }
 
+// LB_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out (synchronises)
+lb_status check_device_error(lb_ctx *h) {
+    int e = 0;
+    LB_CUDA(h, cudaMemcpyAsync(&e, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (e) return fail(h, LB_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy did not complete)");
+    return LB_OK;
+}
+
 lb_status check_handle(lb_ctx *h) {
     if (!h) return fail(nullptr, LB_ERR_ARG, "null handle");
     return LB_OK;
@@ -178,20 +190,32 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
     lbk::FluidArgs a{};
     a.g = h->g;
     a.f = h->f;
+    // MRT coefficients with c_k = w_diag / b_k = (1/36) / b_k folded in
+    static const double bk[19] = {1.0, 1.0 / 3, 1.0 / 3, 1.0 / 3, 2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9,
+                                  1.0 / 9, 2.0 / 3, 2.0 / 3, 2.0 / 3, 2.0 / 9, 2.0 / 9, 2.0 / 9, 2.0, 4.0 / 3,
+                                  4.0 / 9};
+    auto rate = [&](int k) {
+        return k == 4 ? h->p.gamma_bulk : (k <= 9 ? h->p.gamma_shear : (k <= 15 ? h->p.gamma_odd : h->p.gamma_even));
+    };
     a.pd.rho0 = h->p.rho0;
     a.pd.omega = 1.0 / h->p.tau;
-    a.pd.gs = h->p.gamma_shear;
-    a.pd.gb = h->p.gamma_bulk;
-    a.pd.go = h->p.gamma_odd;
-    a.pd.ge = h->p.gamma_even;
-    for (int k = 0; k < 15; ++k) a.pd.sig[k] = h->sig[k];
+    for (int k = 4; k <= 9; ++k) {
+        const double c = (1.0 / 36.0) / bk[k], g = rate(k);
+        a.pd.ke[k - 4] = c * (1.0 - g);
+        a.pd.km[k - 4] = c * g;
+        a.pd.ks[k - 4] = c * 0.5 * (1.0 + g);
+    }
+    for (int k = 10; k <= 18; ++k) a.pd.kg[k - 10] = (1.0 / 36.0) / bk[k] * rate(k);
+    for (int k = 4; k <= 18; ++k) a.pd.kn[k - 4] = (1.0 / 36.0) / bk[k] * h->sig[k - 4];
     a.pf.rho0 = (float)a.pd.rho0;
     a.pf.omega = (float)a.pd.omega;
-    a.pf.gs = (float)a.pd.gs;
-    a.pf.gb = (float)a.pd.gb;
-    a.pf.go = (float)a.pd.go;
-    a.pf.ge = (float)a.pd.ge;
-    for (int k = 0; k < 15; ++k) a.pf.sig[k] = (float)a.pd.sig[k];
+    for (int k = 0; k < 6; ++k) {
+        a.pf.ke[k] = (float)a.pd.ke[k];
+        a.pf.km[k] = (float)a.pd.km[k];
+        a.pf.ks[k] = (float)a.pd.ks[k];
+    }
+    for (int k = 0; k < 9; ++k) a.pf.kg[k] = (float)a.pd.kg[k];
+    for (int k = 0; k < 15; ++k) a.pf.kn[k] = (float)(a.pd.kn[k] * 3.4641016151377544 * 2.3283064365386963e-10);
     a.gforce = h->gforce;
     a.gforce_f = h->gforce_f;
     const bool bodies = !h->hb.empty() && !h->hbody_of.empty();
@@ -204,6 +228,9 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
     a.instance = h->p.instance;
     a.step_base = h->step_dev;
     a.step_off = step_off;
+    a.err = h->err_dev;
+    const size_t es = h->fp32 ? 4 : 8;
+    for (int i = 0; i < 19; ++i) a.plane[i] = static_cast<char *>(h->f) + (size_t)i * (size_t)h->g.N * es;
     return a;
 }
 
@@ -231,7 +258,10 @@ lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
         }
         LB_CUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
     }
-    cudaError_t e = lbk::launch_collide_stream(a, h->fp32, h->p.collision, noise, odd, h->block, h->stream);
+    const bool tma = h->cs_variant == 2 && lbk::tma_collide_supported(h->g, h->fp32);
+    cudaError_t e = tma ? lbk::launch_collide_stream_tma(a, h->p.collision, noise, odd, h->tma_stages, h->tma_ctas,
+                                                         h->stream)
+                        : lbk::launch_collide_stream(a, h->fp32, h->p.collision, noise, odd, h->block, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "collide_stream launch");
     if (h->timing) {
         LB_CUDA(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
@@ -336,7 +366,8 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
     if ((s = dev_alloc(h, &h->f, es * 19 * (size_t)h->g.N)) != LB_OK ||
         (s = dev_alloc(h, &h->gforce, 3 * sizeof(double))) != LB_OK ||
         (s = dev_alloc(h, &h->gforce_f, 3 * sizeof(float))) != LB_OK ||
-        (s = dev_alloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK) {
+        (s = dev_alloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK ||
+        (s = dev_alloc(h, &h->err_dev, sizeof(int))) != LB_OK) {
         g_create_error = h->err;
         lb_destroy(h);
         return s;
@@ -349,6 +380,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
         return s;
     }
     e = cudaMemsetAsync(h->step_dev, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = lbk::launch_init(h->f, h->fp32, h->g.N, p->rho0, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -363,7 +395,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
 lb_status lb_destroy(lb_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
+    void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -545,7 +577,7 @@ lb_status lb_forces(lb_handle h, int id, double F[3], double T[3], double *per_b
         LB_CUDA(h, cudaMemcpyAsync(per_bead, h->dFbead + 3 * (size_t)b0, sizeof(double) * 3 * (b1 - b0),
                                    cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
-    return LB_OK;
+    return check_device_error(h);
 }
 
 lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T) {
@@ -562,7 +594,7 @@ lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T) {
     if (T) LB_CUDA(h, cudaMemcpy2DAsync(T, 3 * sizeof(double), &h->db[0].T_tot[0], sizeof(Body), 3 * sizeof(double),
                                         nbodies, cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
-    return LB_OK;
+    return check_device_error(h);
 }
 
 lb_status lb_get_body(lb_handle h, int id, double X[3], double V[3], double q[4], double w[3]) {
@@ -657,6 +689,8 @@ lb_status lb_conservation(lb_handle h, double *mass, double mom[3]) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(o, h->out4, sizeof(o), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lb_conservation");
+    lb_status de = check_device_error(h);
+    if (de != LB_OK) return de;
     if (h->fp32) o[0] += h->p.rho0 * (double)h->nfluid;
     if (mass) *mass = o[0];
     if (mom)
@@ -676,6 +710,18 @@ lb_status lb_info(lb_handle h, lb_info_t *info) {
     info->nbeads = (int)h->hbody_of.size();
     info->precision = h->fp32 ? 32 : 64;
     info->device_bytes = h->dev_bytes;
+    return LB_OK;
+}
+
+lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_per_sm) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (variant < 0 || variant > 2 || stages < 0 || stages > 6 || ctas_per_sm < 0 || ctas_per_sm > 8)
+        return fail(h, LB_ERR_ARG, "variant 0-2, stages 0-6, ctas_per_sm 0-8");
+    if (variant == 2 && !lbk::tma_collide_supported(h->g, h->fp32))
+        return fail(h, LB_ERR_ARG, "the TMA-staged kernel needs FP32 storage, no pore and nx % 4 == 0");
+    h->cs_variant = variant;
+    h->tma_stages = stages;
+    h->tma_ctas = ctas_per_sm;
     return LB_OK;
 }
 

@@ -15,8 +15,13 @@ template <typename R>
 struct CollParams {
     R rho0;
     R omega;                     // BGK 1/tau
-    R gs, gb, go, ge;            // MRT rates (shear, bulk, odd ghost, even ghost)
-    R sig[15];                   // noise amplitude of modes 4..18 divided by sqrt(rho)
+    // MRT, per mode k with c_k = w_diag / b_k folded in (modes 4-9):
+    R ke[6];                     // c_k (1 - g_k): weight of the equilibrium moment
+    R km[6];                     // c_k g_k: weight of the pre-collision moment
+    R ks[6];                     // c_k (1 + g_k)/2: weight of the Guo source moment
+    R kg[9];                     // ghost modes 10-18: c_k g_k
+    R kn[15];                    // noise modes 4-18: c_k sqrt(3 kT b_k (1 - g_k^2)) / sqrt(rho)
+                                 //   (FP32: times sqrt(12) 2^-32, applied to the centred integer)
 };
 
 // Everything the fused collide-and-stream kernel reads besides populations.
@@ -33,6 +38,8 @@ struct FluidArgs {
     uint32_t key0, key1, instance;
     const unsigned long long *step_base;  // device step counter of the first step of this launch group
     uint32_t step_off;
+    int *err;                    // device error word (a bounded wait ran out), may be null
+    void *plane[19];             // base of each population plane (f + i N), uniform per launch
 };
 
 // Rigid bodies (FP64, array of structs; few bodies, one thread each).
@@ -75,6 +82,10 @@ struct CoupleArgs {
 cudaError_t launch_init(void *f, bool fp32, long long N, double rho0, cudaStream_t s);
 cudaError_t launch_collide_stream(const FluidArgs &a, bool fp32, int collision, bool noise, bool odd,
                                   dim3 block, cudaStream_t s);
+// TMA-staged variant (FP32 storage, periodic, nx % 4 == 0); cudaErrorNotSupported otherwise
+bool tma_collide_supported(const Geom &g, bool fp32);
+cudaError_t launch_collide_stream_tma(const FluidArgs &a, int collision, bool noise, bool odd, int stages_hint,
+                                      int ctas_per_sm_hint, cudaStream_t s);
 cudaError_t launch_gather(const void *f, bool fp32, const Geom &g, bool odd, double rho0, double *out,
                           cudaStream_t s);
 cudaError_t launch_scatter(void *f, bool fp32, const Geom &g, bool odd, double rho0, const double *in,

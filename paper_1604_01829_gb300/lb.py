@@ -64,6 +64,7 @@ _SIGS = {
     "lb_conservation": [C.c_void_p, _dp, _dp],
     "lb_info": [C.c_void_p, C.POINTER(lb_info_t)],
     "lb_set_timing": [C.c_void_p, C.c_int],
+    "lb_set_kernel_variant": [C.c_void_p, C.c_int, C.c_int, C.c_int],
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
 }
 
@@ -263,6 +264,9 @@ class LB:
         i = lb_info_t()
         _check(self.h, load().lb_info(self.h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in lb_info_t._fields_}
+
+    def lb_set_kernel_variant(self, variant=0, stages=0, ctas_per_sm=0):
+        _check(self.h, load().lb_set_kernel_variant(self.h, int(variant), int(stages), int(ctas_per_sm)))
 
     def lb_set_timing(self, on=True):
         _check(self.h, load().lb_set_timing(self.h, int(bool(on))))

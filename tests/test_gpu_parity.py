@@ -68,7 +68,7 @@ def test_pore_bounce_back(precision, axis):
 @pytest.mark.parametrize("precision", [64, 32])
 def test_free_raspberry_periodic(precision):
     L = 24
-    params = dict(collision=0, tau=0.9, gamma_bead=Wl.paper_gamma_to_lattice(200.0),
+    params = dict(collision=0, tau=0.9, gamma_bead=Wl.paper_gamma_to_lattice(100.0),
                   compensate_force=1, body_force=(0, 2e-6, 0))
     P = Pair(L, L, L + 3, precision=precision, **params)
     P.set_populations(perturbed_populations(P.N, amp=0.005, u_amp=0.005, seed=7))
@@ -149,3 +149,46 @@ def test_errors_are_reported_not_raised_in_the_library():
     assert ei.value.status == lb.LB_ERR_STATE
     with pytest.raises(lb.LBError):
         g.lb_sample_populations([8 ** 3])
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("case", ["bgk", "mrt_noise"])
+@pytest.mark.parametrize("steps", [1, 4, 7])
+def test_fp32_kernel_variants(variant, case, steps):
+    """Plain and TMA-staged collide kernels (nx a multiple of 4, periodic)
+    against the oracle; rows of 36 nodes, 9 x 7 rows."""
+    params = dict(collision=0, tau=0.7) if case == "bgk" else dict(MRT, kT=1e-4, seed=99)
+    params["body_force"] = (2e-5, 1e-5, -1e-5)
+    P = Pair(36, 9, 7, precision=32, **params)
+    P.gpu.lb_set_kernel_variant(variant)
+    P.set_populations(perturbed_populations(P.N, seed=17))
+    P.step(steps)
+    assert P.pop_error() <= TOL[32]
+
+
+@pytest.mark.parametrize("stages,ctas", [(2, 1), (3, 2), (6, 1)])
+def test_tma_ring_depths_with_coupling(stages, ctas):
+    """TMA-staged kernel with bead forces in flagged tiles, several ring
+    depths and persistent grids; rows of 64 nodes (several rows per CTA)."""
+    # explicit coupling is stable for N gamma / M well below 2 (here ~0.2)
+    params = dict(MRT, kT=1e-4, seed=5, gamma_bead=Wl.paper_gamma_to_lattice(50.0), compensate_force=1)
+    P = Pair(64, 12, 10, precision=32, **params)
+    P.gpu.lb_set_kernel_variant(2, stages, ctas)
+    ell = Wl.ellipsoid_raspberry(4.0, 2.0, 2.0, seed=8)
+    P.add_body(ell, [30.3, 6.1, 5.2], [0.7, 0.3, -0.5, 0.4], mass=120.0, inertia=(60, 180, 180),
+               F_ext=(1e-3, 0, 0))
+    for _ in range(3):
+        P.step(3)
+        assert P.pop_error() <= TOL[32]
+        e = P.body_errors(0)
+        assert e["bead"] <= 5e-5 and e["F"] <= 5e-5, e
+
+
+def test_kernel_variant_rejects_unsupported_shapes():
+    from paper_1604_01829_gb300 import lb
+    g = lb.LB(37, 8, 8, precision=32)
+    with pytest.raises(lb.LBError):
+        g.lb_set_kernel_variant(2)
+    g64 = lb.LB(36, 8, 8, precision=64)
+    with pytest.raises(lb.LBError):
+        g64.lb_set_kernel_variant(2)
