@@ -183,6 +183,50 @@ lb_status lb_kernel_time(lb_handle h, double *total_ms, long long *launches);
 const char *lb_last_error(lb_handle h);
 const char *lb_status_string(lb_status s);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent lattices of uneven size advanced together: the same step
+ * as above for every instance (Sec. 1.1, Eq. (latticeboltzmannfriction),
+ * Sec. 2.3), with one launch per kernel per step for all instances and the
+ * step sequence replayed from a CUDA graph. Instance k reproduces what a
+ * single handle with params[k] computes. */
+typedef struct lb_batch_ctx *lb_batch_handle;
+
+/* params[n]: one parameter set per instance (all with the same precision,
+ * collision type and thermal noise on/off; sizes, rates, seeds, forces may
+ * differ). cuda_stream as for lb_create. Errors: LB_ERR_ARG, LB_ERR_OOM,
+ * LB_ERR_CUDA. */
+lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_batch_handle *out);
+lb_status lb_batch_destroy(lb_batch_handle h);
+/* As lb_set_pore / lb_add_raspberry for instance `inst` (before the first
+ * step); *body_id is the body's index within its instance. */
+lb_status lb_batch_set_pore(lb_batch_handle h, int inst, double radius, int axis);
+lb_status lb_batch_add_raspberry(lb_batch_handle h, int inst, const double *beads_body_xyz, int nbeads,
+                                 const double X[3], const double q[4], double mass, const double inertia[3],
+                                 const double F_ext[3], const double T_ext[3], int fixed, int *body_id);
+/* Advances every instance nsteps steps (pairs of steps as one graph launch). */
+lb_status lb_batch_step(lb_batch_handle h, int nsteps);
+lb_status lb_batch_forces(lb_batch_handle h, int inst, int body_id, double F[3], double T[3]);
+lb_status lb_batch_get_body(lb_batch_handle h, int inst, int body_id, double X[3], double V[3], double q[4],
+                            double w[3]);
+lb_status lb_batch_get_populations(lb_batch_handle h, int inst, double *host, size_t n);
+lb_status lb_batch_set_populations(lb_batch_handle h, int inst, const double *host, size_t n);
+/* Work schedule of the fluid kernel: tile_nodes (64, 128, 256) consecutive
+ * nodes of one instance per CTA iteration, blocks_per_sm resident CTAs of
+ * the persistent grid (tile_nodes * blocks_per_sm <= 2048), order 0 =
+ * tiles dealt round-robin to CTAs, 1 = contiguous chunks. Results do not
+ * depend on it. */
+lb_status lb_batch_set_schedule(lb_batch_handle h, int tile_nodes, int blocks_per_sm, int order);
+/* Measures every schedule for trial_steps steps on a snapshot of the state
+ * (restored afterwards, so the simulation is unchanged), keeps the fastest;
+ * chosen[3] (may be NULL) receives it, *best_ms_per_step its step time. */
+lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], double *best_ms_per_step);
+lb_status lb_batch_info(lb_batch_handle h, long long *total_nodes, long long *step, int schedule[3]);
+/* Kernel timing of the batched fluid kernel (steps run without the graph
+ * while on), as lb_set_timing / lb_kernel_time. */
+lb_status lb_batch_set_timing(lb_batch_handle h, int on);
+lb_status lb_batch_kernel_time(lb_batch_handle h, double *total_ms, long long *launches);
+const char *lb_batch_last_error(lb_batch_handle h);
+
 /* Allocation-free mass and momentum reduction. The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, either
  * because another allocator (for example a caching allocator) already holds

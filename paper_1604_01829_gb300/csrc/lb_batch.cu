@@ -1,0 +1,992 @@
+// Batched lattices: many independent LB + raspberry instances of uneven size
+// advanced together (one launch per kernel per step for all instances; the
+// step sequence replayed from a CUDA graph).
+//
+// Each instance is the same step as a single lattice (Sec. 1.1 collision
+// and streaming, Eq. (latticeboltzmannfriction) coupling, Sec. 2.3 bodies
+// and pore walls of Ustach & Faller, arXiv:1604.01829); only the
+// scheduling differs. All populations live in one pool (instance k at
+// element offset off_k, its own plane stride N_k); the fluid kernel walks a
+// flattened list of equal work tiles (TS consecutive nodes of one instance)
+// with a persistent grid, so uneven instances load-balance by construction.
+// Tile size, blocks per SM and the tile-to-CTA order are chosen by a
+// measuring autotuner on a snapshot of the state, restored afterwards.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_collide.cuh"
+#include "lb_couple.cuh"
+
+namespace lbk {
+
+struct BInst {
+    Geom g;
+    long long off;               // element offset of plane 0 in the population pool
+    long long foff;              // offset of this instance's [3][N] block in a force pool
+    long long toff;              // offset of its tile flags
+    int ntx, nty, ntz;
+    uint32_t key0, key1, instance;
+    double rho0, gamma, noise_amp;
+    double gd[3];                // uniform force density
+    float gf[3];
+    CollParams<double> pd;
+    CollParams<float> pf;
+};
+
+struct BatchArgs {
+    const BInst *inst;
+    const int *tile_start;       // n + 1: first work tile of each instance
+    int n, ntiles, chunk, order;
+    void *pool;
+    const double *F;             // spread force of this step (pool), nullptr without bodies
+    const unsigned char *tiles;
+    const unsigned long long *step_base;
+    uint32_t step_off;
+};
+
+namespace {
+
+__device__ __forceinline__ int find_instance(const int *start, int n, int t) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T, int COLL, bool NOISE, bool ODD>
+__global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs a) {
+    using R = T;
+    constexpr bool DEV = sizeof(T) == 4;
+    for (int it = 0;; ++it) {
+        int t;
+        if (a.order == 0) t = blockIdx.x + it * gridDim.x;
+        else {
+            if (it >= a.chunk) break;
+            t = blockIdx.x * a.chunk + it;
+        }
+        if (t >= a.ntiles) break;
+        const int k = find_instance(a.tile_start, a.n, t);
+        const BInst &I = a.inst[k];
+        const Geom g = I.g;
+        const long long n = (long long)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
+        if (n >= g.N) continue;
+        const int x = (int)(n % g.nx);
+        const long long r = n / g.nx;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        bool near_wall = false;
+        if (g.pore_axis >= 0) {
+            const long long r2 = pore_r2(g, x, y, z);
+            if (r2 >= g.pore_t) continue;
+            near_wall = r2 >= g.pore_in;
+        }
+        T *A = static_cast<T *>(a.pool) + I.off;
+        const long long N = g.N;
+        const int nxy = g.nx * g.ny;
+        const int xo[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
+        const int yo[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.nx, y * g.nx, (y == g.ny - 1 ? 0 : y + 1) * g.nx};
+        const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * nxy, z * nxy, (z == g.nz - 1 ? 0 : z + 1) * nxy};
+        R f[19];
+        if (!ODD) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[i] = A[i * N + n];
+        } else {
+            f[0] = A[n];
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const long long src = xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)];
+                if (near_wall) {
+                    const int ys = (y - cy(i) + g.ny) % g.ny, zs = (z - cz(i) + g.nz) % g.nz;
+                    if (pore_r2(g, xo[1 - cx(i)], ys, zs) >= g.pore_t) { f[i] = A[i * N + n]; continue; }
+                }
+                f[i] = A[opp(i) * N + src];
+            }
+        }
+        R Fx, Fy, Fz;
+        if constexpr (DEV) { Fx = I.gf[0]; Fy = I.gf[1]; Fz = I.gf[2]; }
+        else { Fx = I.gd[0]; Fy = I.gd[1]; Fz = I.gd[2]; }
+        if (a.tiles && a.tiles[I.toff + tile_of(x, y, z, I.ntx, I.nty)]) {
+            const double *Fn = a.F + I.foff;
+            Fx += (R)Fn[n];
+            Fy += (R)Fn[N + n];
+            Fz += (R)Fn[2 * N + n];
+        }
+        uint32_t step = 0;
+        if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;
+        const uint2 key = make_uint2(I.key0, I.key1);
+        if constexpr (DEV) collide<R, true, COLL, NOISE>(f, Fx, Fy, Fz, I.pf, key, I.instance, (uint32_t)n, step);
+        else collide<R, false, COLL, NOISE>(f, Fx, Fy, Fz, I.pd, key, I.instance, (uint32_t)n, step);
+        if (!ODD) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) A[opp(i) * N + n] = f[i];
+        } else {
+            A[n] = f[0];
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const long long dst = xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)];
+                if (near_wall) {
+                    const int yd = (y + cy(i) + g.ny) % g.ny, zd = (z + cz(i) + g.nz) % g.nz;
+                    if (pore_r2(g, xo[1 + cx(i)], yd, zd) >= g.pore_t) { A[opp(i) * N + n] = f[i]; continue; }
+                }
+                A[i * N + dst] = f[i];
+            }
+        }
+    }
+}
+
+struct BatchCouple {
+    const BInst *inst;
+    const void *pool;
+    bool fp32, odd;
+    const double *Fprev;
+    double *Fcur;
+    unsigned char *tiles_cur;
+    const double *s;
+    const int *bead_body;
+    const int *bead_rng;          // bead index within its own lattice
+    Body *bodies;
+    double *F_bead;
+    int nbeads;
+    const unsigned long long *step_base;
+    uint32_t step_off;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = t >> 3;
+    const bool active = k < b.nbeads;
+    // lanes of inactive groups borrow bead 0's instance (they do no work)
+    const int kk = active ? k : 0;
+    const BInst &I = b.inst[b.bodies[b.bead_body[kk]].inst];
+    CoupleArgs a;
+    a.g = I.g;
+    a.f = static_cast<const T *>(b.pool) + I.off;
+    a.fp32 = b.fp32;
+    a.odd = b.odd;
+    a.rho0 = I.rho0;
+    a.gamma = I.gamma;
+    a.noise_amp = I.noise_amp;
+    a.gforce = I.gd;
+    a.Fprev = b.Fprev + I.foff;
+    a.Fcur = b.Fcur + I.foff;
+    a.tiles_cur = b.tiles_cur + I.toff;
+    a.ntx = I.ntx;
+    a.nty = I.nty;
+    a.s = b.s;
+    a.bead_body = b.bead_body;
+    a.bodies = b.bodies;
+    a.F_bead = b.F_bead;
+    a.nbeads = b.nbeads;
+    a.key0 = I.key0;
+    a.key1 = I.key1;
+    a.instance = I.instance;
+    a.step_base = b.step_base;
+    a.step_off = b.step_off;
+    couple_bead<T>(a, k, active ? b.bead_rng[k] : 0, t & 7, threadIdx.x & 31, active);
+}
+
+// previous step's second half kick (optional), this step's kick and drift,
+// and the clearing of every flagged tile of this step's force pool
+__global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, double *F, unsigned char *tiles,
+                            const BInst *inst, const long long *flag_start, int n, long long ntiles) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < nb) {
+        Body &B = bodies[t];
+        if (finish_prev) kick2(B);
+        kick_drift(B);
+    }
+    if (!tiles || t >= ntiles || !tiles[t]) return;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (flag_start[mid] <= t) lo = mid; else hi = mid;
+    }
+    const BInst &I = inst[lo];
+    const long long lt = t - flag_start[lo];
+    const int tx = (int)(lt % I.ntx), ty = (int)((lt / I.ntx) % I.nty), tz = (int)(lt / ((long long)I.ntx * I.nty));
+    double *Fi = F + I.foff;
+    for (int dz = 0; dz < 4; ++dz) {
+        const int z = 4 * tz + dz;
+        if (z >= I.g.nz) break;
+        for (int dy = 0; dy < 4; ++dy) {
+            const int y = 4 * ty + dy;
+            if (y >= I.g.ny) break;
+            for (int dx = 0; dx < 4; ++dx) {
+                const int x = 4 * tx + dx;
+                if (x >= I.g.nx) break;
+                const long long nn = nidx(I.g, x, y, z);
+                Fi[nn] = 0.0;
+                Fi[I.g.N + nn] = 0.0;
+                Fi[2 * I.g.N + nn] = 0.0;
+            }
+        }
+    }
+    tiles[t] = 0;
+}
+
+template <typename T>
+__global__ void k_batch_gather(const T *A, Geom g, bool odd, double rho0, double *out) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    const int x = (int)(n % g.nx);
+    const long long r = n / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    const bool wall = is_wall(g, x, y, z);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const T v = wall ? A[(long long)i * g.N + n] : load_pre(A, g, x, y, z, n, i, odd);
+        out[(long long)i * g.N + n] = sizeof(T) == 4 ? (double)v + wq(i) * rho0 : (double)v;
+    }
+}
+
+template <typename T>
+__global__ void k_batch_scatter(T *A, Geom g, bool odd, double rho0, const double *in) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    const int x = (int)(n % g.nx);
+    const long long r = n / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    if (is_wall(g, x, y, z)) return;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const double v = in[(long long)i * g.N + n];
+        store_pre(A, g, x, y, z, n, i, odd, sizeof(T) == 4 ? (T)(v - wq(i) * rho0) : (T)v);
+    }
+}
+
+template <typename T>
+__global__ void k_batch_init(T *A, long long N, double rho0) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= N) return;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) A[(long long)i * N + n] = sizeof(T) == 4 ? T(0) : T(wq(i) * rho0);
+}
+
+}  // namespace
+}  // namespace lbk
+
+using lbk::BInst;
+using lbk::Body;
+
+struct lb_batch_ctx {
+    std::vector<lb_params> p;
+    int n = 0;
+    bool fp32 = false;
+    int collision = 0;
+    bool noise = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<BInst> hinst;
+    std::vector<long long> flag_start;      // n + 1
+    std::vector<long long> nfluid;
+    long long Ntot = 0, Ttot = 0, Ftot = 0;
+    void *pool = nullptr;
+    double *Fbuf[2] = {nullptr, nullptr};
+    unsigned char *tiles[2] = {nullptr, nullptr};
+    BInst *dinst = nullptr;
+    int *dtile_start = nullptr;
+    long long *dflag_start = nullptr;
+    unsigned long long *step_dev = nullptr;
+    long long step = 0;
+    // bodies
+    std::vector<Body> hb;
+    std::vector<double> hs;
+    std::vector<int> hbody_of, hbead_rng;
+    std::vector<std::vector<int>> inst_bodies;     // body ids per instance
+    std::vector<int> inst_beads;                   // beads per instance so far
+    Body *db = nullptr;
+    double *ds = nullptr;
+    int *dbody_of = nullptr, *dbead_rng = nullptr;
+    double *dFbead = nullptr;
+    bool uploaded = false;
+    // schedule
+    int TS = 128, bpsm = 8, order = 0, ntiles = 0, sms = 0;
+    // graph of two steps
+    cudaGraphExec_t gexec = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    long long timed_n = 0;
+    size_t dev_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+lb_status bfail(lb_batch_ctx *h, lb_status s, const std::string &m) {
+    if (h) h->err = m;
+    else g_batch_error = m;
+    return s;
+}
+
+#define BCUDA(h, call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return bfail((h), LB_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename P>
+lb_status balloc(lb_batch_ctx *h, P **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)ptr, bytes < 16 ? 16 : bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return bfail(h, LB_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->dev_bytes += bytes;
+    return LB_OK;
+}
+
+void fill_coll(const lb_params &p, BInst &I) {
+    static const double bk[19] = {1.0, 1.0 / 3, 1.0 / 3, 1.0 / 3, 2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9,
+                                  1.0 / 9, 2.0 / 3, 2.0 / 3, 2.0 / 3, 2.0 / 9, 2.0 / 9, 2.0 / 9, 2.0, 4.0 / 3,
+                                  4.0 / 9};
+    auto rate = [&](int k) {
+        return k == 4 ? p.gamma_bulk : (k <= 9 ? p.gamma_shear : (k <= 15 ? p.gamma_odd : p.gamma_even));
+    };
+    I.pd.rho0 = p.rho0;
+    I.pd.omega = 1.0 / p.tau;
+    for (int k = 4; k <= 9; ++k) {
+        const double c = (1.0 / 36.0) / bk[k], g = rate(k);
+        I.pd.ke[k - 4] = c * (1.0 - g);
+        I.pd.km[k - 4] = c * g;
+        I.pd.ks[k - 4] = c * 0.5 * (1.0 + g);
+    }
+    for (int k = 10; k <= 18; ++k) I.pd.kg[k - 10] = (1.0 / 36.0) / bk[k] * rate(k);
+    for (int k = 4; k <= 18; ++k) {
+        const double g = rate(k);
+        const double sig = (p.collision == 1 && p.kT > 0.0) ? std::sqrt(3.0 * p.kT * bk[k] * (1.0 - g * g)) : 0.0;
+        I.pd.kn[k - 4] = (1.0 / 36.0) / bk[k] * sig;
+    }
+    I.pf.rho0 = (float)I.pd.rho0;
+    I.pf.omega = (float)I.pd.omega;
+    for (int k = 0; k < 6; ++k) {
+        I.pf.ke[k] = (float)I.pd.ke[k];
+        I.pf.km[k] = (float)I.pd.km[k];
+        I.pf.ks[k] = (float)I.pd.ks[k];
+    }
+    for (int k = 0; k < 9; ++k) I.pf.kg[k] = (float)I.pd.kg[k];
+    for (int k = 0; k < 15; ++k) I.pf.kn[k] = (float)(I.pd.kn[k] * 3.4641016151377544 * 2.3283064365386963e-10);
+}
+
+lb_status validate(const lb_params &p) {
+    if (p.nx < 2 || p.ny < 2 || p.nz < 2) return LB_ERR_ARG;
+    if ((double)p.nx * p.ny * p.nz > 2.0e9) return LB_ERR_ARG;
+    if (p.collision == 0 && !(p.tau > 0.5)) return LB_ERR_ARG;
+    if (p.collision == 1) {
+        const double r[4] = {p.gamma_shear, p.gamma_bulk, p.gamma_odd, p.gamma_even};
+        for (double v : r)
+            if (!(v > -1.0 && v < 1.0)) return LB_ERR_ARG;
+    }
+    if (!(p.rho0 > 0.0) || !(p.kT >= 0.0) || !(p.gamma_bead >= 0.0)) return LB_ERR_ARG;
+    if (p.kT > 0.0 && p.collision == 0) return LB_ERR_ARG;
+    if (p.md_substeps != 0 && p.md_substeps != 1) return LB_ERR_ARG;
+    return LB_OK;
+}
+
+void compute_g(const lb_batch_ctx *h, int k, double g[3]) {
+    const lb_params &p = h->p[k];
+    for (int a = 0; a < 3; ++a) g[a] = p.body_force[a];
+    if (p.compensate_force && h->nfluid[k] > 0)
+        for (int b : h->inst_bodies[k])
+            if (!h->hb[b].fixed)
+                for (int a = 0; a < 3; ++a) g[a] -= h->hb[b].F_ext[a] / (double)h->nfluid[k];
+}
+
+lb_status rebuild_schedule(lb_batch_ctx *h) {
+    std::vector<int> ts(h->n + 1, 0);
+    long long acc = 0;
+    for (int k = 0; k < h->n; ++k) {
+        ts[k] = (int)acc;
+        acc += (h->hinst[k].g.N + h->TS - 1) / h->TS;
+    }
+    ts[h->n] = (int)acc;
+    if (acc > 2000000000LL) return bfail(h, LB_ERR_ARG, "too many work tiles");
+    h->ntiles = (int)acc;
+    BCUDA(h, cudaMemcpyAsync(h->dtile_start, ts.data(), sizeof(int) * (h->n + 1), cudaMemcpyHostToDevice, h->stream));
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return LB_OK;
+}
+
+lb_status upload(lb_batch_ctx *h) {
+    if (h->uploaded) return LB_OK;
+    // instance table with final body forces / compensation
+    for (int k = 0; k < h->n; ++k) {
+        double g[3];
+        compute_g(h, k, g);
+        for (int a = 0; a < 3; ++a) {
+            h->hinst[k].gd[a] = g[a];
+            h->hinst[k].gf[a] = (float)g[a];
+        }
+    }
+    BCUDA(h, cudaMemcpyAsync(h->dinst, h->hinst.data(), sizeof(BInst) * h->n, cudaMemcpyHostToDevice, h->stream));
+    const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
+    lb_status s;
+    if (nb > 0) {
+        if ((s = balloc(h, &h->db, sizeof(Body) * nb)) != LB_OK) return s;
+        if ((s = balloc(h, &h->ds, sizeof(double) * 3 * (size_t)nbeads)) != LB_OK) return s;
+        if ((s = balloc(h, &h->dbody_of, sizeof(int) * (size_t)nbeads)) != LB_OK) return s;
+        if ((s = balloc(h, &h->dbead_rng, sizeof(int) * (size_t)nbeads)) != LB_OK) return s;
+        if ((s = balloc(h, &h->dFbead, sizeof(double) * 3 * (size_t)nbeads)) != LB_OK) return s;
+        BCUDA(h, cudaMemcpyAsync(h->db, h->hb.data(), sizeof(Body) * nb, cudaMemcpyHostToDevice, h->stream));
+        if (nbeads > 0) {
+            BCUDA(h, cudaMemcpyAsync(h->ds, h->hs.data(), sizeof(double) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
+            BCUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
+            BCUDA(h, cudaMemcpyAsync(h->dbead_rng, h->hbead_rng.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
+        }
+        for (int k = 0; k < 2; ++k) {
+            if ((s = balloc(h, &h->Fbuf[k], sizeof(double) * 3 * (size_t)h->Ftot)) != LB_OK) return s;
+            if ((s = balloc(h, &h->tiles[k], (size_t)h->Ttot)) != LB_OK) return s;
+            BCUDA(h, cudaMemsetAsync(h->Fbuf[k], 0, sizeof(double) * 3 * (size_t)h->Ftot, h->stream));
+            BCUDA(h, cudaMemsetAsync(h->tiles[k], 0, (size_t)h->Ttot, h->stream));
+        }
+    }
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    h->uploaded = true;
+    return LB_OK;
+}
+
+lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
+    const bool odd = ((h->step + k) & 1) != 0;
+    const int cur = (int)((h->step + k) & 1), prev = cur ^ 1;
+    const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
+    const bool coupled = nb > 0 && nbeads > 0;
+    if (nb > 0) {
+        const long long nthreads = std::max<long long>(nb, coupled ? h->Ttot : 0);
+        lbk::k_batch_pre<<<(unsigned)((nthreads + 255) / 256), 256, 0, h->stream>>>(
+            h->db, nb, finish_prev ? 1 : 0, coupled ? h->Fbuf[cur] : nullptr, coupled ? h->tiles[cur] : nullptr,
+            h->dinst, h->dflag_start, h->n, coupled ? h->Ttot : 0);
+        BCUDA(h, cudaGetLastError());
+    }
+    if (coupled) {
+        lbk::BatchCouple c{};
+        c.inst = h->dinst;
+        c.pool = h->pool;
+        c.fp32 = h->fp32;
+        c.odd = odd;
+        c.Fprev = h->Fbuf[prev];
+        c.Fcur = h->Fbuf[cur];
+        c.tiles_cur = h->tiles[cur];
+        c.s = h->ds;
+        c.bead_body = h->dbody_of;
+        c.bead_rng = h->dbead_rng;
+        c.bodies = h->db;
+        c.F_bead = h->dFbead;
+        c.nbeads = nbeads;
+        c.step_base = h->step_dev;
+        c.step_off = (uint32_t)k;
+        const unsigned grid = (unsigned)((8LL * nbeads + 127) / 128);
+        if (h->fp32) lbk::k_batch_couple<float><<<grid, 128, 0, h->stream>>>(c);
+        else lbk::k_batch_couple<double><<<grid, 128, 0, h->stream>>>(c);
+        BCUDA(h, cudaGetLastError());
+    }
+    lbk::BatchArgs a{};
+    a.inst = h->dinst;
+    a.tile_start = h->dtile_start;
+    a.n = h->n;
+    a.ntiles = h->ntiles;
+    int grid = h->sms * h->bpsm;
+    if (grid > h->ntiles) grid = h->ntiles;
+    if (grid < 1) grid = 1;
+    a.order = h->order;
+    a.chunk = (h->ntiles + grid - 1) / grid;
+    a.pool = h->pool;
+    a.F = coupled ? h->Fbuf[cur] : nullptr;
+    a.tiles = coupled ? h->tiles[cur] : nullptr;
+    a.step_base = h->step_dev;
+    a.step_off = (uint32_t)k;
+    if (record) BCUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
+#define BLAUNCH(T, C, NZ)                                                                                   \
+    do {                                                                                                    \
+        if (odd) lbk::k_batch_collide<T, C, NZ, true><<<grid, h->TS, 0, h->stream>>>(a);                    \
+        else lbk::k_batch_collide<T, C, NZ, false><<<grid, h->TS, 0, h->stream>>>(a);                       \
+    } while (0)
+    if (h->fp32) {
+        if (h->collision == 0) BLAUNCH(float, 0, false);
+        else if (h->noise) BLAUNCH(float, 1, true);
+        else BLAUNCH(float, 1, false);
+    } else {
+        if (h->collision == 0) BLAUNCH(double, 0, false);
+        else if (h->noise) BLAUNCH(double, 1, true);
+        else BLAUNCH(double, 1, false);
+    }
+#undef BLAUNCH
+    BCUDA(h, cudaGetLastError());
+    if (record) {
+        BCUDA(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+        h->ev_used += 2;
+    }
+    return LB_OK;
+}
+
+lb_status finish_steps(lb_batch_ctx *h, int nsteps) {
+    const int nb = (int)h->hb.size();
+    if (nb > 0) BCUDA(h, lbk::launch_kick2(h->db, nb, h->stream));
+    BCUDA(h, lbk::launch_advance(h->step_dev, (unsigned)nsteps, h->stream));
+    return LB_OK;
+}
+
+lb_status eager_steps(lb_batch_ctx *h, int nsteps) {
+    for (int k = 0; k < nsteps; ++k) {
+        bool rec = false;
+        if (h->timing) {
+            if (h->ev_used + 2 > h->ev.size())
+                for (int e = 0; e < 256; ++e) {
+                    cudaEvent_t ev;
+                    BCUDA(h, cudaEventCreate(&ev));
+                    h->ev.push_back(ev);
+                }
+            rec = true;
+        }
+        lb_status s = launch_step(h, k, k > 0, rec);
+        if (s != LB_OK) return s;
+    }
+    lb_status s = finish_steps(h, nsteps);
+    h->step += nsteps;
+    return s;
+}
+
+// two steps (even, odd) + second half kick + counter advance, as one graph
+lb_status ensure_graph(lb_batch_ctx *h) {
+    if (h->gexec) return LB_OK;
+    cudaGraph_t graph = nullptr;
+    BCUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lb_status s = launch_step(h, 0, false, false);
+    if (s == LB_OK) s = launch_step(h, 1, true, false);
+    if (s == LB_OK) s = finish_steps(h, 2);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (s != LB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return LB_OK;
+}
+
+lb_status check(lb_batch_ctx *h, int k) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (k < 0 || k >= h->n) return bfail(h, LB_ERR_ARG, "instance index out of range");
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lb_batch_last_error(lb_batch_handle h) { return h ? h->err.c_str() : g_batch_error.c_str(); }
+
+lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_batch_handle *out) {
+    if (!params || n <= 0 || !out) return bfail(nullptr, LB_ERR_ARG, "need n >= 1 parameter sets");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (validate(params[k]) != LB_OK) return bfail(nullptr, LB_ERR_ARG, "invalid parameters for instance " + std::to_string(k));
+        if (params[k].precision != params[0].precision || params[k].collision != params[0].collision ||
+            (params[k].kT > 0.0) != (params[0].kT > 0.0))
+            return bfail(nullptr, LB_ERR_ARG, "all instances must share precision, collision type and noise on/off");
+    }
+    if (params[0].precision != 32 && params[0].precision != 64) return bfail(nullptr, LB_ERR_ARG, "precision must be 32 or 64");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return bfail(nullptr, LB_ERR_CUDA, "no CUDA device");
+    }
+    lb_batch_ctx *h = new (std::nothrow) lb_batch_ctx();
+    if (!h) return bfail(nullptr, LB_ERR_OOM, "host allocation failed");
+    h->p.assign(params, params + n);
+    h->n = n;
+    h->fp32 = params[0].precision == 32;
+    h->collision = params[0].collision;
+    h->noise = params[0].collision == 1 && params[0].kT > 0.0;
+    h->hinst.resize(n);
+    h->flag_start.assign(n + 1, 0);
+    h->nfluid.assign(n, 0);
+    h->inst_bodies.resize(n);
+    h->inst_beads.assign(n, 0);
+    long long off = 0, foff = 0, toff = 0;
+    for (int k = 0; k < n; ++k) {
+        const lb_params &p = params[k];
+        BInst &I = h->hinst[k];
+        std::memset(&I, 0, sizeof(I));
+        I.g.nx = p.nx; I.g.ny = p.ny; I.g.nz = p.nz;
+        I.g.N = (long long)p.nx * p.ny * p.nz;
+        I.g.pore_axis = -1;
+        I.off = off;
+        I.foff = foff;
+        I.toff = toff;
+        I.ntx = (p.nx + 3) / 4; I.nty = (p.ny + 3) / 4; I.ntz = (p.nz + 3) / 4;
+        I.key0 = (uint32_t)p.seed;
+        I.key1 = (uint32_t)(p.seed >> 32);
+        I.instance = p.instance;
+        I.rho0 = p.rho0;
+        I.gamma = p.gamma_bead;
+        I.noise_amp = p.kT > 0.0 ? std::sqrt(2.0 * p.kT * p.gamma_bead) : 0.0;
+        fill_coll(p, I);
+        h->flag_start[k] = toff;
+        h->nfluid[k] = I.g.N;
+        off += 19 * I.g.N;
+        foff += 3 * I.g.N;
+        toff += (long long)I.ntx * I.nty * I.ntz;
+    }
+    h->flag_start[n] = toff;
+    h->Ntot = off / 19;
+    h->Ftot = foff / 3;
+    h->Ttot = toff;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+    else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete h; return bfail(nullptr, LB_ERR_CUDA, "cudaStreamCreate failed"); }
+        h->own_stream = true;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t es = h->fp32 ? 4 : 8;
+    lb_status s;
+    if ((s = balloc(h, &h->pool, es * 19 * (size_t)h->Ntot)) != LB_OK ||
+        (s = balloc(h, &h->dinst, sizeof(BInst) * n)) != LB_OK ||
+        (s = balloc(h, &h->dtile_start, sizeof(int) * (n + 1))) != LB_OK ||
+        (s = balloc(h, &h->dflag_start, sizeof(long long) * (n + 1))) != LB_OK ||
+        (s = balloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK) {
+        g_batch_error = h->err;
+        lb_batch_destroy(h);
+        return s;
+    }
+    e = cudaMemsetAsync(h->step_dev, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->dflag_start, h->flag_start.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, h->stream);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        const BInst &I = h->hinst[k];
+        if (h->fp32) lbk::k_batch_init<float><<<(unsigned)((I.g.N + 255) / 256), 256, 0, h->stream>>>((float *)h->pool + I.off, I.g.N, h->p[k].rho0);
+        else lbk::k_batch_init<double><<<(unsigned)((I.g.N + 255) / 256), 256, 0, h->stream>>>((double *)h->pool + I.off, I.g.N, h->p[k].rho0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        g_batch_error = std::string("batch init: ") + cudaGetErrorString(e);
+        lb_batch_destroy(h);
+        return LB_ERR_CUDA;
+    }
+    if ((s = rebuild_schedule(h)) != LB_OK) {
+        g_batch_error = h->err;
+        lb_batch_destroy(h);
+        return s;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status lb_batch_destroy(lb_batch_handle h) {
+    if (!h) return LB_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->dinst, h->dtile_start,
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_pore(lb_batch_handle h, int k, double radius, int axis) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    if (h->uploaded || h->step > 0) return bfail(h, LB_ERR_STATE, "pores must be set before the first step");
+    if (axis < 0 || axis > 2 || !(radius > 0.0)) return bfail(h, LB_ERR_ARG, "bad pore");
+    BInst &I = h->hinst[k];
+    const double t = std::ceil(4.0 * (radius * radius));
+    I.g.pore_axis = axis;
+    I.g.pore_t = (long long)t;
+    const double inner = std::sqrt(t) - 2.0 * std::sqrt(2.0) - 0.01;
+    I.g.pore_in = inner > 0 ? (long long)std::floor(inner * inner) : 0;
+    const int na = axis == 0 ? I.g.ny : I.g.nx, nb = axis == 2 ? I.g.ny : I.g.nz;
+    const int nl = axis == 0 ? I.g.nx : (axis == 1 ? I.g.ny : I.g.nz);
+    long long c = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < na; ++a) {
+            const long long da = 2LL * a + 1 - na, db = 2LL * b + 1 - nb;
+            if (da * da + db * db < I.g.pore_t) ++c;
+        }
+    h->nfluid[k] = c * nl;
+    return LB_OK;
+}
+
+lb_status lb_batch_add_raspberry(lb_batch_handle h, int k, const double *beads, int nbeads, const double X[3],
+                                 const double q[4], double mass, const double inertia[3], const double F_ext[3],
+                                 const double T_ext[3], int fixed, int *body_id) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    if (h->uploaded) return bfail(h, LB_ERR_STATE, "bodies must be added before the first step");
+    if (nbeads < 0 || (nbeads > 0 && !beads) || !X || !q || !inertia || !(mass > 0.0))
+        return bfail(h, LB_ERR_ARG, "bad raspberry arguments");
+    const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(qn > 0.0)) return bfail(h, LB_ERR_ARG, "quaternion must be non-zero");
+    Body b{};
+    for (int a = 0; a < 3; ++a) {
+        b.X[a] = X[a];
+        b.I[a] = inertia[a];
+        b.F_ext[a] = F_ext ? F_ext[a] : 0.0;
+        b.T_ext[a] = T_ext ? T_ext[a] : 0.0;
+    }
+    for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
+    b.mass = mass;
+    b.fixed = fixed ? 1 : 0;
+    b.inst = k;
+    const int id = (int)h->hb.size();
+    h->hb.push_back(b);
+    for (int j = 0; j < 3 * nbeads; ++j) h->hs.push_back(beads[j]);
+    for (int j = 0; j < nbeads; ++j) {
+        h->hbody_of.push_back(id);
+        h->hbead_rng.push_back(h->inst_beads[k] + j);
+    }
+    h->inst_beads[k] += nbeads;
+    if (body_id) *body_id = (int)h->inst_bodies[k].size();
+    h->inst_bodies[k].push_back(id);
+    return LB_OK;
+}
+
+lb_status lb_batch_step(lb_batch_handle h, int nsteps) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (nsteps < 0) return bfail(h, LB_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return LB_OK;
+    lb_status s = upload(h);
+    if (s != LB_OK) return s;
+    if (h->timing) return eager_steps(h, nsteps);
+    if (h->step & 1) {
+        if ((s = eager_steps(h, 1)) != LB_OK) return s;
+        --nsteps;
+    }
+    const int pairs = nsteps / 2;
+    if (pairs > 0) {
+        if ((s = ensure_graph(h)) != LB_OK) return s;
+        for (int r = 0; r < pairs; ++r) BCUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+        h->step += 2LL * pairs;
+    }
+    if (nsteps & 1) return eager_steps(h, 1);
+    return LB_OK;
+}
+
+lb_status lb_batch_forces(lb_batch_handle h, int k, int body, double F[3], double T[3]) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    if (body < 0 || body >= (int)h->inst_bodies[k].size()) return bfail(h, LB_ERR_ARG, "bad body id");
+    const int id = h->inst_bodies[k][body];
+    if (!h->uploaded) {
+        for (int a = 0; a < 3; ++a) { if (F) F[a] = 0; if (T) T[a] = 0; }
+        return LB_OK;
+    }
+    if (F) BCUDA(h, cudaMemcpyAsync(F, &h->db[id].F_tot[0], 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (T) BCUDA(h, cudaMemcpyAsync(T, &h->db[id].T_tot[0], 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_batch_get_body(lb_batch_handle h, int k, int body, double X[3], double V[3], double q[4], double w[3]) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    if (body < 0 || body >= (int)h->inst_bodies[k].size()) return bfail(h, LB_ERR_ARG, "bad body id");
+    const int id = h->inst_bodies[k][body];
+    Body b = h->hb[id];
+    if (h->uploaded) {
+        BCUDA(h, cudaMemcpyAsync(&b, &h->db[id], sizeof(Body), cudaMemcpyDeviceToHost, h->stream));
+        BCUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (X) X[a] = b.X[a];
+        if (V) V[a] = b.V[a];
+        if (w) w[a] = b.w[a];
+    }
+    if (q) for (int a = 0; a < 4; ++a) q[a] = b.q[a];
+    return LB_OK;
+}
+
+lb_status lb_batch_get_populations(lb_batch_handle h, int k, double *host, size_t n) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    const BInst &I = h->hinst[k];
+    if (!host || n != 19 * (size_t)I.g.N) return bfail(h, LB_ERR_ARG, "buffer must hold 19*N doubles");
+    double *tmp = nullptr;
+    if ((s = balloc(h, &tmp, sizeof(double) * n)) != LB_OK) return s;
+    h->dev_bytes -= sizeof(double) * n;
+    const bool odd = (h->step & 1) != 0;
+    const unsigned grid = (unsigned)((I.g.N + 255) / 256);
+    if (h->fp32) lbk::k_batch_gather<float><<<grid, 256, 0, h->stream>>>((const float *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
+    else lbk::k_batch_gather<double><<<grid, 256, 0, h->stream>>>((const double *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("lb_batch_get_populations: ") + cudaGetErrorString(e));
+    return LB_OK;
+}
+
+lb_status lb_batch_set_populations(lb_batch_handle h, int k, const double *host, size_t n) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    const BInst &I = h->hinst[k];
+    if (!host || n != 19 * (size_t)I.g.N) return bfail(h, LB_ERR_ARG, "buffer must hold 19*N doubles");
+    double *tmp = nullptr;
+    if ((s = balloc(h, &tmp, sizeof(double) * n)) != LB_OK) return s;
+    h->dev_bytes -= sizeof(double) * n;
+    const bool odd = (h->step & 1) != 0;
+    const unsigned grid = (unsigned)((I.g.N + 255) / 256);
+    cudaError_t e = cudaMemcpyAsync(tmp, host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        if (h->fp32) lbk::k_batch_scatter<float><<<grid, 256, 0, h->stream>>>((float *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
+        else lbk::k_batch_scatter<double><<<grid, 256, 0, h->stream>>>((double *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("lb_batch_set_populations: ") + cudaGetErrorString(e));
+    return LB_OK;
+}
+
+lb_status lb_batch_set_schedule(lb_batch_handle h, int tile_nodes, int blocks_per_sm, int order) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if ((tile_nodes != 64 && tile_nodes != 128 && tile_nodes != 256) || blocks_per_sm < 1 ||
+        blocks_per_sm * tile_nodes > 2048 || (order != 0 && order != 1))
+        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 2048, order 0/1");
+    h->TS = tile_nodes;
+    h->bpsm = blocks_per_sm;
+    h->order = order;
+    return rebuild_schedule(h);
+}
+
+lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], double *best_ms_per_step) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (trial_steps < 2) trial_steps = 2;
+    trial_steps &= ~1;   // keep the parity
+    lb_status s = upload(h);
+    if (s != LB_OK) return s;
+    // snapshot of everything a step changes
+    const size_t es = h->fp32 ? 4 : 8;
+    const size_t pbytes = es * 19 * (size_t)h->Ntot;
+    const int nb = (int)h->hb.size();
+    void *snap = nullptr;
+    Body *bsnap = nullptr;
+    double *fsnap[2] = {nullptr, nullptr};
+    unsigned char *tsnap[2] = {nullptr, nullptr};
+    const size_t fbytes = sizeof(double) * 3 * (size_t)h->Ftot;
+    if (cudaMalloc(&snap, pbytes) != cudaSuccess) { cudaGetLastError(); return bfail(h, LB_ERR_OOM, "no room for the autotune snapshot"); }
+    bool ok = true;
+    if (nb > 0) {
+        ok = cudaMalloc((void **)&bsnap, sizeof(Body) * nb) == cudaSuccess;
+        for (int k = 0; k < 2 && ok; ++k)
+            ok = cudaMalloc((void **)&fsnap[k], fbytes) == cudaSuccess && cudaMalloc((void **)&tsnap[k], (size_t)h->Ttot) == cudaSuccess;
+    }
+    auto release = [&]() {
+        cudaFree(snap);
+        if (bsnap) cudaFree(bsnap);
+        for (int k = 0; k < 2; ++k) { if (fsnap[k]) cudaFree(fsnap[k]); if (tsnap[k]) cudaFree(tsnap[k]); }
+    };
+    if (!ok) { cudaGetLastError(); release(); return bfail(h, LB_ERR_OOM, "no room for the autotune snapshot"); }
+    auto copy_state = [&](bool save) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(save ? snap : h->pool, save ? h->pool : snap, pbytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (nb > 0 && e == cudaSuccess) {
+            e = cudaMemcpyAsync(save ? (void *)bsnap : (void *)h->db, save ? (void *)h->db : (void *)bsnap, sizeof(Body) * nb, cudaMemcpyDeviceToDevice, h->stream);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(save ? (void *)fsnap[k] : (void *)h->Fbuf[k], save ? (void *)h->Fbuf[k] : (void *)fsnap[k], fbytes, cudaMemcpyDeviceToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(save ? (void *)tsnap[k] : (void *)h->tiles[k], save ? (void *)h->tiles[k] : (void *)tsnap[k], (size_t)h->Ttot, cudaMemcpyDeviceToDevice, h->stream);
+            }
+        }
+        return e;
+    };
+    unsigned long long step_saved = 0;
+    cudaError_t e = copy_state(true);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&step_saved, h->step_dev, sizeof(step_saved), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { release(); return bfail(h, LB_ERR_CUDA, std::string("autotune snapshot: ") + cudaGetErrorString(e)); }
+    const long long step_host = h->step;
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int tiles[3] = {64, 128, 256};
+    double best = 1e30;
+    int bt = h->TS, bb = h->bpsm, bo = h->order;
+    for (int ts : tiles)
+        for (int bps = 2; bps * ts <= 2048; bps *= 2)
+            for (int order = 0; order < 2; ++order) {
+                if ((s = lb_batch_set_schedule(h, ts, bps, order)) != LB_OK) break;
+                // warm-up pair, then timed pairs
+                if ((s = lb_batch_step(h, 2)) != LB_OK) break;
+                cudaEventRecord(e0, h->stream);
+                if ((s = lb_batch_step(h, trial_steps)) != LB_OK) break;
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / trial_steps < best) { best = ms / trial_steps; bt = ts; bb = bps; bo = order; }
+                // restore
+                e = copy_state(false);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(h->step_dev, &step_saved, sizeof(step_saved), cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+                h->step = step_host;
+                if (e != cudaSuccess) { s = bfail(h, LB_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(e)); break; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    h->timing = timing;
+    if (s != LB_OK) return s;
+    s = lb_batch_set_schedule(h, bt, bb, bo);
+    if (chosen) { chosen[0] = bt; chosen[1] = bb; chosen[2] = bo; }
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return s;
+}
+
+lb_status lb_batch_info(lb_batch_handle h, long long *total_nodes, long long *step, int schedule[3]) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (total_nodes) *total_nodes = h->Ntot;
+    if (step) *step = h->step;
+    if (schedule) { schedule[0] = h->TS; schedule[1] = h->bpsm; schedule[2] = h->order; }
+    return LB_OK;
+}
+
+lb_status lb_batch_set_timing(lb_batch_handle h, int on) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    h->timing = on != 0;
+    return LB_OK;
+}
+
+lb_status lb_batch_kernel_time(lb_batch_handle h, double *total_ms, long long *launches) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        BCUDA(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+        h->timed_ms += ms;
+        h->timed_n += 1;
+    }
+    h->ev_used = 0;
+    if (total_ms) *total_ms = h->timed_ms;
+    if (launches) *launches = h->timed_n;
+    h->timed_ms = 0.0;
+    h->timed_n = 0;
+    return LB_OK;
+}
+
+}  // extern "C"

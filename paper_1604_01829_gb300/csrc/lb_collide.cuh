@@ -13,8 +13,8 @@ namespace lbk {
 // (3c^2-5)c, (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz, 3c^4-6c^2+1,
 // (2c^2-3)(3cx^2-c^2), (2c^2-3)(cy^2-cz^2), with norms b_k = sum w e_k^2.
 template <typename R, bool DEV, int COLL, bool NOISE>
-__device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const CollParams<R> &a,
-                                        const FluidArgs &fa, uint32_t node, uint32_t step) {
+__device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const CollParams<R> &a, uint2 key,
+                                        uint32_t instance, uint32_t node, uint32_t step) {
     const R s1 = f[1] + f[2], d1 = f[1] - f[2];
     const R s3 = f[3] + f[4], d3 = f[3] - f[4];
     const R s5 = f[5] + f[6], d5 = f[5] - f[6];
@@ -107,11 +107,10 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Coll
         // 15 non-conserved modes, variance 3 rho kT b_k (1 - g_k^2); kn_k holds
         // c_k sqrt(3 kT b_k (1 - g_k^2)) (times sqrt(12) 2^-32 in FP32, where
         // the variate is the centred integer converted once)
-        const uint2 key = make_uint2(fa.key0, fa.key1);
-        const uint4 r0 = philox4x32_10(make_uint4(node, step, fa.instance, 0u), key);
-        const uint4 r1 = philox4x32_10(make_uint4(node, step, fa.instance, 1u), key);
-        const uint4 r2 = philox4x32_10(make_uint4(node, step, fa.instance, 2u), key);
-        const uint4 r3 = philox4x32_10(make_uint4(node, step, fa.instance, 3u), key);
+        const uint4 r0 = philox4x32_10(make_uint4(node, step, instance, 0u), key);
+        const uint4 r1 = philox4x32_10(make_uint4(node, step, instance, 1u), key);
+        const uint4 r2 = philox4x32_10(make_uint4(node, step, instance, 2u), key);
+        const uint4 r3 = philox4x32_10(make_uint4(node, step, instance, 3u), key);
         R sr;
         if constexpr (sizeof(R) == 4) asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sr) : "f"(rho));
         else sr = sqrt(rho);
@@ -178,7 +177,7 @@ template <int COLL, bool NOISE>
 __device__ __forceinline__ void collide_fp32(float (&f)[19], float Fx, float Fy, float Fz,
                                              const CollParams<float> &a, const FluidArgs &fa, uint32_t node,
                                              uint32_t step) {
-    collide<float, true, COLL, NOISE>(f, Fx, Fy, Fz, a, fa, node, step);
+    collide<float, true, COLL, NOISE>(f, Fx, Fy, Fz, a, make_uint2(fa.key0, fa.key1), fa.instance, node, step);
 }
 
 }  // namespace lbk

@@ -1,0 +1,132 @@
+// Friction coupling of one raspberry bead to the fluid (Ustach & Faller,
+// arXiv:1604.01829, Sec. 1.1, Eq. (latticeboltzmannfriction)), shared by
+// the single-lattice and batched coupling kernels.
+#pragma once
+
+#include "lb_rigid.cuh"
+
+namespace lbk {
+
+// Pre-collision density and momentum of one node in the compute precision R.
+template <typename R, typename T>
+__device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int y, int z, long long n,
+                                           bool odd, R rho0, R &rho, R j[3]) {
+    R s = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const R v = (R)load_pre(A, g, x, y, z, n, i, odd);
+        s += v;
+        if (cx(i)) jx += cx(i) * v;
+        if (cy(i)) jy += cy(i) * v;
+        if (cz(i)) jz += cz(i) * v;
+    }
+    rho = sizeof(T) == 4 ? rho0 + s : s;
+    j[0] = jx; j[1] = jy; j[2] = jz;
+}
+
+// Eight lanes per bead, one per surrounding node: lane 0 of the group forms
+// the virtual site, every lane interpolates its node's velocity and spreads
+// its share of -F_b, the group reduces by shuffles. Node arithmetic runs in
+// the storage precision (FP32 deviations or FP64), bead and body sums in FP64.
+// k: bead index into a.s / a.bead_body / a.F_bead; k_rng: the bead's index
+// within its own lattice (Philox counter word); c: this lane's corner 0-7.
+// All 32 lanes of the warp must call it (shuffles), active or not.
+template <typename T>
+__device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rng, int c, int lane, bool active) {
+    using R = T;
+    const Geom &g = a.g;
+    const T *A = static_cast<const T *>(a.f);
+    const int body = active ? a.bead_body[k] : -1;
+
+    double rel[3] = {0, 0, 0}, r[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    if (active && c == 0) {
+        const Body &B = a.bodies[body];
+        const double s[3] = {a.s[3 * k], a.s[3 * k + 1], a.s[3 * k + 2]};
+        double wxr[3];
+        for (int q = 0; q < 3; ++q) rel[q] = B.R[3 * q] * s[0] + B.R[3 * q + 1] * s[1] + B.R[3 * q + 2] * s[2];
+        for (int q = 0; q < 3; ++q) r[q] = B.X[q] + rel[q];
+        cross3(B.wl, rel, wxr);
+        for (int q = 0; q < 3; ++q) v[q] = B.V[q] + wxr[q];
+    }
+    for (int q = 0; q < 3; ++q) r[q] = __shfl_sync(0xffffffffu, r[q], 0, 8);
+
+    // this lane's node among the 8 around r (centres at integer + 1/2), periodic
+    const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    int xyz[3];
+    double wt = 1.0;
+    for (int q = 0; q < 3; ++q) {
+        const double tq = r[q] - 0.5;
+        const double fl = floor(tq);
+        const double fr = tq - fl;
+        int b0 = (int)fl % n3[q];
+        if (b0 < 0) b0 += n3[q];
+        xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
+        wt *= o[q] ? fr : 1.0 - fr;
+    }
+    const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
+    const bool fluid = active && !is_wall(g, xyz[0], xyz[1], xyz[2]);
+    double ub[3] = {0.0, 0.0, 0.0};
+    if (fluid) {                         // wall nodes carry u = 0
+        R rho, j[3];
+        node_rho_j<R>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (R)a.rho0, rho, j);
+        const R ir = R(1) / rho;
+        const R ux = (j[0] + R(0.5) * (R)(a.gforce[0] + a.Fprev[n])) * ir;
+        const R uy = (j[1] + R(0.5) * (R)(a.gforce[1] + a.Fprev[g.N + n])) * ir;
+        const R uz = (j[2] + R(0.5) * (R)(a.gforce[2] + a.Fprev[2 * g.N + n])) * ir;
+        ub[0] = wt * (double)ux;
+        ub[1] = wt * (double)uy;
+        ub[2] = wt * (double)uz;
+    }
+    for (int off = 1; off < 8; off <<= 1)
+        for (int q = 0; q < 3; ++q) ub[q] += __shfl_xor_sync(0xffffffffu, ub[q], off, 8);
+
+    // Eq. (latticeboltzmannfriction): F_b = -gamma (v - u(r)) + f_s
+    double Fb[3] = {0.0, 0.0, 0.0};
+    if (active && c == 0) {
+        double fs[3] = {0.0, 0.0, 0.0};
+        if (a.noise_amp > 0.0) {
+            const uint32_t step = (uint32_t)(*a.step_base) + a.step_off;
+            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k_rng, step, a.instance, 4u), make_uint2(a.key0, a.key1));
+            fs[0] = a.noise_amp * unit_uniform_d(rr.x);
+            fs[1] = a.noise_amp * unit_uniform_d(rr.y);
+            fs[2] = a.noise_amp * unit_uniform_d(rr.z);
+        }
+        for (int q = 0; q < 3; ++q) Fb[q] = -a.gamma * (v[q] - ub[q]) + fs[q];
+        for (int q = 0; q < 3; ++q) a.F_bead[3 * k + q] = Fb[q];
+    }
+    for (int q = 0; q < 3; ++q) Fb[q] = __shfl_sync(0xffffffffu, Fb[q], 0, 8);
+
+    // spread -w F_b onto this lane's node; a wall node takes nothing
+    if (fluid) {
+        atomicAdd(&a.Fcur[n], -wt * Fb[0]);
+        atomicAdd(&a.Fcur[g.N + n], -wt * Fb[1]);
+        atomicAdd(&a.Fcur[2 * g.N + n], -wt * Fb[2]);
+        a.tiles_cur[tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty)] = 1;
+    }
+
+    // force and torque on the body: sum the (up to 4) beads of this warp
+    // that belong to the warp's first body, atomics for the others
+    double FT[6] = {0, 0, 0, 0, 0, 0};
+    if (active && c == 0) {
+        double tq[3];
+        cross3(rel, Fb, tq);
+        for (int q = 0; q < 3; ++q) { FT[q] = Fb[q]; FT[3 + q] = tq[q]; }
+    }
+    const int b_first = __shfl_sync(0xffffffffu, body, 0);
+    const bool lead = active && c == 0;
+    const bool same = lead && body == b_first;
+    double red[6];
+    for (int q = 0; q < 6; ++q) red[q] = same ? FT[q] : 0.0;
+    for (int q = 0; q < 6; ++q) {
+        red[q] += __shfl_xor_sync(0xffffffffu, red[q], 8);
+        red[q] += __shfl_xor_sync(0xffffffffu, red[q], 16);
+    }
+    if (lane == 0 && b_first >= 0)
+        for (int q = 0; q < 6; ++q) atomicAdd(&a.bodies[b_first].acc[q], red[q]);
+    if (lead && !same)
+        for (int q = 0; q < 6; ++q) atomicAdd(&a.bodies[body].acc[q], FT[q]);
+}
+
+
+}  // namespace lbk

@@ -90,8 +90,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
     uint32_t step = 0;
     if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;
 
-    if constexpr (sizeof(R) == 4) collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pf, a, (uint32_t)n, step);
-    else collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pd, a, (uint32_t)n, step);
+    const uint2 key = make_uint2(a.key0, a.key1);
+    if constexpr (sizeof(R) == 4) collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pf, key, a.instance, (uint32_t)n, step);
+    else collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pd, key, a.instance, (uint32_t)n, step);
 
     if (!ODD) {
 #pragma unroll

@@ -52,7 +52,8 @@ struct Body {
     double R[9];                     // rotation of the running step (row-major, lab = R body)
     double wl[3];                    // lab-frame omega of the running step
     double mass, I[3];
-    int fixed, pad;
+    int fixed;
+    int inst;                        // instance of a batch (0 for a single lattice)
 };
 
 struct CoupleArgs {

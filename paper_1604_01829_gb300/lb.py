@@ -68,8 +68,26 @@ _SIGS = {
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
 }
 
+_BSIGS = {
+    "lb_batch_create": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)],
+    "lb_batch_destroy": [C.c_void_p],
+    "lb_batch_set_pore": [C.c_void_p, C.c_int, C.c_double, C.c_int],
+    "lb_batch_add_raspberry": [C.c_void_p, C.c_int, _dp, C.c_int, _dp, _dp, C.c_double, _dp, _dp, _dp, C.c_int, _ip],
+    "lb_batch_step": [C.c_void_p, C.c_int],
+    "lb_batch_forces": [C.c_void_p, C.c_int, C.c_int, _dp, _dp],
+    "lb_batch_get_body": [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp],
+    "lb_batch_get_populations": [C.c_void_p, C.c_int, _dp, C.c_size_t],
+    "lb_batch_set_populations": [C.c_void_p, C.c_int, _dp, C.c_size_t],
+    "lb_batch_set_schedule": [C.c_void_p, C.c_int, C.c_int, C.c_int],
+    "lb_batch_autotune": [C.c_void_p, C.c_int, _ip, _dp],
+    "lb_batch_info": [C.c_void_p, _llp, _llp, _ip],
+    "lb_batch_set_timing": [C.c_void_p, C.c_int],
+    "lb_batch_kernel_time": [C.c_void_p, _dp, _llp],
+}
+
 # every symbol include/lb.h declares
-EXPORTS = sorted(list(_SIGS) + ["lb_last_error", "lb_status_string", "lb_lattice", "lb_moments_noalloc"])
+EXPORTS = sorted(list(_SIGS) + list(_BSIGS) + ["lb_last_error", "lb_status_string", "lb_lattice",
+                                                "lb_moments_noalloc", "lb_batch_last_error"])
 
 
 def load():
@@ -82,10 +100,12 @@ def load():
                     f"CUDA library {LIB_PATH} is missing: build it with "
                     "paper_1604_01829_gb300.build.build() (nvcc, sm_103a)")
             L = C.CDLL(LIB_PATH)
-            for name, args in _SIGS.items():
+            for name, args in list(_SIGS.items()) + list(_BSIGS.items()):
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = C.c_int
+            L.lb_batch_last_error.argtypes = [C.c_void_p]
+            L.lb_batch_last_error.restype = C.c_char_p
             L.lb_last_error.argtypes = [C.c_void_p]
             L.lb_last_error.restype = C.c_char_p
             L.lb_status_string.argtypes = [C.c_int]
@@ -289,3 +309,110 @@ def from_workload(w, stream=None, precision=None):
     for b in w.bodies:
         lb.lb_add_raspberry(b.beads, b.X, b.q, b.mass, b.inertia, b.F_ext, b.T_ext, b.fixed)
     return lb
+
+
+def _bcheck(h, status):
+    if status != LB_OK:
+        msg = load().lb_batch_last_error(h)
+        raise LBError(status, msg.decode() if msg else load().lb_status_string(status).decode())
+
+
+class LBBatch:
+    """A batch of independent lattices (lb_batch_* of include/lb.h)."""
+
+    def __init__(self, param_dicts, stream=None):
+        L = load()
+        arr = (lb_params * len(param_dicts))(*[make_params(**d) for d in param_dicts])
+        self.sizes = [d["nx"] * d["ny"] * d["nz"] for d in param_dicts]
+        h = C.c_void_p()
+        st = L.lb_batch_create(arr, len(param_dicts), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != LB_OK:
+            raise LBError(st, L.lb_batch_last_error(None).decode())
+        self.h = h
+        self.n = len(param_dicts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lb_batch_set_pore(self, inst, radius, axis=2):
+        _bcheck(self.h, load().lb_batch_set_pore(self.h, int(inst), float(radius), int(axis)))
+
+    def lb_batch_add_raspberry(self, inst, beads, X, q=(1, 0, 0, 0), mass=1.0, inertia=(1, 1, 1),
+                               F_ext=None, T_ext=None, fixed=False):
+        b = np.ascontiguousarray(beads, dtype=np.float64).reshape(-1)
+        bid = C.c_int(-1)
+        _bcheck(self.h, load().lb_batch_add_raspberry(
+            self.h, int(inst), _d(b), b.size // 3, _d(_vec(X, 3)), _d(_vec(q, 4)), float(mass),
+            _d(_vec(inertia, 3)), _d(_vec(F_ext, 3)), _d(_vec(T_ext, 3)), int(bool(fixed)), C.byref(bid)))
+        return bid.value
+
+    def lb_batch_step(self, n=1):
+        _bcheck(self.h, load().lb_batch_step(self.h, int(n)))
+
+    def lb_batch_forces(self, inst, body=0):
+        F, T = np.zeros(3), np.zeros(3)
+        _bcheck(self.h, load().lb_batch_forces(self.h, int(inst), int(body), _d(F), _d(T)))
+        return F, T
+
+    def lb_batch_get_body(self, inst, body=0):
+        X, V, q, w = np.zeros(3), np.zeros(3), np.zeros(4), np.zeros(3)
+        _bcheck(self.h, load().lb_batch_get_body(self.h, int(inst), int(body), _d(X), _d(V), _d(q), _d(w)))
+        return dict(X=X, V=V, q=q, w=w)
+
+    def lb_batch_get_populations(self, inst):
+        out = np.zeros(19 * self.sizes[inst])
+        _bcheck(self.h, load().lb_batch_get_populations(self.h, int(inst), _d(out), out.size))
+        return out.reshape(19, -1)
+
+    def lb_batch_set_populations(self, inst, f):
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        _bcheck(self.h, load().lb_batch_set_populations(self.h, int(inst), _d(a), a.size))
+
+    def lb_batch_set_schedule(self, tile_nodes=128, blocks_per_sm=8, order=0):
+        _bcheck(self.h, load().lb_batch_set_schedule(self.h, int(tile_nodes), int(blocks_per_sm), int(order)))
+
+    def lb_batch_autotune(self, trial_steps=10):
+        ch = (C.c_int * 3)()
+        ms = C.c_double()
+        _bcheck(self.h, load().lb_batch_autotune(self.h, int(trial_steps), ch, C.byref(ms)))
+        return list(ch), ms.value
+
+    def lb_batch_info(self):
+        n, st = C.c_longlong(), C.c_longlong()
+        sch = (C.c_int * 3)()
+        _bcheck(self.h, load().lb_batch_info(self.h, C.byref(n), C.byref(st), sch))
+        return dict(total_nodes=n.value, step=st.value, schedule=list(sch))
+
+    def lb_batch_set_timing(self, on=True):
+        _bcheck(self.h, load().lb_batch_set_timing(self.h, int(bool(on))))
+
+    def lb_batch_kernel_time(self):
+        ms, n = C.c_double(), C.c_longlong()
+        _bcheck(self.h, load().lb_batch_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+
+def batch_from_workloads(workloads, stream=None, precision=None):
+    """An LBBatch holding a list of workloads.Workload instances."""
+    dicts = []
+    for w in workloads:
+        d = dict(w.params)
+        if precision is not None:
+            d["precision"] = precision
+        d.update(nx=w.nx, ny=w.ny, nz=w.nz)
+        dicts.append(d)
+    B = LBBatch(dicts, stream=stream)
+    for k, w in enumerate(workloads):
+        if w.pore is not None:
+            B.lb_batch_set_pore(k, *w.pore)
+        for b in w.bodies:
+            B.lb_batch_add_raspberry(k, b.beads, b.X, b.q, b.mass, b.inertia, b.F_ext, b.T_ext, b.fixed)
+    return B

@@ -1,0 +1,138 @@
+"""Batched lattices (lb_batch_*): every instance of a batch of uneven
+periodic and pore lattices, with and without raspberries, against the FP64
+oracle run on that instance alone; schedule and autotuner leave results
+unchanged. Tolerances as in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+from helpers import W19, oracle_kw, perturbed_populations
+from oracle import oracle as O
+from paper_1604_01829_gb300 import workloads as Wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 2e-5}
+MRT = dict(collision=1, gamma_shear=-0.45, gamma_bulk=-0.2, gamma_odd=0.3, gamma_even=-0.1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1604_01829_gb300 import build
+    build.build()
+
+
+def _cases(noise):
+    """(params, pore, bodies) of five uneven instances."""
+    kT = dict(kT=1e-4) if noise else {}
+    g = Wl.paper_gamma_to_lattice(50.0)
+    sph = Wl.sphere_raspberry(2.0)
+    ell = Wl.ellipsoid_raspberry(3.0, 1.5, 1.5, seed=4)
+    return [
+        (dict(nx=20, ny=11, nz=9, seed=1, body_force=(1e-5, 0, 0), **MRT, **kT), None, []),
+        (dict(nx=18, ny=18, nz=7, seed=2, gamma_bead=g, **MRT, **kT), (7.2, 2),
+         [dict(beads=sph, X=[9.4, 8.7, 3.3], mass=34.0, inertia=(50, 50, 50), F_ext=(0, 0, 1e-3))]),
+        (dict(nx=13, ny=16, nz=17, seed=3, gamma_bead=g, compensate_force=1, instance=7, **MRT, **kT), None,
+         [dict(beads=ell, X=[6.2, 8.1, 8.9], q=[0.9, 0.1, 0.3, -0.2], mass=40.0, inertia=(20, 50, 50),
+               F_ext=(5e-4, 0, 0))]),
+        (dict(nx=9, ny=14, nz=14, seed=4, **MRT, **kT), (5.5, 0), []),
+        (dict(nx=24, ny=8, nz=12, seed=5, gamma_bead=g, **MRT, **kT), None,
+         [dict(beads=sph, X=[5.1, 4.3, 6.2], fixed=True, V=(0, 0, 0)),
+          dict(beads=sph, X=[17.3, 4.1, 5.8], mass=34.0, inertia=(50, 50, 50), F_ext=(0, 1e-3, 0))]),
+    ]
+
+
+def _build(cases, precision):
+    from paper_1604_01829_gb300 import lb
+    B = lb.LBBatch([dict(c[0], precision=precision) for c in cases])
+    orcs = []
+    for k, (p, pore, bodies) in enumerate(cases):
+        o = O.OracleLB(p["nx"], p["ny"], p["nz"], **oracle_kw(p))
+        if pore is not None:
+            B.lb_batch_set_pore(k, *pore)
+            o.set_pore(*pore)
+        f = perturbed_populations(p["nx"] * p["ny"] * p["nz"], seed=30 + k)
+        B.lb_batch_set_populations(k, f)
+        o.set_populations(f)
+        for b in bodies:
+            q = b.get("q", [1, 0, 0, 0])
+            B.lb_batch_add_raspberry(k, b["beads"], b["X"], q, b.get("mass", 1.0), b.get("inertia", (1, 1, 1)),
+                                     b.get("F_ext"), None, b.get("fixed", False))
+            o.add_raspberry(b["beads"], b["X"], np.asarray(q) / np.linalg.norm(q), b.get("mass", 1.0),
+                            b.get("inertia", (1, 1, 1)), b.get("F_ext", (0, 0, 0)), (0, 0, 0),
+                            b.get("fixed", False))
+        orcs.append(o)
+    return B, orcs
+
+
+def _errors(B, orcs, cases):
+    out = []
+    for k, o in enumerate(orcs):
+        fg = B.lb_batch_get_populations(k)
+        fo = o.populations()
+        fl = np.ones(fg.shape[1], bool) if o.mask is None else o.mask == 0
+        out.append(float(np.max(np.abs(fg[:, fl] - fo[:, fl]) / W19[:, None])))
+        for j in range(len(cases[k][2])):
+            F, _ = B.lb_batch_forces(k, j)
+            Fo = o.body(j)["F"]
+            out.append(float(np.abs(F - Fo).max() / max(np.abs(Fo).max(), 1e-30)) * 1e-1)
+    return out
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("noise", [False, True])
+def test_batch_matches_oracle_per_instance(precision, noise):
+    cases = _cases(noise)
+    B, orcs = _build(cases, precision)
+    for n in (1, 2, 5):          # odd counts mix eager steps with the two-step graph
+        B.lb_batch_step(n)
+        for o in orcs:
+            o.step(n)
+        errs = _errors(B, orcs, cases)
+        assert max(errs) <= TOL[precision], errs
+
+
+@pytest.mark.parametrize("schedule", [(64, 4, 0), (128, 16, 1), (256, 8, 0), (256, 2, 1)])
+def test_batch_schedule_does_not_change_results(schedule):
+    cases = _cases(True)
+    B, orcs = _build(cases, 32)
+    B.lb_batch_set_schedule(*schedule)
+    B.lb_batch_step(4)
+    for o in orcs:
+        o.step(4)
+    assert max(_errors(B, orcs, cases)) <= TOL[32]
+
+
+def test_autotune_restores_state_and_picks_a_valid_schedule():
+    cases = _cases(False)
+    B, orcs = _build(cases, 64)
+    B.lb_batch_step(3)
+    for o in orcs:
+        o.step(3)
+    before = [B.lb_batch_get_populations(k) for k in range(len(cases))]
+    chosen, ms = B.lb_batch_autotune(4)
+    assert chosen[0] in (64, 128, 256) and chosen[1] >= 1 and chosen[2] in (0, 1) and ms > 0
+    info = B.lb_batch_info()
+    assert info["step"] == 3 and info["schedule"] == chosen
+    for k in range(len(cases)):
+        assert np.array_equal(B.lb_batch_get_populations(k), before[k])
+    B.lb_batch_step(3)
+    for o in orcs:
+        o.step(3)
+    assert max(_errors(B, orcs, cases)) <= TOL[64]
+
+
+def test_batch_instance_equals_single_handle():
+    from paper_1604_01829_gb300 import lb
+    cases = _cases(True)
+    B, _ = _build(cases, 64)
+    k = 2
+    p, pore, bodies = cases[k]
+    kw = {key: v for key, v in p.items() if key not in ("nx", "ny", "nz")}
+    S = lb.LB(p["nx"], p["ny"], p["nz"], precision=64, **kw)
+    S.lb_set_populations(perturbed_populations(p["nx"] * p["ny"] * p["nz"], seed=30 + k))
+    b = bodies[0]
+    S.lb_add_raspberry(b["beads"], b["X"], b["q"], b["mass"], b["inertia"], b["F_ext"])
+    B.lb_batch_step(6)
+    S.lb_step(6)
+    assert np.abs(B.lb_batch_get_populations(k) - S.lb_get_populations()).max() <= 1e-13
+    assert np.abs(B.lb_batch_get_body(k)["X"] - S.lb_get_body(0)["X"]).max() <= 1e-13
