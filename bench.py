@@ -236,6 +236,8 @@ def run_ours(args, ws, rank, local):
                      "kernel_achieved_gbs": round(fp64_ach, 1),
                      "frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8}
 
+    batched = None if args.skip_batched else measure_batched(args, torch, lb, barrier_max, ws)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(args.cpu_seconds)
@@ -270,12 +272,83 @@ def run_ours(args, ws, rank, local):
                     "h2d_bytes_per_step": 2 * 3 * 8 * nb, "d2h_bytes_per_step": 2 * 3 * 8 * nb},
             "gpu_launches": 3 * K + 2,
             "fp64": fp64_line,
+            "batched": batched,
             "clocks": main["clocks"],
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_batched(args, torch, lb, barrier_max, ws):
+    """256 independent instances of uneven size (cubic 24-64 periodic boxes and
+    cylindrical pores R 8-28, each with one raspberry), FP32 MRT, advanced
+    together: autotuned schedule, two-step CUDA graph. Compared with the same
+    instances stepped one handle after another."""
+    from paper_1604_01829_gb300 import workloads as W
+    ws_list = W.batched_instances(args.batch_instances)
+    stream = torch.cuda.Stream()
+    B = lb.batch_from_workloads(ws_list, stream=stream.cuda_stream)
+    chosen, _ = B.lb_batch_autotune(10)
+    nodes = B.lb_batch_info()["total_nodes"]
+    K = args.batch_steps
+    B.lb_batch_step(4)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.lb_batch_step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = barrier_max(e0.elapsed_time(e1))
+    # fluid kernel alone (eager launches with events) for the roofline
+    B.lb_batch_set_timing(True)
+    B.lb_batch_step(20)
+    kms, kn = B.lb_batch_kernel_time()
+    B.lb_batch_set_timing(False)
+    fluid = 0
+    for w in ws_list:
+        if w.pore is None:
+            fluid += w.nodes
+        else:
+            R, ax = w.pore
+            n2 = [w.nx, w.ny, w.nz]
+            a1, a2 = [d for d in range(3) if d != ax]
+            c = 0
+            for i in range(n2[a1]):
+                for j in range(n2[a2]):
+                    if (2 * i + 1 - n2[a1]) ** 2 + (2 * j + 1 - n2[a2]) ** 2 < math.ceil(4 * R * R):
+                        c += 1
+            fluid += c * n2[ax]
+    B.close()
+    # the same instances one handle after another (eager launches)
+    K1 = max(2, K // 10)
+    handles = [lb.from_workload(w, stream=stream.cuda_stream) for w in ws_list]
+    for L in handles:
+        L.lb_step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for L in handles:
+        L.lb_step(K1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = barrier_max(e0.elapsed_time(e1))
+    for L in handles:
+        L.close()
+    peak, kind = measured_peak()
+    ach = 152.0 * fluid / (kms / max(kn, 1) * 1e-3) / 1e9
+    return {"workload": f"{len(ws_list)} instances (cubic 24-64 periodic, pores R 8-28), one raspberry each, "
+                        f"FP32 MRT, kT=0", "instances": len(ws_list), "nodes": nodes, "fluid_nodes": fluid,
+            "steps": K, "ms_per_step": round(ms / K, 4),
+            "value": round(nodes * ws * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "fluid_mlups": round(fluid * ws * K / (ms * 1e-3) / 1e6, 1),
+            "one_by_one": {"steps": K1, "ms_per_step": round(ms1 / K1, 4),
+                           "value": round(nodes * ws * K1 / (ms1 * 1e-3) / 1e6, 1)},
+            "speedup_vs_one_by_one": round((ms1 / K1) / (ms / K), 2),
+            "schedule": {"tile_nodes": chosen[0], "blocks_per_sm": chosen[1], "order": chosen[2]},
+            "fluid_kernel": {"ms": round(kms / max(kn, 1), 4), "achieved_gbs": round(ach, 1),
+                             "frac": round(ach / peak, 4), "peak_kind": kind}}
 
 
 def oracle_sample(seconds):
@@ -345,6 +418,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--lattice", type=int, default=256, help="cubic lattice edge (profiling cases)")
     ap.add_argument("--bodies", type=int, default=64, help="number of ellipsoids (profiling cases)")
+    ap.add_argument("--skip-batched", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=1000)
     args = ap.parse_args()
     global ARGS
     ARGS = args

@@ -22,10 +22,17 @@
 #include "lb_collide.cuh"
 #include "lb_couple.cuh"
 
+// resident 256-thread CTAs per SM requested for the FP32 fluid kernel
+#ifndef LB_BATCH_MINB
+#define LB_BATCH_MINB 4
+#endif
+
 namespace lbk {
 
 struct BInst {
     Geom g;
+    uint32_t mx, my;             // ceil(2^32 / nx), ceil(2^32 / ny) for exact quotients (fastdiv)
+    int fastdiv;                 // 1 when n * nx and (n / nx) * ny stay below 2^32 for every node
     long long off;               // element offset of plane 0 in the population pool
     long long foff;              // offset of this instance's [3][N] block in a force pool
     long long toff;              // offset of its tile flags
@@ -41,7 +48,10 @@ struct BInst {
 struct BatchArgs {
     const BInst *inst;
     const int *tile_start;       // n + 1: first work tile of each instance
+    const int *tile_inst;        // instance of each work tile
     int n, ntiles, chunk, order;
+    CollParams<double> pd;       // collision constants shared by all instances (COMMON kernels)
+    CollParams<float> pf;
     void *pool;
     const double *F;             // spread force of this step (pool), nullptr without bodies
     const unsigned char *tiles;
@@ -60,8 +70,25 @@ __device__ __forceinline__ int find_instance(const int *start, int n, int t) {
     return lo;
 }
 
-template <typename T, int COLL, bool NOISE, bool ODD>
-__global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs a) {
+__constant__ signed char kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                       {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                       {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                       {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+// 18-bit mask of the links whose upstream node is a wall node (rolled loop:
+// only nodes next to a pore wall come here)
+__device__ __noinline__ uint32_t upstream_wall_mask(const Geom &g, int x, int y, int z) {
+    uint32_t m = 0;
+#pragma unroll 1
+    for (int i = 1; i < 19; ++i) {
+        const int xs = wrapm(x - kC[i][0], g.nx), ys = wrapm(y - kC[i][1], g.ny), zs = wrapm(z - kC[i][2], g.nz);
+        if (pore_r2(g, xs, ys, zs) >= g.pore_t) m |= 1u << i;
+    }
+    return m;
+}
+
+template <typename T, int COLL, bool NOISE, bool ODD, bool COMMON>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_batch_collide(const BatchArgs a) {
     using R = T;
     constexpr bool DEV = sizeof(T) == 4;
     for (int it = 0;; ++it) {
@@ -72,69 +99,80 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs a) {
             t = blockIdx.x * a.chunk + it;
         }
         if (t >= a.ntiles) break;
-        const int k = find_instance(a.tile_start, a.n, t);
+        const int k = __ldg(a.tile_inst + t);
         const BInst &I = a.inst[k];
         const Geom g = I.g;
-        const long long n = (long long)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
-        if (n >= g.N) continue;
-        const int x = (int)(n % g.nx);
-        const long long r = n / g.nx;
-        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-        bool near_wall = false;
-        if (g.pore_axis >= 0) {
-            const long long r2 = pore_r2(g, x, y, z);
-            if (r2 >= g.pore_t) continue;
-            near_wall = r2 >= g.pore_in;
+        const uint32_t N = (uint32_t)g.N;
+        const uint32_t n = (uint32_t)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
+        if (n >= N) continue;
+        uint32_t r, z;
+        if (I.fastdiv) {
+            r = __umulhi(n, I.mx);
+            z = __umulhi(r, I.my);
+        } else {
+            r = n / (uint32_t)g.nx;
+            z = r / (uint32_t)g.ny;
         }
-        T *A = static_cast<T *>(a.pool) + I.off;
-        const long long N = g.N;
+        const int x = (int)(n - r * (uint32_t)g.nx), y = (int)(r - z * (uint32_t)g.ny);
+        // bit i set: the upstream neighbour x - c_i is a wall node
+        uint32_t wall_up = 0;
+        if (g.pore_axis >= 0) {
+            const long long r2 = pore_r2(g, x, y, (int)z);
+            if (r2 >= g.pore_t) continue;
+            if (ODD && r2 >= g.pore_in) wall_up = upstream_wall_mask(g, x, y, (int)z);
+        }
+        // 32-bit element indices into the pool (the pool holds < 2^32 elements)
+        T *P = static_cast<T *>(a.pool);
+        const uint32_t base = (uint32_t)I.off;
         const int nxy = g.nx * g.ny;
         const int xo[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
         const int yo[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.nx, y * g.nx, (y == g.ny - 1 ? 0 : y + 1) * g.nx};
-        const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * nxy, z * nxy, (z == g.nz - 1 ? 0 : z + 1) * nxy};
+        const int zo[3] = {((int)z == 0 ? g.nz - 1 : (int)z - 1) * nxy, (int)z * nxy,
+                           ((int)z == g.nz - 1 ? 0 : (int)z + 1) * nxy};
+        auto at = [&](int i, uint32_t node) -> T & { return P[base + (uint32_t)i * N + node]; };
         R f[19];
         if (!ODD) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) f[i] = A[i * N + n];
+            for (int i = 0; i < 19; ++i) f[i] = at(i, n);
         } else {
-            f[0] = A[n];
+            f[0] = at(0, n);
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
-                const long long src = xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)];
-                if (near_wall) {
-                    const int ys = (y - cy(i) + g.ny) % g.ny, zs = (z - cz(i) + g.nz) % g.nz;
-                    if (pore_r2(g, xo[1 - cx(i)], ys, zs) >= g.pore_t) { f[i] = A[i * N + n]; continue; }
-                }
-                f[i] = A[opp(i) * N + src];
+                const uint32_t src = (uint32_t)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]);
+                if ((wall_up >> i) & 1u) f[i] = at(i, n);
+                else f[i] = at(opp(i), src);
             }
         }
         R Fx, Fy, Fz;
         if constexpr (DEV) { Fx = I.gf[0]; Fy = I.gf[1]; Fz = I.gf[2]; }
         else { Fx = I.gd[0]; Fy = I.gd[1]; Fz = I.gd[2]; }
-        if (a.tiles && a.tiles[I.toff + tile_of(x, y, z, I.ntx, I.nty)]) {
+        if (a.tiles && a.tiles[I.toff + tile_of(x, y, (int)z, I.ntx, I.nty)]) {
             const double *Fn = a.F + I.foff;
             Fx += (R)Fn[n];
-            Fy += (R)Fn[N + n];
-            Fz += (R)Fn[2 * N + n];
+            Fy += (R)Fn[(size_t)N + n];
+            Fz += (R)Fn[2 * (size_t)N + n];
         }
         uint32_t step = 0;
         if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;
         const uint2 key = make_uint2(I.key0, I.key1);
-        if constexpr (DEV) collide<R, true, COLL, NOISE>(f, Fx, Fy, Fz, I.pf, key, I.instance, (uint32_t)n, step);
-        else collide<R, false, COLL, NOISE>(f, Fx, Fy, Fz, I.pd, key, I.instance, (uint32_t)n, step);
+        if constexpr (DEV) collide<R, true, COLL, NOISE>(f, Fx, Fy, Fz, COMMON ? a.pf : I.pf, key, I.instance, n, step);
+        else collide<R, false, COLL, NOISE>(f, Fx, Fy, Fz, COMMON ? a.pd : I.pd, key, I.instance, n, step);
+        // re-read the plane layout for the stores instead of keeping 19 plane
+        // offsets live across the collision (register pressure)
+        const uint32_t base2 = *(const volatile uint32_t *)&a.inst[k].off;
+        const uint32_t N2 = *(const volatile uint32_t *)&a.inst[k].g.N;
+        auto at2 = [&](int i, uint32_t node) -> T & { return P[base2 + (uint32_t)i * N2 + node]; };
         if (!ODD) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) A[opp(i) * N + n] = f[i];
+            for (int i = 0; i < 19; ++i) at2(opp(i), n) = f[i];
         } else {
-            A[n] = f[0];
+            at2(0, n) = f[0];
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
-                const long long dst = xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)];
-                if (near_wall) {
-                    const int yd = (y + cy(i) + g.ny) % g.ny, zd = (z + cz(i) + g.nz) % g.nz;
-                    if (pore_r2(g, xo[1 + cx(i)], yd, zd) >= g.pore_t) { A[opp(i) * N + n] = f[i]; continue; }
-                }
-                A[i * N + dst] = f[i];
+                const uint32_t dst = (uint32_t)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
+                // downstream node x + c_i is upstream node x - c_opp(i)
+                if ((wall_up >> opp(i)) & 1u) at2(opp(i), n) = f[i];
+                else at2(i, dst) = f[i];
             }
         }
     }
@@ -292,6 +330,9 @@ struct lb_batch_ctx {
     unsigned char *tiles[2] = {nullptr, nullptr};
     BInst *dinst = nullptr;
     int *dtile_start = nullptr;
+    int *dtile_inst = nullptr;
+    size_t tile_inst_cap = 0;
+    bool common = false;                    // all instances share their collision constants
     long long *dflag_start = nullptr;
     unsigned long long *step_dev = nullptr;
     long long step = 0;
@@ -308,6 +349,7 @@ struct lb_batch_ctx {
     bool uploaded = false;
     // schedule
     int TS = 128, bpsm = 8, order = 0, ntiles = 0, sms = 0;
+    int resident = 0;                       // resident CTAs per SM of the fluid kernel at TS threads
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
     // timing
@@ -414,12 +456,41 @@ lb_status rebuild_schedule(lb_batch_ctx *h) {
     ts[h->n] = (int)acc;
     if (acc > 2000000000LL) return bfail(h, LB_ERR_ARG, "too many work tiles");
     h->ntiles = (int)acc;
+    std::vector<int> ti((size_t)acc);
+    for (int k = 0; k < h->n; ++k)
+        for (int t = ts[k]; t < ts[k + 1]; ++t) ti[t] = k;
+    if ((size_t)acc > h->tile_inst_cap) {
+        if (h->dtile_inst) { cudaFree(h->dtile_inst); h->dtile_inst = nullptr; }
+        lb_status s = balloc(h, &h->dtile_inst, sizeof(int) * (size_t)acc);
+        if (s != LB_OK) return s;
+        h->tile_inst_cap = (size_t)acc;
+    }
     BCUDA(h, cudaMemcpyAsync(h->dtile_start, ts.data(), sizeof(int) * (h->n + 1), cudaMemcpyHostToDevice, h->stream));
+    BCUDA(h, cudaMemcpyAsync(h->dtile_inst, ti.data(), sizeof(int) * (size_t)acc, cudaMemcpyHostToDevice, h->stream));
     BCUDA(h, cudaStreamSynchronize(h->stream));
     if (h->gexec) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
     }
+    // resident CTAs of the (even-step) fluid kernel at this tile size: the
+    // persistent grid never exceeds it, so every CTA runs concurrently
+    int occ = 0;
+    cudaError_t e;
+#define BOCC(T, C, NZ)                                                                                            \
+    e = h->common ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::k_batch_collide<T, C, NZ, false, true>, h->TS, 0) \
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::k_batch_collide<T, C, NZ, false, false>, h->TS, 0)
+    if (h->fp32) {
+        if (h->collision == 0) BOCC(float, 0, false);
+        else if (h->noise) BOCC(float, 1, true);
+        else BOCC(float, 1, false);
+    } else {
+        if (h->collision == 0) BOCC(double, 0, false);
+        else if (h->noise) BOCC(double, 1, true);
+        else BOCC(double, 1, false);
+    }
+#undef BOCC
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    h->resident = occ > 0 ? occ : 1;
     return LB_OK;
 }
 
@@ -498,9 +569,12 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     lbk::BatchArgs a{};
     a.inst = h->dinst;
     a.tile_start = h->dtile_start;
+    a.tile_inst = h->dtile_inst;
     a.n = h->n;
     a.ntiles = h->ntiles;
-    int grid = h->sms * h->bpsm;
+    a.pd = h->hinst[0].pd;
+    a.pf = h->hinst[0].pf;
+    int grid = h->sms * std::min(h->bpsm, h->resident > 0 ? h->resident : h->bpsm);
     if (grid > h->ntiles) grid = h->ntiles;
     if (grid < 1) grid = 1;
     a.order = h->order;
@@ -513,8 +587,13 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     if (record) BCUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
 #define BLAUNCH(T, C, NZ)                                                                                   \
     do {                                                                                                    \
-        if (odd) lbk::k_batch_collide<T, C, NZ, true><<<grid, h->TS, 0, h->stream>>>(a);                    \
-        else lbk::k_batch_collide<T, C, NZ, false><<<grid, h->TS, 0, h->stream>>>(a);                       \
+        if (h->common) {                                                                                    \
+            if (odd) lbk::k_batch_collide<T, C, NZ, true, true><<<grid, h->TS, 0, h->stream>>>(a);          \
+            else lbk::k_batch_collide<T, C, NZ, false, true><<<grid, h->TS, 0, h->stream>>>(a);             \
+        } else {                                                                                            \
+            if (odd) lbk::k_batch_collide<T, C, NZ, true, false><<<grid, h->TS, 0, h->stream>>>(a);         \
+            else lbk::k_batch_collide<T, C, NZ, false, false><<<grid, h->TS, 0, h->stream>>>(a);            \
+        }                                                                                                   \
     } while (0)
     if (h->fp32) {
         if (h->collision == 0) BLAUNCH(float, 0, false);
@@ -639,6 +718,10 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         I.gamma = p.gamma_bead;
         I.noise_amp = p.kT > 0.0 ? std::sqrt(2.0 * p.kT * p.gamma_bead) : 0.0;
         fill_coll(p, I);
+        I.mx = (uint32_t)((0x100000000ULL + p.nx - 1) / p.nx);
+        I.my = (uint32_t)((0x100000000ULL + p.ny - 1) / p.ny);
+        // exact while n * nx < 2^32 and (n / nx) * ny < 2^32 for all n < N
+        I.fastdiv = ((double)I.g.N * p.nx < 4294967296.0 && (double)(I.g.N / p.nx) * p.ny < 4294967296.0) ? 1 : 0;
         h->flag_start[k] = toff;
         h->nfluid[k] = I.g.N;
         off += 19 * I.g.N;
@@ -646,6 +729,13 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         toff += (long long)I.ntx * I.nty * I.ntz;
     }
     h->flag_start[n] = toff;
+    if (off >= 4294967296LL) {
+        delete h;
+        return bfail(nullptr, LB_ERR_ARG, "a batch holds at most 2^32 population values (19 per node)");
+    }
+    h->common = true;
+    for (int k = 1; k < n; ++k)
+        if (std::memcmp(&h->hinst[k].pd, &h->hinst[0].pd, sizeof(h->hinst[0].pd)) != 0) h->common = false;
     h->Ntot = off / 19;
     h->Ftot = foff / 3;
     h->Ttot = toff;
@@ -698,7 +788,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->dinst, h->dtile_start,
+    void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->dinst, h->dtile_start, h->dtile_inst,
                     h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -864,9 +954,10 @@ lb_status lb_batch_set_populations(lb_batch_handle h, int k, const double *host,
 
 lb_status lb_batch_set_schedule(lb_batch_handle h, int tile_nodes, int blocks_per_sm, int order) {
     if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    // the fluid kernel is capped at 64 registers, so 1024 threads per SM are resident
     if ((tile_nodes != 64 && tile_nodes != 128 && tile_nodes != 256) || blocks_per_sm < 1 ||
-        blocks_per_sm * tile_nodes > 2048 || (order != 0 && order != 1))
-        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 2048, order 0/1");
+        blocks_per_sm * tile_nodes > 1024 || (order != 0 && order != 1))
+        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 1024, order 0/1");
     h->TS = tile_nodes;
     h->bpsm = blocks_per_sm;
     h->order = order;
@@ -928,7 +1019,7 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     double best = 1e30;
     int bt = h->TS, bb = h->bpsm, bo = h->order;
     for (int ts : tiles)
-        for (int bps = 2; bps * ts <= 2048; bps *= 2)
+        for (int bps = 2; bps * ts <= 1024; bps *= 2)
             for (int order = 0; order < 2; ++order) {
                 if ((s = lb_batch_set_schedule(h, ts, bps, order)) != LB_OK) break;
                 // warm-up pair, then timed pairs

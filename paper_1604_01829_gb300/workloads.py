@@ -71,7 +71,7 @@ def _ellipsoid_shell(a, b, c, n, rng):
     """n roughly evenly spread points on the ellipsoid (x/a)^2+(y/b)^2+(z/c)^2=1."""
     if n <= 0:
         return np.zeros((0, 3))
-    m = max(20 * n, 200)
+    m = max(10 * n, 200)
     # area-uniform candidates: map sphere points, accept by the local area ratio
     cand = []
     gmax = max(b * c, a * c, a * b)
