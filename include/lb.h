@@ -100,7 +100,9 @@ lb_status lb_set_pore(lb_handle h, double radius, int axis);
  * q[4] = (w, x, y, z) (normalised by the library), mass and principal
  * moments inertia[3] (body axes = principal axes), constant external force
  * F_ext[3] and torque T_ext[3] (lab frame, may be NULL = 0). fixed = 1 holds
- * the body's position, orientation and velocities (a fixed colloid in flow).
+ * the body's position, orientation and velocities (a fixed colloid in flow);
+ * fixed = 2 integrates translation only, the orientation held and omega = 0
+ * (a colloid pulled along a body axis, the case the adjoint differentiates).
  * *body_id receives the body index (0, 1, ...). Only before the first lb_step.
  * Errors: LB_ERR_ARG, LB_ERR_STATE. */
 lb_status lb_add_raspberry(lb_handle h, const double *beads_body_xyz, int nbeads,

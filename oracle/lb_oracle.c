@@ -201,7 +201,8 @@ typedef struct {
     const double *inertia;  /* per body, principal moments (3) */
     const double *F_ext;    /* per body, lab frame (3) */
     const double *T_ext;    /* per body, lab frame (3) */
-    const int *fixed;       /* per body: 1 = kinematics held, not integrated */
+    const int *fixed;       /* per body: 1 = kinematics held, not integrated;
+                               2 = translation integrated, orientation held (omega = 0) */
     double *F_bead;         /* out: lab-frame force on each bead (3 per bead) */
     double *F_tot, *T_tot;  /* out: per body, lab-frame total force and torque (3, 3) */
 } orc_bodies;
@@ -529,7 +530,7 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
     for (int a = 0; a < 3; ++a) g[a] = p->body_force[a];
     if (p->compensate_force && nfluid > 0)
         for (int bi = 0; bi < nbodies; ++bi)
-            if (!b->fixed[bi])
+            if (b->fixed[bi] != 1)
                 for (int a = 0; a < 3; ++a) g[a] -= b->F_ext[3 * bi + a] / (double)nfluid;
 
     double *Fnew = (double *)calloc(3 * N, sizeof(double));
@@ -538,12 +539,16 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
 
     /* 1. first half kick and drift */
     for (int bi = 0; bi < nbodies; ++bi) {
-        if (b->fixed[bi]) continue;
+        if (b->fixed[bi] == 1) continue;
         double M = b->mass[bi];
         double *X = &b->X[3 * bi], *V = &b->V[3 * bi], *q = &b->q[4 * bi], *w = &b->w[3 * bi];
         for (int a = 0; a < 3; ++a) {
             V[a] += 0.5 * b->F_last[3 * bi + a] / M;
             X[a] += V[a];
+        }
+        if (b->fixed[bi] == 2) {           /* orientation held */
+            for (int a = 0; a < 3; ++a) w[a] = 0.0;
+            continue;
         }
         euler_half_kick(w, &b->inertia[3 * bi], &b->T_last[3 * bi]);
         double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -675,13 +680,370 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
             b->F_last[3 * bi + a] = b->F_tot[3 * bi + a];
             b->T_last[3 * bi + a] = Tb[a];
         }
-        if (b->fixed[bi]) continue;
+        if (b->fixed[bi] == 1) continue;
         for (int a = 0; a < 3; ++a) b->V[3 * bi + a] += 0.5 * b->F_tot[3 * bi + a] / b->mass[bi];
+        if (b->fixed[bi] == 2) continue;
         euler_half_kick_implicit(&b->w[3 * bi], &b->inertia[3 * bi], Tb);
     }
 
     memcpy(Fnode, Fnew, sizeof(double) * 3 * N);
     free(Fnew);
     free(fpost);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Reverse of one node's collision: given lam_out = dJ/df* (19), returns
+ * dJ/df (19) and dJ/dF (3) of f* = collide(f, F) for the deterministic
+ * collision (kT = 0), by the chain rule through rho, j, u = (j + F/2)/rho,
+ * f_eq(rho, u) and the Guo source s(u, F) in population space. */
+static void collide_node_adjoint(const orc_params *p, const double f[NQ], const double F[3],
+                                 const double lam_out[NQ], double lam_f[NQ], double lam_F[3])
+{
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < NQ; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) j[a] += CV[i][a] * f[i];
+    }
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
+    double lam_feq[NQ], lam_s[NQ];
+    for (int i = 0; i < NQ; ++i) lam_f[i] = 0.0;
+    if (p->collision == 0) {
+        const double om = 1.0 / p->tau;
+        for (int i = 0; i < NQ; ++i) {
+            lam_f[i] = (1.0 - om) * lam_out[i];
+            lam_feq[i] = om * lam_out[i];
+            lam_s[i] = (1.0 - 0.5 * om) * lam_out[i];
+        }
+    } else {
+        double lam_ms[NQ];
+        for (int k = 0; k < NQ; ++k) {
+            lam_ms[k] = 0.0;
+            for (int i = 0; i < NQ; ++i) lam_ms[k] += MINV[i][k] * lam_out[i];
+        }
+        for (int i = 0; i < NQ; ++i) {
+            lam_feq[i] = lam_s[i] = 0.0;
+            for (int k = 0; k < NQ; ++k) {
+                double g = mode_rate(p, k);
+                lam_f[i] += MM[k][i] * g * lam_ms[k];
+                lam_feq[i] += MM[k][i] * (1.0 - g) * lam_ms[k];
+                lam_s[i] += MM[k][i] * 0.5 * (1.0 + g) * lam_ms[k];
+            }
+        }
+    }
+    /* through f_eq(rho, u) and s(u, F) */
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double lam_rho = 0.0, lam_u[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) lam_F[a] = 0.0;
+    for (int i = 0; i < NQ; ++i) {
+        double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+        double cF = CV[i][0] * F[0] + CV[i][1] * F[1] + CV[i][2] * F[2];
+        lam_rho += lam_feq[i] * WQ[i] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        for (int a = 0; a < 3; ++a) {
+            lam_u[a] += lam_feq[i] * WQ[i] * rho * (3.0 * CV[i][a] + 9.0 * cu * CV[i][a] - 3.0 * u[a]);
+            lam_u[a] += lam_s[i] * WQ[i] * (-3.0 * F[a] + 9.0 * CV[i][a] * cF);
+            lam_F[a] += lam_s[i] * WQ[i] * (3.0 * (CV[i][a] - u[a]) + 9.0 * cu * CV[i][a]);
+        }
+    }
+    /* u = (j + F/2) / rho */
+    double lam_j[3];
+    for (int a = 0; a < 3; ++a) {
+        lam_j[a] = lam_u[a] / rho;
+        lam_F[a] += 0.5 * lam_u[a] / rho;
+        lam_rho -= lam_u[a] * u[a] / rho;
+    }
+    for (int i = 0; i < NQ; ++i)
+        lam_f[i] += lam_rho + CV[i][0] * lam_j[0] + CV[i][1] * lam_j[1] + CV[i][2] * lam_j[2];
+}
+
+void orc_collide_node_adjoint(const orc_params *p, const double *f, const double *F, const double *lam_out,
+                              double *lam_f, double *lam_F)
+{
+    init_tables();
+    collide_node_adjoint(p, f, F, lam_out, lam_f, lam_F);
+}
+
+/* Gradient of J = (1/W) sum over the last W steps of V_axis of body jb
+ * (its velocity after each step) with respect to the bead friction gamma and
+ * to every body-frame bead offset, by reverse-mode differentiation of
+ * orc_step over nsteps steps starting from the given state (which the call
+ * advances, exactly as orc_step would). Deterministic steps only (kT = 0);
+ * every body must be fixed (1) or translation-only (2). All intermediate
+ * states are stored (small cases only). Returns 0, -1 (memory), -2 (bad
+ * input). dJ_ds: 3 per bead of all bodies (may be NULL). */
+int orc_adjoint_drag(const orc_params *p, double *f, const unsigned char *mask, double *Fnode,
+                     orc_bodies *b, int64_t step0, int nsteps, int window, int jb, int axis,
+                     double *J, double *dJ_dgamma, double *dJ_ds)
+{
+    init_tables();
+    if (p->kT > 0.0 || nsteps < 1 || window < 1 || window > nsteps || !b || jb < 0 || jb >= b->nbodies ||
+        axis < 0 || axis > 2)
+        return -2;
+    if (b->nbodies > 64) return -2;
+    for (int bi = 0; bi < b->nbodies; ++bi)
+        if (b->fixed[bi] != 1 && b->fixed[bi] != 2) return -2;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const int nb = b->nbodies, nbeads = b->bead_start[nb];
+    double *fs = (double *)malloc(sizeof(double) * NQ * N * (size_t)nsteps);
+    double *Fs = (double *)malloc(sizeof(double) * 3 * N * (size_t)nsteps);
+    double *Bs = (double *)malloc(sizeof(double) * 9 * nb * (size_t)nsteps); /* X, V, F_last */
+    double *lf = (double *)calloc(NQ * N, sizeof(double)), *lf2 = (double *)calloc(NQ * N, sizeof(double));
+    double *lFp = (double *)calloc(3 * N, sizeof(double)), *lFp2 = (double *)calloc(3 * N, sizeof(double));
+    double *lFn = (double *)calloc(3 * N, sizeof(double));
+    double *Fnew = (double *)calloc(3 * N, sizeof(double));
+    double *lb_ = (double *)calloc(9 * nb, sizeof(double));   /* lam X, V, F_last per body */
+    double *Fb = (double *)malloc(sizeof(double) * 3 * (nbeads > 0 ? nbeads : 1));
+    if (!fs || !Fs || !Bs || !lf || !lf2 || !lFp || !lFp2 || !lFn || !Fnew || !lb_ || !Fb) {
+        free(fs); free(Fs); free(Bs); free(lf); free(lf2); free(lFp); free(lFp2); free(lFn); free(Fnew); free(lb_); free(Fb);
+        return -1;
+    }
+    /* forward, storing the state before every step */
+    double Jsum = 0.0;
+    for (int n = 0; n < nsteps; ++n) {
+        memcpy(fs + (size_t)n * NQ * N, f, sizeof(double) * NQ * N);
+        memcpy(Fs + (size_t)n * 3 * N, Fnode, sizeof(double) * 3 * N);
+        for (int bi = 0; bi < nb; ++bi)
+            for (int a = 0; a < 3; ++a) {
+                Bs[((size_t)n * nb + bi) * 9 + a] = b->X[3 * bi + a];
+                Bs[((size_t)n * nb + bi) * 9 + 3 + a] = b->V[3 * bi + a];
+                Bs[((size_t)n * nb + bi) * 9 + 6 + a] = b->F_last[3 * bi + a];
+            }
+        orc_step(p, f, mask, Fnode, b, step0 + n);
+        if (n >= nsteps - window) Jsum += b->V[3 * jb + axis];
+    }
+    *J = Jsum / window;
+
+    /* uniform force density as orc_step forms it */
+    size_t nfluid = 0;
+    for (size_t n = 0; n < N; ++n) nfluid += (mask && mask[n]) ? 0 : 1;
+    double g[3];
+    for (int a = 0; a < 3; ++a) g[a] = p->body_force[a];
+    if (p->compensate_force && nfluid > 0)
+        for (int bi = 0; bi < nb; ++bi)
+            if (b->fixed[bi] != 1)
+                for (int a = 0; a < 3; ++a) g[a] -= b->F_ext[3 * bi + a] / (double)nfluid;
+
+    double lgam = 0.0;
+    if (dJ_ds) memset(dJ_ds, 0, sizeof(double) * 3 * nbeads);
+    for (int n = nsteps - 1; n >= 0; --n) {
+        const double *fn = fs + (size_t)n * NQ * N;
+        const double *Fp = Fs + (size_t)n * 3 * N;
+        if (n >= nsteps - window) lb_[9 * jb + 3 + axis] += 1.0 / window;
+
+        /* recompute the step's coupling quantities */
+        double Ftot[64][3];
+        double Xp[64][3], Vp[64][3], Rm[64][3][3], wl[64][3];
+        memset(Fnew, 0, sizeof(double) * 3 * N);
+        for (int bi = 0; bi < nb; ++bi) {
+            const double *Bn = Bs + ((size_t)n * nb + bi) * 9;
+            for (int a = 0; a < 3; ++a) {
+                if (b->fixed[bi] == 2) {
+                    Vp[bi][a] = Bn[3 + a] + 0.5 * Bn[6 + a] / b->mass[bi];
+                    Xp[bi][a] = Bn[a] + Vp[bi][a];
+                } else {
+                    Vp[bi][a] = Bn[3 + a];
+                    Xp[bi][a] = Bn[a];
+                }
+                Ftot[bi][a] = b->F_ext[3 * bi + a];
+            }
+            rotation(&b->q[4 * bi], Rm[bi]);
+            const double *wb = &b->w[3 * bi];
+            for (int a = 0; a < 3; ++a) wl[bi][a] = Rm[bi][a][0] * wb[0] + Rm[bi][a][1] * wb[1] + Rm[bi][a][2] * wb[2];
+        }
+        for (int bi = 0; bi < nb; ++bi)
+            for (int k = b->bead_start[bi]; k < b->bead_start[bi + 1]; ++k) {
+                const double *s = &b->s[3 * k];
+                double rel[3], r[3], v[3], wxr[3];
+                for (int a = 0; a < 3; ++a) rel[a] = Rm[bi][a][0] * s[0] + Rm[bi][a][1] * s[1] + Rm[bi][a][2] * s[2];
+                for (int a = 0; a < 3; ++a) r[a] = Xp[bi][a] + rel[a];
+                cross(wl[bi], rel, wxr);
+                for (int a = 0; a < 3; ++a) v[a] = Vp[bi][a] + wxr[a];
+                int base[3];
+                double fr[3];
+                for (int a = 0; a < 3; ++a) {
+                    double t = r[a] - 0.5, fl = floor(t);
+                    base[a] = (int)fl;
+                    fr[a] = t - fl;
+                }
+                double ub[3] = {0, 0, 0};
+                for (int c = 0; c < 8; ++c) {
+                    int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                    double wt = 1.0;
+                    for (int a = 0; a < 3; ++a) wt *= o[a] ? fr[a] : 1.0 - fr[a];
+                    size_t nn = nidx(p, wrap(base[0] + o[0], nx), wrap(base[1] + o[1], ny), wrap(base[2] + o[2], nz));
+                    if (mask && mask[nn]) continue;
+                    double rho = 0.0, jj[3] = {0, 0, 0};
+                    for (int i = 0; i < NQ; ++i) {
+                        double fv = fn[(size_t)i * N + nn];
+                        rho += fv;
+                        for (int a = 0; a < 3; ++a) jj[a] += CV[i][a] * fv;
+                    }
+                    for (int a = 0; a < 3; ++a) ub[a] += wt * (jj[a] + 0.5 * (g[a] + Fp[(size_t)a * N + nn])) / rho;
+                }
+                for (int a = 0; a < 3; ++a) {
+                    Fb[3 * k + a] = -p->gamma_bead * (v[a] - ub[a]);
+                    Ftot[bi][a] += Fb[3 * k + a];
+                }
+                for (int c = 0; c < 8; ++c) {
+                    int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                    double wt = 1.0;
+                    for (int a = 0; a < 3; ++a) wt *= o[a] ? fr[a] : 1.0 - fr[a];
+                    size_t nn = nidx(p, wrap(base[0] + o[0], nx), wrap(base[1] + o[1], ny), wrap(base[2] + o[2], nz));
+                    if (mask && mask[nn]) continue;
+                    for (int a = 0; a < 3; ++a) Fnew[(size_t)a * N + nn] -= wt * Fb[3 * k + a];
+                }
+            }
+
+        /* kick2 reversed: V_{n+1} = V' + F_tot/(2M) (translation-only bodies), F_last_{n+1} = F_tot */
+        double lVp[64][3], lXp[64][3], lFt[64][3];
+        for (int bi = 0; bi < nb; ++bi)
+            for (int a = 0; a < 3; ++a) {
+                lXp[bi][a] = lb_[9 * bi + a];
+                lFt[bi][a] = lb_[9 * bi + 6 + a];
+                lVp[bi][a] = 0.0;
+                if (b->fixed[bi] == 2) {
+                    lVp[bi][a] = lb_[9 * bi + 3 + a];
+                    lFt[bi][a] += lb_[9 * bi + 3 + a] / (2.0 * b->mass[bi]);
+                }
+            }
+        /* F_prev_{n+1} = F_new */
+        for (size_t q = 0; q < 3 * N; ++q) lFn[q] = lFp[q];
+        /* streaming reversed: adjoint of the post-collision population */
+        memset(lf2, 0, sizeof(double) * NQ * N);
+        memset(lFp2, 0, sizeof(double) * 3 * N);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t nn = nidx(p, x, y, z);
+                    if (mask && mask[nn]) continue;
+                    double lpost[NQ], fl[NQ], F[3], lfn[NQ], lF[3];
+                    for (int i = 0; i < NQ; ++i) {
+                        size_t to = nidx(p, wrap(x + CV[i][0], nx), wrap(y + CV[i][1], ny), wrap(z + CV[i][2], nz));
+                        lpost[i] = (mask && mask[to]) ? lf[(size_t)OPP[i] * N + nn] : lf[(size_t)i * N + to];
+                        fl[i] = fn[(size_t)i * N + nn];
+                    }
+                    for (int a = 0; a < 3; ++a) F[a] = g[a] + Fnew[(size_t)a * N + nn];
+                    collide_node_adjoint(p, fl, F, lpost, lfn, lF);
+                    for (int i = 0; i < NQ; ++i) lf2[(size_t)i * N + nn] = lfn[i];
+                    for (int a = 0; a < 3; ++a) lFn[(size_t)a * N + nn] += lF[a];
+                }
+        /* coupling reversed */
+        for (int bi = 0; bi < nb; ++bi)
+            for (int k = b->bead_start[bi]; k < b->bead_start[bi + 1]; ++k) {
+                const double *s = &b->s[3 * k];
+                double rel[3], r[3], v[3], wxr[3];
+                for (int a = 0; a < 3; ++a) rel[a] = Rm[bi][a][0] * s[0] + Rm[bi][a][1] * s[1] + Rm[bi][a][2] * s[2];
+                for (int a = 0; a < 3; ++a) r[a] = Xp[bi][a] + rel[a];
+                cross(wl[bi], rel, wxr);
+                for (int a = 0; a < 3; ++a) v[a] = Vp[bi][a] + wxr[a];
+                int base[3];
+                double fr[3];
+                for (int a = 0; a < 3; ++a) {
+                    double t = r[a] - 0.5, fl = floor(t);
+                    base[a] = (int)fl;
+                    fr[a] = t - fl;
+                }
+                double uj[8][3], rhoj[8], wts[8];
+                size_t nns[8];
+                int fl8[8];
+                double ub[3] = {0, 0, 0};
+                for (int c = 0; c < 8; ++c) {
+                    int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                    double wt = 1.0;
+                    for (int a = 0; a < 3; ++a) wt *= o[a] ? fr[a] : 1.0 - fr[a];
+                    size_t nn = nidx(p, wrap(base[0] + o[0], nx), wrap(base[1] + o[1], ny), wrap(base[2] + o[2], nz));
+                    wts[c] = wt;
+                    nns[c] = nn;
+                    fl8[c] = !(mask && mask[nn]);
+                    rhoj[c] = 1.0;
+                    for (int a = 0; a < 3; ++a) uj[c][a] = 0.0;
+                    if (!fl8[c]) continue;
+                    double rho = 0.0, jj[3] = {0, 0, 0};
+                    for (int i = 0; i < NQ; ++i) {
+                        double fv = fn[(size_t)i * N + nn];
+                        rho += fv;
+                        for (int a = 0; a < 3; ++a) jj[a] += CV[i][a] * fv;
+                    }
+                    rhoj[c] = rho;
+                    for (int a = 0; a < 3; ++a) {
+                        uj[c][a] = (jj[a] + 0.5 * (g[a] + Fp[(size_t)a * N + nn])) / rho;
+                        ub[a] += wt * uj[c][a];
+                    }
+                }
+                /* lam F_b: from the body total and from the spread */
+                double lFbk[3], lw[8];
+                for (int a = 0; a < 3; ++a) lFbk[a] = lFt[bi][a];
+                for (int c = 0; c < 8; ++c) {
+                    lw[c] = 0.0;
+                    if (!fl8[c]) continue;
+                    for (int a = 0; a < 3; ++a) {
+                        lFbk[a] -= wts[c] * lFn[(size_t)a * N + nns[c]];
+                        lw[c] -= Fb[3 * k + a] * lFn[(size_t)a * N + nns[c]];
+                    }
+                }
+                /* F_b = -gamma (v - u_b) */
+                double lv[3], lub[3];
+                for (int a = 0; a < 3; ++a) {
+                    lgam += -(v[a] - ub[a]) * lFbk[a];
+                    lv[a] = -p->gamma_bead * lFbk[a];
+                    lub[a] = p->gamma_bead * lFbk[a];
+                }
+                /* u_b = sum_c w_c u_c; u_c = (j_c + (g + Fprev_c)/2) / rho_c */
+                for (int c = 0; c < 8; ++c) {
+                    if (!fl8[c]) continue;
+                    double luj[3], lrho = 0.0, lj[3];
+                    for (int a = 0; a < 3; ++a) {
+                        lw[c] += uj[c][a] * lub[a];
+                        luj[a] = wts[c] * lub[a];
+                        lj[a] = luj[a] / rhoj[c];
+                        lrho -= luj[a] * uj[c][a] / rhoj[c];
+                        lFp2[(size_t)a * N + nns[c]] += 0.5 * luj[a] / rhoj[c];
+                    }
+                    for (int i = 0; i < NQ; ++i)
+                        lf2[(size_t)i * N + nns[c]] += lrho + CV[i][0] * lj[0] + CV[i][1] * lj[1] + CV[i][2] * lj[2];
+                }
+                /* weights w_c = prod_a (o_a ? fr_a : 1 - fr_a), d fr_a / d r_a = 1 */
+                double lr[3] = {0, 0, 0};
+                for (int c = 0; c < 8; ++c) {
+                    int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                    for (int a = 0; a < 3; ++a) {
+                        double d = o[a] ? 1.0 : -1.0;
+                        for (int a2 = 0; a2 < 3; ++a2)
+                            if (a2 != a) d *= o[a2] ? fr[a2] : 1.0 - fr[a2];
+                        lr[a] += lw[c] * d;
+                    }
+                }
+                /* r = X' + R s, v = V' + w x (R s) */
+                double lrel[3], lxw[3];
+                cross(lv, wl[bi], lxw);   /* (lam_v x w) is the adjoint of w x rel */
+                for (int a = 0; a < 3; ++a) {
+                    lXp[bi][a] += lr[a];
+                    lVp[bi][a] += lv[a];
+                    lrel[a] = lr[a] + lxw[a];
+                }
+                if (dJ_ds)
+                    for (int a = 0; a < 3; ++a)
+                        dJ_ds[3 * k + a] += Rm[bi][0][a] * lrel[0] + Rm[bi][1][a] * lrel[1] + Rm[bi][2][a] * lrel[2];
+            }
+        /* kick-drift reversed: V' = V + F_last/(2M), X' = X + V' (translation-only bodies) */
+        for (int bi = 0; bi < nb; ++bi)
+            for (int a = 0; a < 3; ++a) {
+                if (b->fixed[bi] == 2) {
+                    double lvt = lVp[bi][a] + lXp[bi][a];
+                    lb_[9 * bi + a] = lXp[bi][a];
+                    lb_[9 * bi + 3 + a] = lvt;
+                    lb_[9 * bi + 6 + a] = lvt / (2.0 * b->mass[bi]);
+                } else {
+                    lb_[9 * bi + a] = lb_[9 * bi + 3 + a] = lb_[9 * bi + 6 + a] = 0.0;
+                }
+            }
+        double *t = lf; lf = lf2; lf2 = t;
+        t = lFp; lFp = lFp2; lFp2 = t;
+    }
+    *dJ_dgamma = lgam;
+    free(fs); free(Fs); free(Bs); free(lf); free(lf2); free(lFp); free(lFp2); free(lFn); free(Fnew); free(lb_); free(Fb);
     return 0;
 }

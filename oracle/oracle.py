@@ -80,6 +80,10 @@ def lib():
             L.orc_rotation.argtypes = [_dp, _dp]
             L.orc_quat_mul.argtypes = [_dp, _dp, _dp]
             L.orc_pore_mask.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p]
+            L.orc_collide_node_adjoint.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp]
+            L.orc_adjoint_drag.argtypes = [C.POINTER(Params), _dp, C.c_void_p, _dp, C.c_void_p, C.c_int64,
+                                           C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
+            L.orc_adjoint_drag.restype = C.c_int
             _lib = L
     return _lib
 
@@ -166,6 +170,16 @@ def collide_node(p: Params, f, F, node_id=0, step=0):
     return out
 
 
+def collide_node_adjoint(p: Params, f, F, lam_out):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    lo = np.ascontiguousarray(lam_out, dtype=np.float64)
+    lf = np.zeros(NQ)
+    lF = np.zeros(3)
+    lib().orc_collide_node_adjoint(C.byref(p), _d(f), _d(F), _d(lo), _d(lf), _d(lF))
+    return lf, lF
+
+
 # ------------------------------------------------------------------ the stepper
 
 class OracleLB:
@@ -202,7 +216,7 @@ class OracleLB:
                                 q=np.array(q, np.float64), w=np.array(w, np.float64),
                                 mass=float(mass), inertia=np.array(inertia, np.float64),
                                 F_ext=np.array(F_ext, np.float64), T_ext=np.array(T_ext, np.float64),
-                                fixed=int(bool(fixed))))
+                                fixed=int(fixed)))
         self._packed = None
         return len(self.bodies) - 1
 
@@ -254,6 +268,48 @@ class OracleLB:
             if rc != 0:
                 raise ValueError("oracle step rejected its input")
             self.step_index += 1
+
+    def adjoint_drag(self, nsteps, window, body=0, axis=2):
+        """Runs nsteps steps (advancing the state like step()) and returns
+        J = mean V_axis of `body` over the last `window` steps with dJ/dgamma
+        and dJ/ds (3 per bead, all bodies), by the oracle's reverse pass."""
+        if self.bodies and self._packed is None:
+            self._pack()
+        mptr = self.mask.ctypes.data_as(C.c_void_p) if self.mask is not None else None
+        J = C.c_double()
+        dg = C.c_double()
+        ds = np.zeros(3 * int(self._packed["bead_start"][-1]))
+        rc = lib().orc_adjoint_drag(C.byref(self.p), _d(self.f), mptr, _d(self.Fnode), C.byref(self._struct),
+                                    self.step_index, int(nsteps), int(window), int(body), int(axis),
+                                    C.byref(J), C.byref(dg), _d(ds))
+        if rc != 0:
+            raise ValueError(f"oracle adjoint rejected its input ({rc})")
+        self.step_index += nsteps
+        return J.value, dg.value, ds.reshape(-1, 3)
+
+    def clone(self):
+        """Deep copy of the whole state (for finite differences)."""
+        import copy
+        o = OracleLB.__new__(OracleLB)
+        o.p = copy.copy(self.p)
+        o.p.body_force = (C.c_double * 3)(*self.p.body_force)
+        o.N = self.N
+        o.f = self.f.copy()
+        o.mask = None if self.mask is None else self.mask.copy()
+        o.Fnode = self.Fnode.copy()
+        o.step_index = self.step_index
+        o.bodies = [{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in b.items()} for b in self.bodies]
+        o._packed = None
+        if self._packed is not None:
+            # carry the evolving body state
+            P = self._packed
+            for i, b in enumerate(o.bodies):
+                for k, sz in (("X", 3), ("V", 3), ("q", 4), ("w", 3)):
+                    b[k] = P[k][sz * i:sz * i + sz].copy()
+            o._pack()
+            for k in ("F_last", "T_last"):
+                o._packed[k][:] = P[k]
+        return o
 
     # state access -------------------------------------------------------------
     def populations(self):

@@ -96,7 +96,7 @@ void compute_gforce(const lb_ctx *h, double g[3]) {
     for (int a = 0; a < 3; ++a) g[a] = h->p.body_force[a];
     if (h->p.compensate_force && h->nfluid > 0)
         for (const Body &b : h->hb)
-            if (!b.fixed)
+            if (b.fixed != 1)
                 for (int a = 0; a < 3; ++a) g[a] -= b.F_ext[a] / (double)h->nfluid;
 }
 
@@ -444,7 +444,8 @@ lb_status lb_add_raspberry(lb_handle h, const double *beads, int nbeads, const d
     }
     for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
     b.mass = mass;
-    b.fixed = fixed ? 1 : 0;
+    if (fixed < 0 || fixed > 2) return fail(h, LB_ERR_ARG, "fixed must be 0, 1 or 2");
+    b.fixed = fixed;
     const int id = (int)h->hb.size();
     h->hb.push_back(b);
     for (int k = 0; k < 3 * nbeads; ++k) h->hs.push_back(beads[k]);

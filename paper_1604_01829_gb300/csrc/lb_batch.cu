@@ -442,7 +442,7 @@ void compute_g(const lb_batch_ctx *h, int k, double g[3]) {
     for (int a = 0; a < 3; ++a) g[a] = p.body_force[a];
     if (p.compensate_force && h->nfluid[k] > 0)
         for (int b : h->inst_bodies[k])
-            if (!h->hb[b].fixed)
+            if (h->hb[b].fixed != 1)
                 for (int a = 0; a < 3; ++a) g[a] -= h->hb[b].F_ext[a] / (double)h->nfluid[k];
 }
 
@@ -840,7 +840,8 @@ lb_status lb_batch_add_raspberry(lb_batch_handle h, int k, const double *beads, 
     }
     for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
     b.mass = mass;
-    b.fixed = fixed ? 1 : 0;
+    if (fixed < 0 || fixed > 2) return bfail(h, LB_ERR_ARG, "fixed must be 0, 1 or 2");
+    b.fixed = fixed;
     b.inst = k;
     const int id = (int)h->hb.size();
     h->hb.push_back(b);

@@ -55,15 +55,22 @@ __device__ __forceinline__ void kick2(Body &B) {
         B.F_last[a] = B.F_tot[a];
         B.T_last[a] = Tb[a];
     }
-    if (B.fixed) return;
+    if (B.fixed == 1) return;
     for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * B.F_tot[a] / B.mass;
+    if (B.fixed == 2) return;          // orientation held
     euler_half_implicit(B.w, B.I, Tb);
 }
 
 // First half kick with last step's force and torque, then drift: X += V,
 // q <- q (x) exp(omega/2) with the half-step body-frame omega.
 __device__ __forceinline__ void kick_drift(Body &B) {
-    if (!B.fixed) {
+    if (B.fixed == 2) {                // translation only, orientation held
+        for (int a = 0; a < 3; ++a) {
+            B.V[a] += 0.5 * B.F_last[a] / B.mass;
+            B.X[a] += B.V[a];
+            B.w[a] = 0.0;
+        }
+    } else if (!B.fixed) {
         for (int a = 0; a < 3; ++a) {
             B.V[a] += 0.5 * B.F_last[a] / B.mass;
             B.X[a] += B.V[a];

@@ -216,7 +216,7 @@ class LB:
         bid = C.c_int(-1)
         _check(self.h, load().lb_add_raspberry(
             self.h, _d(b), b.size // 3, _d(_vec(X, 3)), _d(_vec(q, 4)), float(mass),
-            _d(_vec(inertia, 3)), _d(_vec(F_ext, 3)), _d(_vec(T_ext, 3)), int(bool(fixed)),
+            _d(_vec(inertia, 3)), _d(_vec(F_ext, 3)), _d(_vec(T_ext, 3)), int(fixed),
             C.byref(bid)))
         self.bead_counts.append(b.size // 3)
         return bid.value
@@ -351,7 +351,7 @@ class LBBatch:
         bid = C.c_int(-1)
         _bcheck(self.h, load().lb_batch_add_raspberry(
             self.h, int(inst), _d(b), b.size // 3, _d(_vec(X, 3)), _d(_vec(q, 4)), float(mass),
-            _d(_vec(inertia, 3)), _d(_vec(F_ext, 3)), _d(_vec(T_ext, 3)), int(bool(fixed)), C.byref(bid)))
+            _d(_vec(inertia, 3)), _d(_vec(F_ext, 3)), _d(_vec(T_ext, 3)), int(fixed), C.byref(bid)))
         return bid.value
 
     def lb_batch_step(self, n=1):

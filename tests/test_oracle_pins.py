@@ -486,3 +486,76 @@ def test_wall_nodes_absorb_spread_force_and_keep_mass():
     Fn = L.Fnode.reshape(3, -1)
     assert np.abs(Fn[:, L.mask == 1]).max() == 0.0
     assert np.abs(Fn).max() > 0
+
+
+# --------------------------------------------------------------- adjoint pins
+
+@pytest.mark.parametrize("kind", ["bgk", "mrt"])
+def test_collision_adjoint_matches_finite_differences(kind):
+    """Reverse of one node's collision (oracle adjoint) against central
+    differences of the oracle collision, for f and for the force."""
+    kw = dict(collision=0, tau=0.8) if kind == "bgk" else dict(
+        collision=1, gamma_shear=-0.4, gamma_bulk=0.2, gamma_odd=0.3, gamma_even=-0.1)
+    p = _params(**kw)
+    rng = np.random.default_rng(1)
+    f = O.equilibrium(1.0, [0.02, -0.01, 0.03]) * (1 + 0.05 * rng.standard_normal(19))
+    F = 1e-3 * rng.standard_normal(3)
+    lam = rng.standard_normal(19)
+    lf, lF = O.collide_node_adjoint(p, f, F, lam)
+    h = 1e-6
+    fd = np.array([(O.collide_node(p, f + h * e, F) - O.collide_node(p, f - h * e, F)) @ lam / (2 * h)
+                   for e in np.eye(19)])
+    fdF = np.array([(O.collide_node(p, f, F + h * e) - O.collide_node(p, f, F - h * e)) @ lam / (2 * h)
+                    for e in np.eye(3)])
+    assert np.abs(lf - fd).max() <= 1e-8 * np.abs(fd).max()
+    assert np.abs(lF - fdF).max() <= 1e-8 * np.abs(fdF).max()
+
+
+def _adjoint_case(gamma, pore=False):
+    from paper_1604_01829_gb300 import workloads as W
+    kw = dict(collision=1, gamma_shear=-0.3, gamma_bulk=-0.3, gamma_odd=0.0, gamma_even=0.0,
+              gamma_bead=gamma, compensate_force=0 if pore else 1)
+    L = O.OracleLB(12, 12, 12, **kw)
+    if pore:
+        L.set_pore(5.5, axis=2)
+    L.add_raspberry(W.sphere_raspberry(2.0), [6.3, 5.9, 6.1], mass=40.0, inertia=(60, 60, 60),
+                    F_ext=(0, 0, 2e-3), fixed=2)
+    L.step(5)
+    return L
+
+
+@pytest.mark.parametrize("pore", [False, True])
+def test_drag_adjoint_matches_finite_differences(pore):
+    """Gradient of J = mean pulled-body velocity over the last steps with
+    respect to gamma and to bead offsets, from the oracle's reverse pass,
+    against central differences of the oracle forward (no bead crosses a
+    cell face under the perturbation)."""
+    g0 = 0.1
+    base = _adjoint_case(g0, pore)
+    run = base.clone()
+    J, dg, ds = run.adjoint_drag(30, 10)
+    assert J > 0
+    h = 1e-6
+    Jp = base.clone()
+    Jp.p.gamma_bead = g0 + h
+    Jm = base.clone()
+    Jm.p.gamma_bead = g0 - h
+    fd = (Jp.adjoint_drag(30, 10)[0] - Jm.adjoint_drag(30, 10)[0]) / (2 * h)
+    assert abs(dg - fd) <= 1e-6 * abs(fd)
+    for (k, a) in [(0, 0), (5, 2), (40, 1)]:
+        vals = []
+        for d in (1e-5, -1e-5):
+            c = base.clone()
+            c.bodies[0]["s"] = c.bodies[0]["s"].copy()
+            c.bodies[0]["s"][k, a] += d
+            P = base._packed
+            c._pack()
+            for key in ("X", "V", "q", "w", "F_last", "T_last"):
+                c._packed[key][:] = P[key]
+            vals.append(c.adjoint_drag(30, 10)[0])
+        fd = (vals[0] - vals[1]) / 2e-5
+        assert abs(ds[k, a] - fd) <= 2e-5 * abs(fd) + 1e-12, (k, a, ds[k, a], fd)
+    # the pass advances the state exactly like plain steps
+    plain = base.clone()
+    plain.step(30)
+    assert np.array_equal(plain.populations(), run.populations())
