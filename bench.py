@@ -237,6 +237,7 @@ def run_ours(args, ws, rank, local):
                      "frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8}
 
     batched = None if args.skip_batched else measure_batched(args, torch, lb, barrier_max, ws)
+    adjoint = None if args.skip_adjoint else measure_adjoint(args, torch, lb)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -273,6 +274,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": 3 * K + 2,
             "fp64": fp64_line,
             "batched": batched,
+            "adjoint": adjoint,
             "clocks": main["clocks"],
             "cpu_baseline": cpu,
         }
@@ -351,6 +353,60 @@ def measure_batched(args, torch, lb, barrier_max, ws):
                              "frac": round(ach / peak, 4), "peak_kind": kind}}
 
 
+def measure_adjoint(args, torch, lb):
+    """Hand-written adjoint on the 96^3 deterministic box with one prolate
+    ellipsoid (a = 15, b = c = 5) pulled along its long axis: J = terminal
+    velocity over the last steps, dJ/dgamma, dJ/ds for every bead, FP32
+    storage, two-level checkpointing. Compared with the FP64 forward step on
+    the same workload; the FP32 drag is compared with the FP64 drag."""
+    from paper_1604_01829_gb300 import workloads as W
+    w32 = W.ellipsoid_adjoint_96(precision=32)
+    T, Wn = args.adjoint_steps, max(1, args.adjoint_steps // 15)
+    stream = torch.cuda.Stream()
+    L = lb.from_workload(w32, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J32, dg, ds = L.lb_adjoint_drag(T, Wn, body=0, axis=0)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    L.close()
+    # FP32 forward alone (same steps) and FP64 forward on the same workload
+    def forward(precision, steps):
+        Lf = lb.from_workload(W.ellipsoid_adjoint_96(precision=precision), stream=stream.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        Lf.lb_step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        Lf.lb_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v = Lf.lb_get_body(0)["V"][0]
+        Lf.close()
+        return e0.elapsed_time(e1) / steps, v
+    f32_ms, _ = forward(32, min(T, 500))
+    f64_ms, _ = forward(64, 50)
+    # drag of the FP64 reference run over the same steps and window
+    L64 = lb.from_workload(W.ellipsoid_adjoint_96(precision=64), stream=stream.cuda_stream)
+    vs = []
+    for n in range(T):
+        L64.lb_step(1)
+        if n >= T - Wn:
+            vs.append(L64.lb_get_body(0)["V"][0])
+    L64.close()
+    J64 = float(np.mean(vs))
+    F = w32.bodies[0].F_ext[0]
+    return {"workload": f"96^3 periodic, MRT nu=0.016, kT=0, FP32; prolate ellipsoid 15x5x5 "
+                        f"({w32.nbeads} beads) pulled along its axis, {T} steps, J over the last {Wn}",
+            "adjoint_s": round(t_adj, 3), "adjoint_ms_per_step": round(1e3 * t_adj / T, 4),
+            "fp32_forward_ms_per_step": round(f32_ms, 4), "fp64_forward_ms_per_step": round(f64_ms, 4),
+            "adjoint_step_over_fp64_forward_step": round(1e3 * t_adj / T / f64_ms, 3),
+            "drag_fp32": F / J32, "drag_fp64": F / J64,
+            "drag_rel_error_fp32_vs_fp64": abs(J64 / J32 - 1.0),
+            "dJ_dgamma": dg, "dxi_dgamma": -F / J32 ** 2 * dg,
+            "dJ_ds_norm": float(np.linalg.norm(ds))}
+
+
 def oracle_sample(seconds):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
     a 64^3 periodic box (1/64 of the lattice) with the same physics, holding
@@ -421,6 +477,8 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--adjoint-steps", type=int, default=3000)
     args = ap.parse_args()
     global ARGS
     ARGS = args

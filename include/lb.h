@@ -185,6 +185,21 @@ lb_status lb_kernel_time(lb_handle h, double *total_ms, long long *launches);
 const char *lb_last_error(lb_handle h);
 const char *lb_status_string(lb_status s);
 
+/* Adjoint of the deterministic step (kT = 0; every body fixed (1) or
+ * translation-only (2)). Runs nsteps steps from the current state (the
+ * handle ends exactly where lb_step(h, nsteps) would leave it) and returns
+ * J = mean over the last `window` steps of component `axis` of the velocity
+ * of body `body` (the terminal velocity of a colloid pulled by F_ext, whose
+ * drag is F_ext / J as in Eq. (stokesflow)), dJ/dgamma (bead friction of
+ * Eq. (latticeboltzmannfriction)) and, if dJ_dbeads is not NULL, dJ/ds for
+ * every body-frame bead offset of every body (3 per bead, in the order the
+ * beads were added). checkpoints: snapshot slots of the two-level schedule
+ * (0 = ceil(sqrt(nsteps))); memory ~ (checkpoints + nsteps/checkpoints)
+ * lattice states, cost ~ two forward sweeps plus one reverse sweep.
+ * Errors: LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA. */
+lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int body, int axis, int checkpoints,
+                          double *J, double *dJ_dgamma, double *dJ_dbeads);
+
 /* ------------------------------------------------------------------ batches
  * Many independent lattices of uneven size advanced together: the same step
  * as above for every instance (Sec. 1.1, Eq. (latticeboltzmannfriction),

@@ -1,0 +1,64 @@
+// Host state of one lattice handle, shared by the C-ABI runtime (lb_api.cu)
+// and the adjoint driver (lb_adjoint.cu). Not part of the public ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+using lbk::Body;
+
+struct lb_ctx {
+    lb_params p{};
+    lbk::Geom g{};
+    bool fp32 = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *f = nullptr;
+    double *gforce = nullptr;               // device (3)
+    float *gforce_f = nullptr;              // device (3), FP32 copy
+    unsigned long long *step_dev = nullptr; // device step counter
+    int *err_dev = nullptr;                 // device error word of bounded waits
+    int cs_variant = 0;                     // collide kernel: 0 auto (plain), 1 plain, 2 TMA-staged
+    int tma_stages = 0, tma_ctas = 0;       // 0 = library default
+    long long step = 0;                     // host mirror
+    long long nfluid = 0;
+    double sig[15] = {};
+    // bead force fields (double buffered) and their 4x4x4 tile flags
+    double *Fbuf[2] = {nullptr, nullptr};
+    unsigned char *tiles[2] = {nullptr, nullptr};
+    int ntx = 0, nty = 0, ntz = 0;
+    // bodies
+    std::vector<Body> hb;
+    std::vector<double> hs;
+    std::vector<int> hbody_of;
+    std::vector<int> bead_start{0};
+    Body *db = nullptr;
+    double *ds = nullptr;
+    int *dbody_of = nullptr;
+    double *dFbead = nullptr;
+    bool uploaded = false;
+    // reductions
+    double *partials = nullptr;
+    double *out4 = nullptr;
+    int red_blocks = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // pairs
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    long long timed_n = 0;
+    dim3 block{128, 1, 1};
+    size_t dev_bytes = 0;
+    double g_host[3] = {};
+    float gf_host[3] = {};
+    std::string err;
+};
+
+
+namespace lbk {
+lb_status ctx_upload(lb_ctx *h);
+lb_status ctx_fail(lb_ctx *h, lb_status s, const std::string &m);
+}  // namespace lbk

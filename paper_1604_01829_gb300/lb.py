@@ -65,6 +65,7 @@ _SIGS = {
     "lb_info": [C.c_void_p, C.POINTER(lb_info_t)],
     "lb_set_timing": [C.c_void_p, C.c_int],
     "lb_set_kernel_variant": [C.c_void_p, C.c_int, C.c_int, C.c_int],
+    "lb_adjoint_drag": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
 }
 
@@ -290,6 +291,14 @@ class LB:
 
     def lb_set_timing(self, on=True):
         _check(self.h, load().lb_set_timing(self.h, int(bool(on))))
+
+    def lb_adjoint_drag(self, nsteps, window, body=0, axis=2, checkpoints=0):
+        """(J, dJ/dgamma, dJ/ds[nbeads, 3]) from the hand-written adjoint."""
+        J, dg = C.c_double(), C.c_double()
+        ds = np.zeros(3 * sum(self.bead_counts))
+        _check(self.h, load().lb_adjoint_drag(self.h, int(nsteps), int(window), int(body), int(axis),
+                                              int(checkpoints), C.byref(J), C.byref(dg), _d(ds)))
+        return J.value, dg.value, ds.reshape(-1, 3)
 
     def lb_kernel_time(self):
         ms = C.c_double()

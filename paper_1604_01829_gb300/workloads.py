@@ -144,7 +144,7 @@ class Body:
     inertia: np.ndarray
     F_ext: np.ndarray = field(default_factory=lambda: np.zeros(3))
     T_ext: np.ndarray = field(default_factory=lambda: np.zeros(3))
-    fixed: bool = False
+    fixed: int = 0          # 0 free, 1 held, 2 translation only
 
 
 @dataclass
@@ -291,8 +291,9 @@ def ellipsoid_adjoint_96(seed: int = 1609, precision: int = 32) -> Workload:
     a = 15) under constant force along its long axis."""
     beads = ellipsoid_raspberry(15.0, 5.0, 5.0, seed=seed)
     mass = (4.0 / 3.0) * math.pi * 15 * 25
+    # pulled along its long (body x) axis with the orientation held
     b = Body(beads, np.array([48.0, 48.0, 48.0]), np.array([1.0, 0, 0, 0]), mass,
-             solid_ellipsoid_inertia(mass, 15, 5, 5), F_ext=np.array([1e-3, 0, 0]))
+             solid_ellipsoid_inertia(mass, 15, 5, 5), F_ext=np.array([1e-3, 0, 0]), fixed=2)
     params = dict(collision=1, rho0=1.0, kT=0.0, gamma_bead=paper_gamma_to_lattice(20.0), seed=seed, precision=precision,
                   compensate_force=1, **mrt_rates(NU_PAPER))
     return Workload("ellipsoid_adjoint_96^3", 96, 96, 96, params, [b], None, 3000)

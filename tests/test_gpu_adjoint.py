@@ -1,0 +1,97 @@
+"""Hand-written adjoint of the deterministic step (lb_adjoint_drag) against
+the oracle's reverse pass (itself pinned to finite differences on the CPU),
+in FP64 and FP32, periodic and pore, BGK and MRT, several checkpoint
+schedules; and the autograd wrapper.
+
+Tolerances: FP64 J to 1e-12 and gradients to 1e-8 relative (the two reverse
+passes differ in formulation and summation order, accumulated over tens of
+steps); FP32 storage: gradients to 5e-3 relative."""
+import numpy as np
+import pytest
+
+from helpers import oracle_kw
+from oracle import oracle as O
+from paper_1604_01829_gb300 import workloads as Wl
+
+pytestmark = pytest.mark.gpu
+
+MRT = dict(collision=1, gamma_shear=-0.3, gamma_bulk=-0.3, gamma_odd=0.1, gamma_even=0.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1604_01829_gb300 import build
+    build.build()
+
+
+def _pair(precision, params, pore=None, gamma=0.1, n=12):
+    from paper_1604_01829_gb300 import lb
+    params = dict(params, gamma_bead=gamma, compensate_force=0 if pore else 1)
+    g = lb.LB(n, n, n, precision=precision, **params)
+    o = O.OracleLB(n, n, n, **oracle_kw(params))
+    if pore:
+        g.lb_set_pore(*pore)
+        o.set_pore(*pore)
+    sph = Wl.sphere_raspberry(2.0)
+    for tgt in (g, o):
+        tgt_add = tgt.lb_add_raspberry if hasattr(tgt, "lb_add_raspberry") else tgt.add_raspberry
+        tgt_add(sph, [6.3, 5.9, 6.1], [1, 0, 0, 0], 40.0, (60, 60, 60), (0, 0, 2e-3), (0, 0, 0), 2)
+    g.lb_step(5)
+    o.step(5)
+    return g, o
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("case", ["mrt", "bgk", "pore"])
+@pytest.mark.parametrize("checkpoints", [0, 3, 30])
+def test_adjoint_matches_oracle(precision, case, checkpoints):
+    params = dict(collision=0, tau=0.9) if case == "bgk" else dict(MRT)
+    pore = (5.5, 2) if case == "pore" else None
+    g, o = _pair(precision, params, pore)
+    Jg, dgg, dsg = g.lb_adjoint_drag(30, 10, body=0, axis=2, checkpoints=checkpoints)
+    Jo, dgo, dso = o.adjoint_drag(30, 10, body=0, axis=2)
+    if precision == 64:
+        assert abs(Jg - Jo) <= 1e-9 * abs(Jo)
+        assert abs(dgg - dgo) <= 1e-8 * abs(dgo)
+        assert np.abs(dsg - dso).max() <= 1e-8 * np.abs(dso).max()
+    else:
+        assert abs(Jg - Jo) <= 2e-5 * abs(Jo)
+        assert abs(dgg - dgo) <= 5e-3 * abs(dgo)
+        assert np.abs(dsg - dso).max() <= 5e-3 * np.abs(dso).max()
+    # the handle ends where plain steps would leave it
+    assert np.abs(g.lb_get_populations() - o.populations()).max() <= (1e-12 if precision == 64 else 2e-5)
+
+
+def test_adjoint_rejects_noise_and_free_rotation():
+    from paper_1604_01829_gb300 import lb
+    g = lb.LB(8, 8, 8, precision=64, kT=1e-4, gamma_bead=0.1, **MRT)
+    g.lb_add_raspberry(Wl.sphere_raspberry(1.5), [4, 4, 4], fixed=2)
+    with pytest.raises(lb.LBError):
+        g.lb_adjoint_drag(4, 2)
+    h = lb.LB(8, 8, 8, precision=64, gamma_bead=0.1, **MRT)
+    h.lb_add_raspberry(Wl.sphere_raspberry(1.5), [4, 4, 4], fixed=0)
+    with pytest.raises(lb.LBError):
+        h.lb_adjoint_drag(4, 2)
+
+
+def test_autograd_function_chains_the_adjoint():
+    import torch
+    from paper_1604_01829_gb300 import adjoint, lb
+    sph = Wl.sphere_raspberry(2.0)
+
+    def make(gamma, beads):
+        L = lb.LB(12, 12, 12, precision=64, gamma_bead=gamma, compensate_force=1, **MRT)
+        L.lb_add_raspberry(beads, [6.3, 5.9, 6.1], mass=40.0, inertia=(60, 60, 60), F_ext=(0, 0, 2e-3), fixed=2)
+        return L
+
+    gamma = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    beads = torch.tensor(sph, dtype=torch.float64, requires_grad=True)
+    J = adjoint.terminal_velocity(gamma, beads, make, 30, 10)
+    xi = 2e-3 / J                    # drag of the pulled colloid
+    xi.backward()
+    o = O.OracleLB(12, 12, 12, gamma_bead=0.1, compensate_force=1, **MRT)
+    o.add_raspberry(sph, [6.3, 5.9, 6.1], mass=40.0, inertia=(60, 60, 60), F_ext=(0, 0, 2e-3), fixed=2)
+    Jo, dgo, dso = o.adjoint_drag(30, 10)
+    assert abs(J.item() - Jo) <= 1e-9 * abs(Jo)
+    assert abs(gamma.grad.item() - (-2e-3 / Jo ** 2) * dgo) <= 1e-8 * abs((2e-3 / Jo ** 2) * dgo)
+    assert np.abs(beads.grad.numpy() - (-2e-3 / Jo ** 2) * dso).max() <= 1e-8 * np.abs((2e-3 / Jo ** 2) * dso).max()
