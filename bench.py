@@ -359,6 +359,7 @@ def measure_adjoint(args, torch, lb):
     velocity over the last steps, dJ/dgamma, dJ/ds for every bead, FP32
     storage, two-level checkpointing. Compared with the FP64 forward step on
     the same workload; the FP32 drag is compared with the FP64 drag."""
+    import numpy as np
     from paper_1604_01829_gb300 import workloads as W
     w32 = W.ellipsoid_adjoint_96(precision=32)
     T, Wn = args.adjoint_steps, max(1, args.adjoint_steps // 15)
