@@ -134,6 +134,25 @@ class ClockSampler:
 ARGS = None
 
 
+def make_reducer(dist, device):
+    """max over ranks of a host float (identity without a process group)."""
+    def barrier_max(v):
+        if dist is None:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return barrier_max
+
+
+def whole_job_mlups(nodes_per_rank, steps, world_size, max_ms):
+    """Weak scaling: every rank advances its own replica of `nodes_per_rank`
+    nodes; the job's throughput is all ranks' node updates over the slowest
+    rank's time."""
+    return nodes_per_rank * steps * world_size / (max_ms * 1e-3) / 1e6
+
+
 def build_workload(precision):
     from paper_1604_01829_gb300 import workloads as W
     L = ARGS.lattice if ARGS else 256
@@ -153,12 +172,7 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    def barrier_max(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier_max = make_reducer(dist, "cuda")
 
     def measure(precision, steps, warmup, with_clocks):
         w = build_workload(precision)
@@ -195,7 +209,7 @@ def run_ours(args, ws, rank, local):
     main = measure(32, args.steps, args.warmup, True)
     N = main["nodes"]
     K = args.steps
-    value = N * K * ws / (main["ms"] * 1e-3) / 1e6
+    value = whole_job_mlups(N, K, ws, main["ms"])
     peak, peak_kind = measured_peak()
     bytes_per_node = 2 * 19 * 4
     achieved = bytes_per_node * N / (main["kernel_ms"] * 1e-3) / 1e9
