@@ -559,3 +559,41 @@ def test_drag_adjoint_matches_finite_differences(pore):
     plain = base.clone()
     plain.step(30)
     assert np.array_equal(plain.populations(), run.populations())
+
+
+# ------------------------------------------------------------- Hasimoto pin
+
+def _mean_flow_drag(L, R=1.5, gamma=0.3, g=1e-6):
+    """Drag of a fixed raspberry in a periodic box driven by a uniform force
+    density g: xi = g N / U_inf, where the mean fluid velocity approaches its
+    steady value U_inf as a single exponential once the viscous transient
+    (~L^2/nu) has gone; U_inf from three equally spaced samples (Aitken)."""
+    from paper_1604_01829_gb300 import workloads as W
+    o = O.OracleLB(L, L, L, collision=0, tau=1.0, gamma_bead=gamma, body_force=(g, 0, 0))
+    o.add_raspberry(W.sphere_raspberry(R), [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], fixed=1)
+    o.step(int(1.5 * L * L))
+    us = []
+    for k in range(3):
+        rho, u = o.node_velocity()
+        us.append((rho * u[:, 0]).sum() / rho.sum())
+        if k < 2:
+            o.step(int(0.6 * L * L))
+    U1, U2, U3 = us
+    return g * L ** 3 / ((U1 * U3 - U2 * U2) / (U1 + U3 - 2 * U2))
+
+
+def test_hasimoto_finite_size_slope():
+    """Sec. 2.4, Eq. (hasimoto) in drag form (the printed '6 rho eta' read as
+    6 pi eta): for a periodic array of drag centres 1/xi(L) = 1/xi_0 -
+    2.837/(6 pi eta L) + O(L^-3), whatever the raspberry's permeability (the
+    bead friction only sets xi_0). Fitted over L = 12-24 with the next
+    (L^-3) term free, the 1/L coefficient matches -2.837/(6 pi eta) with
+    eta = rho0 (tau - 1/2)/3."""
+    Ls = np.array([12, 16, 20, 24])
+    xi = np.array([_mean_flow_drag(int(L)) for L in Ls])
+    x = 1.0 / Ls
+    A = np.stack([np.ones_like(x), x, x ** 3], axis=1)
+    a, b, c = np.linalg.lstsq(A, 1.0 / xi, rcond=None)[0]
+    eta = 1.0 * (1.0 - 0.5) / 3.0
+    assert abs(b / (-2.837 / (6 * math.pi * eta)) - 1) < 0.02
+    assert np.all(np.diff(xi) < 0)   # drag falls towards infinite dilution
