@@ -230,8 +230,9 @@ lb_status lb_batch_set_populations(lb_batch_handle h, int inst, const double *ho
 /* Work schedule of the fluid kernel: tile_nodes (64, 128, 256) consecutive
  * nodes of one instance per CTA iteration, blocks_per_sm resident CTAs of
  * the persistent grid (tile_nodes * blocks_per_sm <= 1024), order 0 =
- * tiles dealt round-robin to CTAs, 1 = contiguous chunks. Results do not
- * depend on it. */
+ * tiles dealt round-robin to CTAs, 1 = contiguous chunks, 2 = no persistent
+ * grid: one CTA per tile, left to the hardware block scheduler
+ * (blocks_per_sm is then not used). Results do not depend on it. */
 lb_status lb_batch_set_schedule(lb_batch_handle h, int tile_nodes, int blocks_per_sm, int order);
 /* Measures every schedule for trial_steps steps on a snapshot of the state
  * (restored afterwards, so the simulation is unchanged), keeps the fastest;

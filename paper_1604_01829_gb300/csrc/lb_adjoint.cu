@@ -52,8 +52,8 @@ struct AdjArgs {
     Geom g;
     const void *fn;             // taped population buffer before step n (AA layout)
     bool odd;                   // parity of n
-    const double *Fprev;        // taped spread force read by step n ([3][N])
-    const double *Fnew;         // taped spread force written by step n
+    const void *Fprev;          // taped spread force read by step n ([3][N], storage precision)
+    const void *Fnew;           // taped spread force written by step n
     const double *gforce;       // uniform force density (3)
     const void *lam_in;         // adjoint of f_{n+1}, natural layout [19][N]
     void *lam_out;              // adjoint of f_n
@@ -245,8 +245,9 @@ __global__ void __launch_bounds__(128) k_adj_collide(const AdjArgs a) {
         lam[i] = is_wall(g, xd, yd, zd) ? lin[opp(i) * N + n] : lin[i * N + nidx(g, xd, yd, zd)];
         f[i] = (R)load_pre(fn, g, x, y, z, n, i, a.odd);
     }
-    const R Fx = (R)(a.gforce[0] + a.Fnew[n]), Fy = (R)(a.gforce[1] + a.Fnew[N + n]);
-    const R Fz = (R)(a.gforce[2] + a.Fnew[2 * N + n]);
+    const T *Fnew = static_cast<const T *>(a.Fnew);
+    const R Fx = (R)(a.gforce[0] + (double)Fnew[n]), Fy = (R)(a.gforce[1] + (double)Fnew[N + n]);
+    const R Fz = (R)(a.gforce[2] + (double)Fnew[2 * N + n]);
     R lFx, lFy, lFz;
     if constexpr (DEV) collide_adjoint<R, true>(lam, f, Fx, Fy, Fz, a.pf, lFx, lFy, lFz);
     else collide_adjoint<R, false>(lam, f, Fx, Fy, Fz, a.pd, lFx, lFy, lFz);
@@ -270,7 +271,7 @@ struct AdjCouple {
     bool odd;
     double rho0, gamma;
     const double *gforce;
-    const double *Fprev;
+    const void *Fprev;
     const void *lFn;            // adjoint of F_node of step n
     void *lam_f;                // adjoint of f_n (accumulated)
     void *lFp;                  // adjoint of F_prev_n (accumulated)
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(128) k_adj_couple(const AdjCouple a) {
         node_rho_j<R>(fn, g, xyz[0], xyz[1], xyz[2], n, a.odd, (R)a.rho0, rr, j);
         rho = (double)rr;
         for (int q = 0; q < 3; ++q)
-            uc[q] = ((double)j[q] + 0.5 * (a.gforce[q] + a.Fprev[q * g.N + n])) / rho;
+            uc[q] = ((double)j[q] + 0.5 * (a.gforce[q] + (double)static_cast<const T *>(a.Fprev)[q * g.N + n])) / rho;
     }
     double ub[3], lsum[3] = {0, 0, 0};
     const T *lFn = static_cast<const T *>(a.lFn);
@@ -452,16 +453,17 @@ namespace {
 
 struct Snapshot {
     void *f = nullptr;
-    double *F[2] = {nullptr, nullptr};
-    unsigned char *tiles[2] = {nullptr, nullptr};
+    void *F[2] = {nullptr, nullptr};
+    int *tiles[2] = {nullptr, nullptr};
+    int *tlist[2] = {nullptr, nullptr};   // list entries, then the count
     Body *bodies = nullptr;
     long long step = 0;
 };
 
 struct Tape {
     void *f = nullptr;        // populations before the step
-    double *Fprev = nullptr;  // spread force the step reads
-    double *Fnew = nullptr;   // spread force the step writes
+    void *Fprev = nullptr;    // spread force the step reads
+    void *Fnew = nullptr;     // spread force the step writes
     Body *bodies = nullptr;   // bodies before the step
     long long step = 0;
 };
@@ -491,8 +493,9 @@ extern "C" lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int bo
     cudaStream_t s = h->stream;
     const long long N = h->g.N;
     const size_t es = h->fp32 ? 4 : 8;
-    const size_t fbytes = es * 19 * (size_t)N, Fbytes = sizeof(double) * 3 * (size_t)N;
-    const size_t tbytes = (size_t)h->ntx * h->nty * h->ntz, bbytes = sizeof(Body) * nb;
+    const size_t fbytes = es * 19 * (size_t)N, Fbytes = es * 3 * (size_t)N;
+    const size_t tbytes = sizeof(int) * (size_t)h->ntx * h->nty * h->ntz, bbytes = sizeof(Body) * nb;
+    const size_t lbytes = sizeof(int) * (size_t)h->list_cap;
     int c = checkpoints > 0 ? checkpoints : (int)std::ceil(std::sqrt((double)nsteps));
     if (c > nsteps) c = nsteps;
     const int K = (nsteps + c - 1) / c;
@@ -516,6 +519,7 @@ extern "C" lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int bo
         for (int k = 0; k < 2; ++k) {
             ACUDA(amalloc(pool, &S.F[k], Fbytes));
             ACUDA(amalloc(pool, &S.tiles[k], tbytes));
+            ACUDA(amalloc(pool, &S.tlist[k], lbytes + sizeof(int)));
         }
         ACUDA(amalloc(pool, &S.bodies, bbytes));
     }
@@ -544,6 +548,9 @@ extern "C" lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int bo
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaMemcpyAsync(S.F[k], h->Fbuf[k], Fbytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(S.tiles[k], h->tiles[k], tbytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S.tlist[k], h->tlist[k], lbytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char *)S.tlist[k] + lbytes, h->tcount[k], sizeof(int), cudaMemcpyDeviceToDevice, s);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(S.bodies, h->db, bbytes, cudaMemcpyDeviceToDevice, s);
         S.step = h->step;
@@ -554,6 +561,9 @@ extern "C" lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int bo
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaMemcpyAsync(h->Fbuf[k], S.F[k], Fbytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->tiles[k], S.tiles[k], tbytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->tlist[k], S.tlist[k], lbytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->tcount[k], (char *)S.tlist[k] + lbytes, sizeof(int), cudaMemcpyDeviceToDevice, s);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->db, S.bodies, bbytes, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) {

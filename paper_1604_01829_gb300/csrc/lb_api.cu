@@ -1,6 +1,7 @@
 // C ABI (include/lb.h) and host runtime: parameter validation, device
 // memory, the per-step launch sequence, population and force I/O, kernel
 // timing. Every entry point returns an lb_status and never throws.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -93,11 +94,16 @@ lb_status upload_bodies(lb_ctx *h) {
             LB_CUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
         }
         LB_CUDA(h, cudaMemsetAsync(h->dFbead, 0, sizeof(double) * 3 * (size_t)std::max(nbeads, 1), h->stream));
-        const size_t fbytes = sizeof(double) * 3 * (size_t)h->g.N;
-        const size_t tbytes = (size_t)h->ntx * h->nty * h->ntz;
+        const size_t fbytes = (h->fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)h->g.N;
+        const long long ntiles = (long long)h->ntx * h->nty * h->ntz;
+        const size_t tbytes = sizeof(int) * (size_t)ntiles;
+        h->list_cap = (int)std::min<long long>(ntiles, 8LL * std::max(nbeads, 1));
         for (int k = 0; k < 2; ++k) {
             if ((s = dev_alloc(h, &h->Fbuf[k], fbytes)) != LB_OK) return s;
             if ((s = dev_alloc(h, &h->tiles[k], tbytes)) != LB_OK) return s;
+            if ((s = dev_alloc(h, &h->tlist[k], sizeof(int) * (size_t)h->list_cap)) != LB_OK) return s;
+            if ((s = dev_alloc(h, &h->tcount[k], sizeof(int))) != LB_OK) return s;
+            LB_CUDA(h, cudaMemsetAsync(h->tcount[k], 0, sizeof(int), h->stream));
             LB_CUDA(h, cudaMemsetAsync(h->Fbuf[k], 0, fbytes, h->stream));
             LB_CUDA(h, cudaMemsetAsync(h->tiles[k], 0, tbytes, h->stream));
         }
@@ -353,6 +359,7 @@ lb_status lb_destroy(lb_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
+                    h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
                     h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -401,6 +408,8 @@ lb_status lb_add_raspberry(lb_handle h, const double *beads, int nbeads, const d
     }
     for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
     b.mass = mass;
+    b.inv_mass = 1.0 / mass;
+    for (int a = 0; a < 3; ++a) b.inv_I[a] = 1.0 / inertia[a];
     if (fixed < 0 || fixed > 2) return fail(h, LB_ERR_ARG, "fixed must be 0, 1 or 2");
     b.fixed = fixed;
     const int id = (int)h->hb.size();
@@ -470,10 +479,12 @@ lb_status lb_step(lb_handle h, int nsteps) {
         if (nb > 0) {
             // previous step's second half kick (k > 0), this step's kick and
             // drift, and the clearing of this step's spread-force tiles
-            cudaError_t e = lbk::launch_step_pre(h->db, nb, k > 0, coupled ? h->Fbuf[cur] : nullptr,
-                                                 coupled ? h->tiles[cur] : nullptr, h->g,
-                                                 coupled ? h->ntx : 0, h->nty, h->ntz, h->stream);
+            cudaError_t e = lbk::launch_step_pre(h->db, nb, k > 0, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
+                                                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
+                                                 h->list_cap, h->g, h->ntx, h->nty, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
+            // the list of this buffer restarts empty for this step's coupling
+            if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
         }
         if (coupled) {
             lbk::CoupleArgs c{};
@@ -485,9 +496,12 @@ lb_status lb_step(lb_handle h, int nsteps) {
             c.gamma = h->p.gamma_bead;
             c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
             c.gforce = h->gforce;
+            c.gforce_f = h->gforce_f;
             c.Fprev = h->Fbuf[prev];
             c.Fcur = h->Fbuf[cur];
             c.tiles_cur = h->tiles[cur];
+            c.tlist = h->tlist[cur];
+            c.tcount = h->tcount[cur];
             c.ntx = h->ntx;
             c.nty = h->nty;
             c.s = h->ds;
@@ -634,6 +648,13 @@ lb_status lb_get_node_force(lb_handle h, double *host, size_t n) {
         return LB_OK;
     }
     const int last = (int)((h->step - 1) & 1);
+    if (h->fp32) {
+        std::vector<float> tmp(n);
+        LB_CUDA(h, cudaMemcpyAsync(tmp.data(), h->Fbuf[last], sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+        LB_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (size_t k = 0; k < n; ++k) host[k] = tmp[k];
+        return LB_OK;
+    }
     LB_CUDA(h, cudaMemcpyAsync(host, h->Fbuf[last], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return LB_OK;

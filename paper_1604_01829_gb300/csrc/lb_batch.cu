@@ -8,9 +8,10 @@
 // scheduling differs. All populations live in one pool (instance k at
 // element offset off_k, its own plane stride N_k); the fluid kernel walks a
 // flattened list of equal work tiles (TS consecutive nodes of one instance)
-// with a persistent grid, so uneven instances load-balance by construction.
-// Tile size, blocks per SM and the tile-to-CTA order are chosen by a
-// measuring autotuner on a snapshot of the state, restored afterwards.
+// with a persistent grid or one CTA per tile, so uneven instances
+// load-balance by construction. Tile size, blocks per SM and the tile-to-CTA
+// order are chosen by a measuring autotuner on a snapshot of the state,
+// restored afterwards.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -53,8 +54,8 @@ struct BatchArgs {
     CollParams<double> pd;       // collision constants shared by all instances (COMMON kernels)
     CollParams<float> pf;
     void *pool;
-    const double *F;             // spread force of this step (pool), nullptr without bodies
-    const unsigned char *tiles;
+    const void *F;               // spread force of this step (pool, storage precision), nullptr without bodies
+    const int *tiles;
     const unsigned long long *step_base;
     uint32_t step_off;
 };
@@ -147,10 +148,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         if constexpr (DEV) { Fx = I.gf[0]; Fy = I.gf[1]; Fz = I.gf[2]; }
         else { Fx = I.gd[0]; Fy = I.gd[1]; Fz = I.gd[2]; }
         if (a.tiles && a.tiles[I.toff + tile_of(x, y, (int)z, I.ntx, I.nty)]) {
-            const double *Fn = a.F + I.foff;
-            Fx += (R)Fn[n];
-            Fy += (R)Fn[(size_t)N + n];
-            Fz += (R)Fn[2 * (size_t)N + n];
+            const T *Fn = static_cast<const T *>(a.F) + I.foff;
+            Fx += Fn[n];
+            Fy += Fn[(size_t)N + n];
+            Fz += Fn[2 * (size_t)N + n];
         }
         uint32_t step = 0;
         if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;
@@ -182,9 +183,11 @@ struct BatchCouple {
     const BInst *inst;
     const void *pool;
     bool fp32, odd;
-    const double *Fprev;
-    double *Fcur;
-    unsigned char *tiles_cur;
+    const void *Fprev;
+    void *Fcur;
+    int *tiles_cur;
+    int *tlist;
+    int *tcount;
     const double *s;
     const int *bead_body;
     const int *bead_rng;          // bead index within its own lattice
@@ -212,9 +215,13 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.gamma = I.gamma;
     a.noise_amp = I.noise_amp;
     a.gforce = I.gd;
-    a.Fprev = b.Fprev + I.foff;
-    a.Fcur = b.Fcur + I.foff;
+    a.gforce_f = I.gf;
+    a.Fprev = static_cast<const T *>(b.Fprev) + I.foff;
+    a.Fcur = static_cast<T *>(b.Fcur) + I.foff;
     a.tiles_cur = b.tiles_cur + I.toff;
+    a.tlist = b.tlist;
+    a.tcount = b.tcount;
+    a.tile_base = (int)I.toff;
     a.ntx = I.ntx;
     a.nty = I.nty;
     a.s = b.s;
@@ -232,41 +239,40 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
 
 // previous step's second half kick (optional), this step's kick and drift,
 // and the clearing of every flagged tile of this step's force pool
-__global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, double *F, unsigned char *tiles,
-                            const BInst *inst, const long long *flag_start, int n, long long ntiles) {
+template <typename T>
+__global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
+                            const int *tcount, const BInst *inst, const long long *flag_start, int n) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < nb) {
-        Body &B = bodies[t];
+    if (threadIdx.x == 0 && blockIdx.x < nb) {     // one body per block
+        Body B = bodies[blockIdx.x];
         if (finish_prev) kick2(B);
         kick_drift(B);
+        bodies[blockIdx.x] = B;
     }
-    if (!tiles || t >= ntiles || !tiles[t]) return;
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (flag_start[mid] <= t) lo = mid; else hi = mid;
-    }
-    const BInst &I = inst[lo];
-    const long long lt = t - flag_start[lo];
-    const int tx = (int)(lt % I.ntx), ty = (int)((lt / I.ntx) % I.nty), tz = (int)(lt / ((long long)I.ntx * I.nty));
-    double *Fi = F + I.foff;
-    for (int dz = 0; dz < 4; ++dz) {
-        const int z = 4 * tz + dz;
-        if (z >= I.g.nz) break;
-        for (int dy = 0; dy < 4; ++dy) {
-            const int y = 4 * ty + dy;
-            if (y >= I.g.ny) break;
-            for (int dx = 0; dx < 4; ++dx) {
-                const int x = 4 * tx + dx;
-                if (x >= I.g.nx) break;
-                const long long nn = nidx(I.g, x, y, z);
-                Fi[nn] = 0.0;
-                Fi[I.g.N + nn] = 0.0;
-                Fi[2 * I.g.N + nn] = 0.0;
-            }
+    if (!tiles) return;
+    // one thread per (listed tile, node of the tile)
+    const long long total = 64LL * (*tcount);
+    for (long long i = t; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long gt = tlist[i >> 6];
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (flag_start[mid] <= gt) lo = mid; else hi = mid;
         }
+        const BInst &I = inst[lo];
+        const int lt = (int)(gt - flag_start[lo]);
+        const int l = (int)(i & 63);
+        const int tx = lt % I.ntx, ty = (lt / I.ntx) % I.nty, tz = lt / (I.ntx * I.nty);
+        const int x = 4 * tx + (l & 3), y = 4 * ty + ((l >> 2) & 3), z = 4 * tz + (l >> 4);
+        if (x < I.g.nx && y < I.g.ny && z < I.g.nz) {
+            T *Fi = F + I.foff;
+            const long long nn = nidx(I.g, x, y, z);
+            Fi[nn] = T(0);
+            Fi[I.g.N + nn] = T(0);
+            Fi[2 * I.g.N + nn] = T(0);
+        }
+        if (l == 0) tiles[gt] = 0;
     }
-    tiles[t] = 0;
 }
 
 template <typename T>
@@ -326,8 +332,11 @@ struct lb_batch_ctx {
     std::vector<long long> nfluid;
     long long Ntot = 0, Ttot = 0, Ftot = 0;
     void *pool = nullptr;
-    double *Fbuf[2] = {nullptr, nullptr};
-    unsigned char *tiles[2] = {nullptr, nullptr};
+    void *Fbuf[2] = {nullptr, nullptr};     // force pools, storage precision
+    int *tiles[2] = {nullptr, nullptr};
+    int *tlist[2] = {nullptr, nullptr};
+    int *tcount[2] = {nullptr, nullptr};
+    int list_cap = 0;
     BInst *dinst = nullptr;
     int *dtile_start = nullptr;
     int *dtile_inst = nullptr;
@@ -520,11 +529,16 @@ lb_status upload(lb_batch_ctx *h) {
             BCUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
             BCUDA(h, cudaMemcpyAsync(h->dbead_rng, h->hbead_rng.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
         }
+        const size_t fb = (h->fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)h->Ftot;
+        h->list_cap = (int)std::min<long long>(h->Ttot, 8LL * std::max(nbeads, 1));
         for (int k = 0; k < 2; ++k) {
-            if ((s = balloc(h, &h->Fbuf[k], sizeof(double) * 3 * (size_t)h->Ftot)) != LB_OK) return s;
-            if ((s = balloc(h, &h->tiles[k], (size_t)h->Ttot)) != LB_OK) return s;
-            BCUDA(h, cudaMemsetAsync(h->Fbuf[k], 0, sizeof(double) * 3 * (size_t)h->Ftot, h->stream));
-            BCUDA(h, cudaMemsetAsync(h->tiles[k], 0, (size_t)h->Ttot, h->stream));
+            if ((s = balloc(h, &h->Fbuf[k], fb)) != LB_OK) return s;
+            if ((s = balloc(h, &h->tiles[k], sizeof(int) * (size_t)h->Ttot)) != LB_OK) return s;
+            if ((s = balloc(h, &h->tlist[k], sizeof(int) * (size_t)h->list_cap)) != LB_OK) return s;
+            if ((s = balloc(h, &h->tcount[k], sizeof(int))) != LB_OK) return s;
+            BCUDA(h, cudaMemsetAsync(h->Fbuf[k], 0, fb, h->stream));
+            BCUDA(h, cudaMemsetAsync(h->tiles[k], 0, sizeof(int) * (size_t)h->Ttot, h->stream));
+            BCUDA(h, cudaMemsetAsync(h->tcount[k], 0, sizeof(int), h->stream));
         }
     }
     BCUDA(h, cudaStreamSynchronize(h->stream));
@@ -538,11 +552,18 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
     const bool coupled = nb > 0 && nbeads > 0;
     if (nb > 0) {
-        const long long nthreads = std::max<long long>(nb, coupled ? h->Ttot : 0);
-        lbk::k_batch_pre<<<(unsigned)((nthreads + 255) / 256), 256, 0, h->stream>>>(
-            h->db, nb, finish_prev ? 1 : 0, coupled ? h->Fbuf[cur] : nullptr, coupled ? h->tiles[cur] : nullptr,
-            h->dinst, h->dflag_start, h->n, coupled ? h->Ttot : 0);
+        const long long nthreads = std::min<long long>(64LL * h->list_cap, 152LL * 2048);
+        const unsigned pg = std::max<unsigned>((unsigned)((nthreads + 255) / 256), (unsigned)nb);
+        if (h->fp32)
+            lbk::k_batch_pre<float><<<pg, 256, 0, h->stream>>>(
+                h->db, nb, finish_prev ? 1 : 0, coupled ? (float *)h->Fbuf[cur] : nullptr,
+                coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n);
+        else
+            lbk::k_batch_pre<double><<<pg, 256, 0, h->stream>>>(
+                h->db, nb, finish_prev ? 1 : 0, coupled ? (double *)h->Fbuf[cur] : nullptr,
+                coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n);
         BCUDA(h, cudaGetLastError());
+        if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
     }
     if (coupled) {
         lbk::BatchCouple c{};
@@ -553,6 +574,8 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
         c.Fprev = h->Fbuf[prev];
         c.Fcur = h->Fbuf[cur];
         c.tiles_cur = h->tiles[cur];
+        c.tlist = h->tlist[cur];
+        c.tcount = h->tcount[cur];
         c.s = h->ds;
         c.bead_body = h->dbody_of;
         c.bead_rng = h->dbead_rng;
@@ -575,9 +598,10 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     a.pd = h->hinst[0].pd;
     a.pf = h->hinst[0].pf;
     int grid = h->sms * std::min(h->bpsm, h->resident > 0 ? h->resident : h->bpsm);
+    if (h->order == 2) grid = h->ntiles;    // one CTA per tile, round-robin loop runs once
     if (grid > h->ntiles) grid = h->ntiles;
     if (grid < 1) grid = 1;
-    a.order = h->order;
+    a.order = h->order == 1 ? 1 : 0;
     a.chunk = (h->ntiles + grid - 1) / grid;
     a.pool = h->pool;
     a.F = coupled ? h->Fbuf[cur] : nullptr;
@@ -788,7 +812,8 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->dinst, h->dtile_start, h->dtile_inst,
+    void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
+                    h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
                     h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -827,7 +852,8 @@ lb_status lb_batch_add_raspberry(lb_batch_handle h, int k, const double *beads, 
     lb_status s = check(h, k);
     if (s != LB_OK) return s;
     if (h->uploaded) return bfail(h, LB_ERR_STATE, "bodies must be added before the first step");
-    if (nbeads < 0 || (nbeads > 0 && !beads) || !X || !q || !inertia || !(mass > 0.0))
+    if (nbeads < 0 || (nbeads > 0 && !beads) || !X || !q || !inertia || !(mass > 0.0) ||
+        !(inertia[0] > 0 && inertia[1] > 0 && inertia[2] > 0))
         return bfail(h, LB_ERR_ARG, "bad raspberry arguments");
     const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
     if (!(qn > 0.0)) return bfail(h, LB_ERR_ARG, "quaternion must be non-zero");
@@ -840,6 +866,8 @@ lb_status lb_batch_add_raspberry(lb_batch_handle h, int k, const double *beads, 
     }
     for (int a = 0; a < 4; ++a) b.q[a] = q[a] / qn;
     b.mass = mass;
+    b.inv_mass = 1.0 / mass;
+    for (int a = 0; a < 3; ++a) b.inv_I[a] = 1.0 / inertia[a];
     if (fixed < 0 || fixed > 2) return bfail(h, LB_ERR_ARG, "fixed must be 0, 1 or 2");
     b.fixed = fixed;
     b.inst = k;
@@ -957,8 +985,8 @@ lb_status lb_batch_set_schedule(lb_batch_handle h, int tile_nodes, int blocks_pe
     if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
     // the fluid kernel is capped at 64 registers, so 1024 threads per SM are resident
     if ((tile_nodes != 64 && tile_nodes != 128 && tile_nodes != 256) || blocks_per_sm < 1 ||
-        blocks_per_sm * tile_nodes > 1024 || (order != 0 && order != 1))
-        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 1024, order 0/1");
+        blocks_per_sm * tile_nodes > 1024 || order < 0 || order > 2)
+        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 1024, order 0/1/2");
     h->TS = tile_nodes;
     h->bpsm = blocks_per_sm;
     h->order = order;
@@ -977,20 +1005,27 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     const int nb = (int)h->hb.size();
     void *snap = nullptr;
     Body *bsnap = nullptr;
-    double *fsnap[2] = {nullptr, nullptr};
-    unsigned char *tsnap[2] = {nullptr, nullptr};
-    const size_t fbytes = sizeof(double) * 3 * (size_t)h->Ftot;
+    void *fsnap[2] = {nullptr, nullptr};
+    int *tsnap[2] = {nullptr, nullptr};
+    int *lsnap[2] = {nullptr, nullptr};
+    const size_t fbytes = (h->fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)h->Ftot;
     if (cudaMalloc(&snap, pbytes) != cudaSuccess) { cudaGetLastError(); return bfail(h, LB_ERR_OOM, "no room for the autotune snapshot"); }
     bool ok = true;
     if (nb > 0) {
         ok = cudaMalloc((void **)&bsnap, sizeof(Body) * nb) == cudaSuccess;
         for (int k = 0; k < 2 && ok; ++k)
-            ok = cudaMalloc((void **)&fsnap[k], fbytes) == cudaSuccess && cudaMalloc((void **)&tsnap[k], (size_t)h->Ttot) == cudaSuccess;
+            ok = cudaMalloc((void **)&fsnap[k], fbytes) == cudaSuccess &&
+                 cudaMalloc((void **)&tsnap[k], sizeof(int) * (size_t)h->Ttot) == cudaSuccess &&
+                 cudaMalloc((void **)&lsnap[k], sizeof(int) * ((size_t)h->list_cap + 1)) == cudaSuccess;
     }
     auto release = [&]() {
         cudaFree(snap);
         if (bsnap) cudaFree(bsnap);
-        for (int k = 0; k < 2; ++k) { if (fsnap[k]) cudaFree(fsnap[k]); if (tsnap[k]) cudaFree(tsnap[k]); }
+        for (int k = 0; k < 2; ++k) {
+            if (fsnap[k]) cudaFree(fsnap[k]);
+            if (tsnap[k]) cudaFree(tsnap[k]);
+            if (lsnap[k]) cudaFree(lsnap[k]);
+        }
     };
     if (!ok) { cudaGetLastError(); release(); return bfail(h, LB_ERR_OOM, "no room for the autotune snapshot"); }
     auto copy_state = [&](bool save) -> cudaError_t {
@@ -1000,7 +1035,11 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
             for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
                 e = cudaMemcpyAsync(save ? (void *)fsnap[k] : (void *)h->Fbuf[k], save ? (void *)h->Fbuf[k] : (void *)fsnap[k], fbytes, cudaMemcpyDeviceToDevice, h->stream);
                 if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(save ? (void *)tsnap[k] : (void *)h->tiles[k], save ? (void *)h->tiles[k] : (void *)tsnap[k], (size_t)h->Ttot, cudaMemcpyDeviceToDevice, h->stream);
+                    e = cudaMemcpyAsync(save ? (void *)tsnap[k] : (void *)h->tiles[k], save ? (void *)h->tiles[k] : (void *)tsnap[k], sizeof(int) * (size_t)h->Ttot, cudaMemcpyDeviceToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(save ? (void *)lsnap[k] : (void *)h->tlist[k], save ? (void *)h->tlist[k] : (void *)lsnap[k], sizeof(int) * (size_t)h->list_cap, cudaMemcpyDeviceToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(save ? (void *)(lsnap[k] + h->list_cap) : (void *)h->tcount[k], save ? (void *)h->tcount[k] : (void *)(lsnap[k] + h->list_cap), sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
             }
         }
         return e;
@@ -1021,7 +1060,8 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     int bt = h->TS, bb = h->bpsm, bo = h->order;
     for (int ts : tiles)
         for (int bps = 2; bps * ts <= 1024; bps *= 2)
-            for (int order = 0; order < 2; ++order) {
+            for (int order = 0; order < 3; ++order) {
+                if (order == 2 && bps != 2) continue;     // blocks_per_sm unused: one trial per tile size
                 if ((s = lb_batch_set_schedule(h, ts, bps, order)) != LB_OK) break;
                 // warm-up pair, then timed pairs
                 if ((s = lb_batch_step(h, 2)) != LB_OK) break;

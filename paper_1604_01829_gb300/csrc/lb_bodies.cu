@@ -13,43 +13,47 @@ namespace lbk {
 
 namespace {
 
-// Step prologue in one launch: threads [0, nb) finish the previous step's
-// bodies (second half kick) if asked and start this step's (half kick,
-// drift, rotation); every thread also clears one flagged 4x4x4 tile of this
-// step's spread-force buffer.
-__global__ void k_step_pre(Body *bodies, int nb, int finish_prev, double *F, unsigned char *tiles, Geom g,
-                           int ntx, int nty, int ntz) {
+// Step prologue in one launch: thread 0 of blocks [0, nb) finishes the
+// previous step's body (second half kick) if asked and starts this step's
+// (half kick, drift, rotation); every thread also clears nodes of the
+// flagged 4x4x4 tiles of this step's spread-force buffer.
+template <typename T>
+__global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
+                           const int *tcount, Geom g, int ntx, int nty) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < nb) {
-        Body &B = bodies[t];
+    // one body per block, so the FP64 work of the bodies spreads over SMs;
+    // a private copy means one read and one write of the record
+    if (threadIdx.x == 0 && blockIdx.x < nb) {
+        Body B = bodies[blockIdx.x];
         if (finish_prev) kick2(B);
         kick_drift(B);
+        bodies[blockIdx.x] = B;
     }
-    const long long nt = (long long)ntx * nty * ntz;
-    if (t >= nt || !tiles[t]) return;
-    const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
-    for (int dz = 0; dz < 4; ++dz) {
-        const int z = 4 * tz + dz;
-        if (z >= g.nz) break;
-        for (int dy = 0; dy < 4; ++dy) {
-            const int y = 4 * ty + dy;
-            if (y >= g.ny) break;
-            for (int dx = 0; dx < 4; ++dx) {
-                const int x = 4 * tx + dx;
-                if (x >= g.nx) break;
-                const long long n = nidx(g, x, y, z);
-                F[n] = 0.0;
-                F[g.N + n] = 0.0;
-                F[2 * g.N + n] = 0.0;
-            }
+    if (!tiles) return;
+    // one thread per (listed tile, node of the tile): zero the force, drop the flag
+    const long long total = 64LL * (*tcount);
+    for (long long i = t; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int tile = tlist[i >> 6];
+        const int l = (int)(i & 63);
+        const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+        const int x = 4 * tx + (l & 3), y = 4 * ty + ((l >> 2) & 3), z = 4 * tz + (l >> 4);
+        if (x < g.nx && y < g.ny && z < g.nz) {
+            const long long n = nidx(g, x, y, z);
+            F[n] = T(0);
+            F[g.N + n] = T(0);
+            F[2 * g.N + n] = T(0);
         }
+        if (l == 0) tiles[tile] = 0;
     }
-    tiles[t] = 0;
 }
 
 __global__ void k_kick2(Body *bodies, int nb) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) kick2(bodies[b]);
+    const int b = blockIdx.x;          // one body per block, as in k_step_pre
+    if (threadIdx.x == 0 && b < nb) {
+        Body B = bodies[b];
+        kick2(B);
+        bodies[b] = B;
+    }
 }
 
 template <typename T>
@@ -61,12 +65,15 @@ __global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
 
 }  // namespace
 
-cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, double *F, unsigned char *tiles,
-                            const Geom &g, int ntx, int nty, int ntz, cudaStream_t s) {
-    const long long nt = (long long)ntx * nty * ntz;
-    const long long n = nt > nbodies ? nt : nbodies;
-    k_step_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, F, tiles, g, ntx,
-                                                           nty, ntz);
+cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
+                            const int *tcount, int list_cap, const Geom &g, int ntx, int nty, cudaStream_t s) {
+    // enough threads for the bodies and for a full list (grid-stride beyond)
+    long long n = 64LL * list_cap;
+    if (n > 152LL * 2048) n = 152LL * 2048;
+    unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid < (unsigned)nbodies) grid = (unsigned)nbodies;
+    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty);
+    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty);
     return cudaGetLastError();
 }
 
@@ -80,7 +87,7 @@ cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s) {
 
 cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s) {
     if (nbodies <= 0) return cudaSuccess;
-    k_kick2<<<(nbodies + 63) / 64, 64, 0, s>>>(b, nbodies);
+    k_kick2<<<nbodies, 32, 0, s>>>(b, nbodies);
     return cudaGetLastError();
 }
 

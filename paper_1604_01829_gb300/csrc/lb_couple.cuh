@@ -54,29 +54,34 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
     const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
     const int n3[3] = {g.nx, g.ny, g.nz};
     int xyz[3];
-    double wt = 1.0;
+    // positions in FP64; the weight and the node sums in the storage precision
+    R wt = R(1);
     for (int q = 0; q < 3; ++q) {
         const double tq = r[q] - 0.5;
         const double fl = floor(tq);
-        const double fr = tq - fl;
+        const R fr = (R)(tq - fl);
         int b0 = (int)fl % n3[q];
         if (b0 < 0) b0 += n3[q];
         xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
-        wt *= o[q] ? fr : 1.0 - fr;
+        wt *= o[q] ? fr : R(1) - fr;
     }
     const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
     const bool fluid = active && !is_wall(g, xyz[0], xyz[1], xyz[2]);
-    double ub[3] = {0.0, 0.0, 0.0};
+    R ub[3] = {R(0), R(0), R(0)};
     if (fluid) {                         // wall nodes carry u = 0
         R rho, j[3];
         node_rho_j<R>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (R)a.rho0, rho, j);
         const R ir = R(1) / rho;
-        const R ux = (j[0] + R(0.5) * (R)(a.gforce[0] + a.Fprev[n])) * ir;
-        const R uy = (j[1] + R(0.5) * (R)(a.gforce[1] + a.Fprev[g.N + n])) * ir;
-        const R uz = (j[2] + R(0.5) * (R)(a.gforce[2] + a.Fprev[2 * g.N + n])) * ir;
-        ub[0] = wt * (double)ux;
-        ub[1] = wt * (double)uy;
-        ub[2] = wt * (double)uz;
+        const T *Fp = static_cast<const T *>(a.Fprev);
+        R gx, gy, gz;
+        if constexpr (sizeof(R) == 4) { gx = a.gforce_f[0]; gy = a.gforce_f[1]; gz = a.gforce_f[2]; }
+        else { gx = a.gforce[0]; gy = a.gforce[1]; gz = a.gforce[2]; }
+        const R ux = (j[0] + R(0.5) * (gx + Fp[n])) * ir;
+        const R uy = (j[1] + R(0.5) * (gy + Fp[g.N + n])) * ir;
+        const R uz = (j[2] + R(0.5) * (gz + Fp[2 * g.N + n])) * ir;
+        ub[0] = wt * ux;
+        ub[1] = wt * uy;
+        ub[2] = wt * uz;
     }
     for (int off = 1; off < 8; off <<= 1)
         for (int q = 0; q < 3; ++q) ub[q] += __shfl_xor_sync(0xffffffffu, ub[q], off, 8);
@@ -92,17 +97,20 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
             fs[1] = a.noise_amp * unit_uniform_d(rr.y);
             fs[2] = a.noise_amp * unit_uniform_d(rr.z);
         }
-        for (int q = 0; q < 3; ++q) Fb[q] = -a.gamma * (v[q] - ub[q]) + fs[q];
+        for (int q = 0; q < 3; ++q) Fb[q] = -a.gamma * (v[q] - (double)ub[q]) + fs[q];
         for (int q = 0; q < 3; ++q) a.F_bead[3 * k + q] = Fb[q];
     }
     for (int q = 0; q < 3; ++q) Fb[q] = __shfl_sync(0xffffffffu, Fb[q], 0, 8);
 
     // spread -w F_b onto this lane's node; a wall node takes nothing
     if (fluid) {
-        atomicAdd(&a.Fcur[n], -wt * Fb[0]);
-        atomicAdd(&a.Fcur[g.N + n], -wt * Fb[1]);
-        atomicAdd(&a.Fcur[2 * g.N + n], -wt * Fb[2]);
-        a.tiles_cur[tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty)] = 1;
+        T *Fc = static_cast<T *>(a.Fcur);
+        atomicAdd(&Fc[n], -wt * (T)Fb[0]);
+        atomicAdd(&Fc[g.N + n], -wt * (T)Fb[1]);
+        atomicAdd(&Fc[2 * g.N + n], -wt * (T)Fb[2]);
+        const int tile = (int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty);
+        // first flag of a tile also records it for clearing two steps later
+        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0) a.tlist[atomicAdd(a.tcount, 1)] = a.tile_base + tile;
     }
 
     // force and torque on the body: sum the (up to 4) beads of this warp

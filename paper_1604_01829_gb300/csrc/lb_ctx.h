@@ -27,8 +27,11 @@ struct lb_ctx {
     long long nfluid = 0;
     double sig[15] = {};
     // bead force fields (double buffered) and their 4x4x4 tile flags
-    double *Fbuf[2] = {nullptr, nullptr};
-    unsigned char *tiles[2] = {nullptr, nullptr};
+    void *Fbuf[2] = {nullptr, nullptr};     // [3][N] each, storage precision
+    int *tiles[2] = {nullptr, nullptr};      // 4x4x4 tile flags of each force buffer
+    int *tlist[2] = {nullptr, nullptr};      // flagged tiles of each buffer
+    int *tcount[2] = {nullptr, nullptr};     // entries of tlist
+    int list_cap = 0;
     int ntx = 0, nty = 0, ntz = 0;
     // bodies
     std::vector<Body> hb;

@@ -83,9 +83,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
         Fx = __ldg(a.gforce); Fy = __ldg(a.gforce + 1); Fz = __ldg(a.gforce + 2);
     }
     if (a.tiles && a.tiles[tile_of(x, y, z, a.ntx, a.nty)]) {
-        Fx += (R)a.Fn[n];
-        Fy += (R)a.Fn[N + n];
-        Fz += (R)a.Fn[2 * N + n];
+        const T *Fn = static_cast<const T *>(a.Fn);
+        Fx += Fn[n];
+        Fy += Fn[N + n];
+        Fz += Fn[2 * N + n];
     }
     uint32_t step = 0;
     if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;

@@ -156,9 +156,10 @@ __global__ void __launch_bounds__(kThreads, LB_TMA_MINB) k_collide_stream_tma(co
             const unsigned n = (unsigned)(x + y0 + z0);
             float Fx = g0, Fy = g1, Fz = g2;
             if (a.tiles && a.tiles[tile_of(x, y, z, a.ntx, a.nty)]) {
-                Fx += (float)a.Fn[n];
-                Fy += (float)a.Fn[(size_t)N32 + n];
-                Fz += (float)a.Fn[2 * (size_t)N32 + n];
+                const float *Fn = static_cast<const float *>(a.Fn);
+                Fx += Fn[n];
+                Fy += Fn[(size_t)N32 + n];
+                Fz += Fn[2 * (size_t)N32 + n];
             }
             uint32_t step = 0;
             if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;

@@ -32,8 +32,8 @@ struct FluidArgs {
     CollParams<float> pf;
     const double *gforce;        // device: uniform force density (3)
     const float *gforce_f;       // device: the same, rounded to FP32
-    const double *Fn;            // device: spread bead force [3][N] or nullptr
-    const unsigned char *tiles;  // device: 4x4x4 tile flags of Fn or nullptr
+    const void *Fn;              // device: spread bead force [3][N] in the storage precision, or nullptr
+    const int *tiles;            // device: 4x4x4 tile flags of Fn or nullptr
     int ntx, nty;
     uint32_t key0, key1, instance;
     const unsigned long long *step_base;  // device step counter of the first step of this launch group
@@ -52,6 +52,7 @@ struct Body {
     double R[9];                     // rotation of the running step (row-major, lab = R body)
     double wl[3];                    // lab-frame omega of the running step
     double mass, I[3];
+    double inv_mass, inv_I[3];       // reciprocals, so the step divides nothing
     int fixed;
     int inst;                        // instance of a batch (0 for a single lattice)
 };
@@ -65,9 +66,13 @@ struct CoupleArgs {
     double gamma;
     double noise_amp;            // sqrt(2 kT gamma), 0 = off
     const double *gforce;        // uniform force density (3)
-    const double *Fprev;         // [3][N] spread force of the previous step
-    double *Fcur;                // [3][N] spread force of this step (zero on entry)
-    unsigned char *tiles_cur;    // flags of Fcur
+    const void *Fprev;           // [3][N] spread force of the previous step (storage precision)
+    void *Fcur;                  // [3][N] spread force of this step (zero on entry)
+    const float *gforce_f;       // uniform force density rounded to FP32
+    int *tiles_cur;              // flags of Fcur
+    int *tlist;                  // flagged tiles of Fcur, in the order they were flagged
+    int *tcount;                 // entries of tlist
+    int tile_base;               // added to tile indices recorded in tlist (batch pools)
     int ntx, nty;
     const double *s;             // body-frame bead offsets [3*nbeads]
     const int *bead_body;        // body index of each bead
@@ -97,8 +102,8 @@ cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, do
                            int nblocks, double *out4, cudaStream_t s);
 cudaError_t launch_advance(unsigned long long *step, unsigned int by, cudaStream_t s);
 
-cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, double *F, unsigned char *tiles,
-                            const Geom &g, int ntx, int nty, int ntz, cudaStream_t s);
+cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
+                            const int *tcount, int list_cap, const Geom &g, int ntx, int nty, cudaStream_t s);
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
 cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s);
 

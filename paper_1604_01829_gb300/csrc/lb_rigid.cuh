@@ -22,23 +22,25 @@ __device__ __forceinline__ void quat_to_R(const double q[4], double R[9]) {
 }
 
 // Euler's equations I dw/dt = T - w x (I w) over half a step, explicit in w
-__device__ __forceinline__ void euler_half_explicit(double w[3], const double I[3], const double T[3]) {
+__device__ __forceinline__ void euler_half_explicit(double w[3], const double I[3], const double invI[3],
+                                                    const double T[3]) {
     const double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]};
     double c[3];
     cross3(w, Iw, c);
-    for (int a = 0; a < 3; ++a) w[a] += 0.5 * (T[a] - c[a]) / I[a];
+    for (int a = 0; a < 3; ++a) w[a] += 0.5 * (T[a] - c[a]) * invI[a];
 }
 
 // ... and implicit in w (fixed point), so that the two half kicks around a
 // step boundary form the trapezoidal rule: a second-order, time-symmetric
 // rotation update like the velocity-Verlet rotation schemes of Sec. 2.3.
-__device__ __forceinline__ void euler_half_implicit(double w[3], const double I[3], const double T[3]) {
+__device__ __forceinline__ void euler_half_implicit(double w[3], const double I[3], const double invI[3],
+                                                    const double T[3]) {
     const double w0[3] = {w[0], w[1], w[2]};
     for (int it = 0; it < 6; ++it) {
         const double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]};
         double c[3];
         cross3(w, Iw, c);
-        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * (T[a] - c[a]) / I[a];
+        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * (T[a] - c[a]) * invI[a];
     }
 }
 
@@ -56,9 +58,9 @@ __device__ __forceinline__ void kick2(Body &B) {
         B.T_last[a] = Tb[a];
     }
     if (B.fixed == 1) return;
-    for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * B.F_tot[a] / B.mass;
+    for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * B.F_tot[a] * B.inv_mass;
     if (B.fixed == 2) return;          // orientation held
-    euler_half_implicit(B.w, B.I, Tb);
+    euler_half_implicit(B.w, B.I, B.inv_I, Tb);
 }
 
 // First half kick with last step's force and torque, then drift: X += V,
@@ -66,30 +68,31 @@ __device__ __forceinline__ void kick2(Body &B) {
 __device__ __forceinline__ void kick_drift(Body &B) {
     if (B.fixed == 2) {                // translation only, orientation held
         for (int a = 0; a < 3; ++a) {
-            B.V[a] += 0.5 * B.F_last[a] / B.mass;
+            B.V[a] += 0.5 * B.F_last[a] * B.inv_mass;
             B.X[a] += B.V[a];
             B.w[a] = 0.0;
         }
     } else if (!B.fixed) {
         for (int a = 0; a < 3; ++a) {
-            B.V[a] += 0.5 * B.F_last[a] / B.mass;
+            B.V[a] += 0.5 * B.F_last[a] * B.inv_mass;
             B.X[a] += B.V[a];
         }
-        euler_half_explicit(B.w, B.I, B.T_last);
+        euler_half_explicit(B.w, B.I, B.inv_I, B.T_last);
         const double wn = sqrt(B.w[0] * B.w[0] + B.w[1] * B.w[1] + B.w[2] * B.w[2]);
         double *q = B.q;
         if (wn > 0.0) {
             double sh, ch;
             sincos(0.5 * wn, &sh, &ch);
-            const double d[4] = {ch, sh * B.w[0] / wn, sh * B.w[1] / wn, sh * B.w[2] / wn};
+            const double sw = sh / wn;
+            const double d[4] = {ch, sw * B.w[0], sw * B.w[1], sw * B.w[2]};
             const double r[4] = {q[0] * d[0] - q[1] * d[1] - q[2] * d[2] - q[3] * d[3],
                                  q[0] * d[1] + q[1] * d[0] + q[2] * d[3] - q[3] * d[2],
                                  q[0] * d[2] - q[1] * d[3] + q[2] * d[0] + q[3] * d[1],
                                  q[0] * d[3] + q[1] * d[2] - q[2] * d[1] + q[3] * d[0]};
             for (int a = 0; a < 4; ++a) q[a] = r[a];
         }
-        const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        for (int a = 0; a < 4; ++a) q[a] /= qn;
+        const double iqn = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int a = 0; a < 4; ++a) q[a] *= iqn;
     }
     quat_to_R(B.q, B.R);
     for (int a = 0; a < 3; ++a) B.wl[a] = B.R[3 * a] * B.w[0] + B.R[3 * a + 1] * B.w[1] + B.R[3 * a + 2] * B.w[2];

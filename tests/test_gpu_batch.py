@@ -91,7 +91,7 @@ def test_batch_matches_oracle_per_instance(precision, noise):
         assert max(errs) <= TOL[precision], errs
 
 
-@pytest.mark.parametrize("schedule", [(64, 4, 0), (128, 8, 1), (256, 4, 0), (256, 2, 1)])
+@pytest.mark.parametrize("schedule", [(64, 4, 0), (128, 8, 1), (256, 4, 0), (256, 2, 1), (128, 2, 2)])
 def test_batch_schedule_does_not_change_results(schedule):
     cases = _cases(True)
     B, orcs = _build(cases, 32)
