@@ -55,6 +55,29 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def copy_ceiling(torch, stream, nbytes=2 << 30, reps=10):
+    """Live device-copy bandwidth (read + write bytes per second) of a plain
+    torch copy between two buffers far larger than L2, timed with events on
+    the given stream: a second denominator beside the roofline peak."""
+    n = nbytes // 4
+    with torch.cuda.stream(stream):
+        src = torch.ones(n, dtype=torch.float32, device="cuda")
+        dst = torch.empty_like(src)
+        for _ in range(3):
+            dst.copy_(src)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            dst.copy_(src)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del src, dst
+    torch.cuda.empty_cache()
+    return 2.0 * n * 4 / (ms * 1e-3) / 1e9
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("lb_fluid.cu", "lb_collide.cuh", "lb_device.cuh", "lb_internal.h"):
@@ -62,20 +85,32 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_key):
-    """DRAM bytes per launch of the collide kernel from the committed ncu
-    summary, or None if none exists or the kernel changed since."""
+def ncu_entry(key):
+    """An entry of the committed ncu summary, or None if there is none or the
+    kernel sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
-        e = d.get(workload_key)
+        e = json.load(open(p)).get(key)
         if not e or e.get("kernel_source_hash") != kernel_source_hash():
             return None
-        return float(e["dram_bytes_per_launch"])
+        return e
     except Exception:
         return None
+
+
+def ncu_traffic(workload_key):
+    """DRAM bytes per launch of the collide kernel from the committed ncu
+    summary, or None if none exists or the kernel changed since."""
+    e = ncu_entry(workload_key)
+    return None if e is None else float(e["dram_bytes_per_launch"])
+
+
+# FP64 pipe of GB300: the nominal 1.25 TFLOP/s FP64 over 152 SMs at 2.07 GHz
+# is 2 FMA lanes per SM per clock, i.e. this many FP64 thread-instructions/s
+FP64_PIPE_INSTR_PER_S = 152 * 2 * 2.07e9
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 class ClockSampler:
@@ -214,6 +249,7 @@ def run_ours(args, ws, rank, local):
     bytes_per_node = 2 * 19 * 4
     achieved = bytes_per_node * N / (main["kernel_ms"] * 1e-3) / 1e9
     traffic = ncu_traffic(WORKLOAD)
+    copy_gbs = copy_ceiling(torch, torch.cuda.Stream())
 
     # end to end through the C ABI with host buffers: per step the host sets
     # the external forces of every body (H2D) and reads every body's force
@@ -247,8 +283,23 @@ def run_ours(args, ws, rank, local):
         fp64["L"].close()
         fp64_line = {"value": round(fp64_value, 1), "unit": "MLUPS", "steps": k64,
                      "ms_per_step": round(fp64["ms"] / k64, 4),
+                     "kernel_ms": round(fp64["kernel_ms"], 4),
                      "kernel_achieved_gbs": round(fp64_ach, 1),
-                     "frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8}
+                     "hbm_frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8}
+        # the FP64 step is bound by the FP64 pipe: instruction counts per node
+        # from the committed ncu capture of the same kernel
+        ops = ncu_entry(WORKLOAD.replace("_fp32", "_fp64_ops"))
+        if ops is not None:
+            rate = fp64["nodes"] / (fp64["kernel_ms"] * 1e-3)
+            pipe = ops["fp64_thread_inst_per_node"]["fp64_pipe"] * rate
+            flops = ops["flops_per_node"] * rate / 1e12
+            fp64_line["roofline"] = {
+                "bound": "alu", "unit": "G FP64-pipe thread-instr/s",
+                "achieved": round(pipe / 1e9, 1), "peak": round(FP64_PIPE_INSTR_PER_S / 1e9, 1),
+                "frac": round(pipe / FP64_PIPE_INSTR_PER_S, 4),
+                "peak_kind": "derived from nominal FP64 rate, SM count and clock",
+                "fp64_pipe_instr_per_node": ops["fp64_thread_inst_per_node"]["fp64_pipe"],
+                "achieved_tflops": round(flops, 3), "nominal_tflops": FP64_NOMINAL_TFLOPS}
 
     batched = None if args.skip_batched else measure_batched(args, torch, lb, barrier_max, ws)
     adjoint = None if args.skip_adjoint else measure_adjoint(args, torch, lb)
@@ -282,7 +333,9 @@ def run_ours(args, ws, rank, local):
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "bytes_per_node": bytes_per_node,
                          "kernel_ms": round(main["kernel_ms"], 5),
-                         "traffic": traffic},
+                         "traffic": traffic,
+                         "copy_ceiling_gbs": round(copy_gbs, 1),
+                         "frac_of_copy_ceiling": round(achieved / copy_gbs, 4)},
             "e2e": {"value": None if e2e_value is None else round(e2e_value, 1), "unit": "MLUPS", "steps": e2e_steps,
                     "h2d_bytes_per_step": 2 * 3 * 8 * nb, "d2h_bytes_per_step": 2 * 3 * 8 * nb},
             "gpu_launches": 3 * K + 2,
