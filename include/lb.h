@@ -275,6 +275,58 @@ lb_status lb_moments_noalloc(const void *d_populations, int precision, int nx, i
                              int odd_parity, double rho0, double pore_radius, int pore_axis,
                              double *d_out, void *cuda_stream, char *err, size_t err_len);
 
+/* ---------------------------------------------------------------------
+ * Trajectories and their mean squared displacements (Sec. 2.4-2.7: the
+ * transport of a raspberry is measured from its centre and orientation
+ * recorded at a fixed interval).
+ *
+ * lb_record_bodies: from the next step on, every `every` steps (the step
+ * count after a step is a multiple of `every`) the step prologue writes the
+ * centre X (unwrapped, lattice units) and orientation q (w, x, y, z) of
+ * every body into a device ring of `capacity` records, without host
+ * synchronisation. every = 0 turns recording off and frees the ring;
+ * calling it again restarts the ring. LB_ERR_ARG for every < 0,
+ * capacity < 1 when every > 0, or no bodies; LB_ERR_OOM if the ring
+ * ([capacity][nbodies][7] doubles) does not fit. */
+lb_status lb_record_bodies(lb_handle h, int every, int capacity);
+/* The records of one body still in the ring, oldest first (at most
+ * max_records, the most recent ones): steps[k] (step count of record k),
+ * X[3k..3k+2], q[4k..4k+3]; any of the three may be NULL. *count receives
+ * the number written. */
+lb_status lb_get_trajectory(lb_handle h, int body_id, int max_records, long long *steps, double *X, double *q,
+                            int *count);
+/* The same for the batched handle (all instances share the step count). */
+lb_status lb_batch_record_bodies(lb_batch_handle h, int every, int capacity);
+lb_status lb_batch_get_trajectory(lb_batch_handle h, int inst, int body_id, int max_records, long long *steps,
+                                  double *X, double *q, int *count);
+
+/* Mean squared displacements of nbodies trajectories on the GPU.
+ * X: host [nbodies][nrec][3] centres (unwrapped), q: host [nbodies][nrec][4]
+ * unit quaternions (w, x, y, z; lab = R(q) body), records equally spaced.
+ * For every body b and lag l = 1..max_lag records, averaged over the
+ * nrec - l time origins, out[(b*max_lag + l-1)*LB_MSD_COLS + c] holds
+ *   c = 0-2  squared lab-frame displacement per lab axis, Eq. (dt_lab);
+ *   c = 3-5  squared displacement of the body-frame trajectory per body axis:
+ *            increments R(q_{n-1})^T (X_n - X_{n-1}) summed over the records,
+ *            Eqs. (labdisp), (quat), (bodyframedisplacement),
+ *            (bodyframetrajectory), (dt_body);
+ *   c = 6    squared angle between p(t) and p(t+l), p = R(q) p_ref (p_ref a
+ *            body-frame reference vector), Eq. (delta_theta);
+ *   c = 7-9  squared change of the summed body-frame angular displacements
+ *            about body axis x, y, z (projection method of the SI section
+ *            "Body-frame angular displacement"; Eqs.
+ *            (bodyframerotdisplacement), (bodyframerottrajectory)).
+ * Divide by the paper's denominators for diffusivities (Eq. (dt_lab): sum of
+ * c = 0-2 over 6 tau; Eq. (dt_body): 2 tau per axis; Eq. (dr_lab): 6 tau;
+ * Eq. (dr_body): 3 tau). The stream may be NULL. Errors: LB_ERR_ARG
+ * (null pointers, nrec < 2, max_lag outside [1, nrec), nbodies outside
+ * [1, 65535], p_ref zero), LB_ERR_OOM, LB_ERR_CUDA; the message goes to
+ * err (err_len bytes, may be NULL). Allocates and frees its own device
+ * memory (inputs, a work array of 9 doubles per record, the output). */
+#define LB_MSD_COLS 10
+lb_status lb_msd_trajectory(const double *X, const double *q, int nrec, int nbodies, int max_lag,
+                            const double p_ref[3], double *out, void *cuda_stream, char *err, size_t err_len);
+
 /* Host-only: the velocity set c[19*3], weights w[19] and opposite-link table
  * opp[19] the library uses. Needs no GPU. Returns 19. */
 int lb_lattice(int *c, double *w, int *opp);

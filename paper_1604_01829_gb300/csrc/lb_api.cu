@@ -360,7 +360,7 @@ lb_status lb_destroy(lb_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
-                    h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4};
+                    h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -479,9 +479,10 @@ lb_status lb_step(lb_handle h, int nsteps) {
         if (nb > 0) {
             // previous step's second half kick (k > 0), this step's kick and
             // drift, and the clearing of this step's spread-force tiles
+            const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
             cudaError_t e = lbk::launch_step_pre(h->db, nb, k > 0, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
                                                  coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
-                                                 h->list_cap, h->g, h->ntx, h->nty, h->stream);
+                                                 h->list_cap, h->g, h->ntx, h->nty, rec, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
             // the list of this buffer restarts empty for this step's coupling
             if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
@@ -701,6 +702,38 @@ lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_p
     h->cs_variant = variant;
     h->tma_stages = stages;
     h->tma_ctas = ctas_per_sm;
+    return LB_OK;
+}
+
+lb_status lb_record_bodies(lb_handle h, int every, int capacity) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (every < 0 || (every > 0 && capacity < 1)) return fail(h, LB_ERR_ARG, "every >= 0 and capacity >= 1");
+    if (every > 0 && h->hb.empty()) return fail(h, LB_ERR_ARG, "no bodies to record");
+    if (h->rec) {
+        LB_CUDA(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->rec);
+        h->dev_bytes -= sizeof(double) * 7 * (size_t)h->rec_cap * h->hb.size();
+        h->rec = nullptr;
+    }
+    h->rec_every = h->rec_cap = 0;
+    if (every == 0) return LB_OK;
+    lb_status s = upload_bodies(h);        // the body set is fixed from here on
+    if (s != LB_OK) return s;
+    if ((s = dev_alloc(h, &h->rec, sizeof(double) * 7 * (size_t)capacity * h->hb.size())) != LB_OK) return s;
+    h->rec_every = every;
+    h->rec_cap = capacity;
+    h->rec_k0 = h->step / every + 1;
+    return LB_OK;
+}
+
+lb_status lb_get_trajectory(lb_handle h, int body, int max_records, long long *steps, double *X, double *q,
+                            int *count) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!count || max_records < 0) return fail(h, LB_ERR_ARG, "count must not be NULL, max_records >= 0");
+    if (body < 0 || body >= (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body id");
+    cudaError_t e = lbk::copy_records(h->rec, h->rec_every, h->rec_cap, h->rec_k0, h->step, (int)h->hb.size(), body,
+                                      max_records, steps, X, q, count, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_get_trajectory");
     return LB_OK;
 }
 

@@ -241,13 +241,15 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
 // and the clearing of every flagged tile of this step's force pool
 template <typename T>
 __global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
-                            const int *tcount, const BInst *inst, const long long *flag_start, int n) {
+                            const int *tcount, const BInst *inst, const long long *flag_start, int n,
+                            Recorder rec) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (threadIdx.x == 0 && blockIdx.x < nb) {     // one body per block
         Body B = bodies[blockIdx.x];
         if (finish_prev) kick2(B);
         kick_drift(B);
         bodies[blockIdx.x] = B;
+        record_body(rec, B, blockIdx.x, nb);
     }
     if (!tiles) return;
     // one thread per (listed tile, node of the tile)
@@ -361,6 +363,10 @@ struct lb_batch_ctx {
     int resident = 0;                       // resident CTAs per SM of the fluid kernel at TS threads
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
+    // trajectory recorder ([rec_cap][nbodies][7], records k >= rec_k0)
+    double *rec = nullptr;
+    int rec_every = 0, rec_cap = 0;
+    long long rec_k0 = 0;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -552,16 +558,19 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
     const bool coupled = nb > 0 && nbeads > 0;
     if (nb > 0) {
+        const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
         const long long nthreads = std::min<long long>(64LL * h->list_cap, 152LL * 2048);
         const unsigned pg = std::max<unsigned>((unsigned)((nthreads + 255) / 256), (unsigned)nb);
         if (h->fp32)
             lbk::k_batch_pre<float><<<pg, 256, 0, h->stream>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (float *)h->Fbuf[cur] : nullptr,
-                coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n);
+                coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
+                rec);
         else
             lbk::k_batch_pre<double><<<pg, 256, 0, h->stream>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (double *)h->Fbuf[cur] : nullptr,
-                coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n);
+                coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
+                rec);
         BCUDA(h, cudaGetLastError());
         if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
     }
@@ -814,7 +823,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead};
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead, h->rec};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -902,6 +911,43 @@ lb_status lb_batch_step(lb_batch_handle h, int nsteps) {
         h->step += 2LL * pairs;
     }
     if (nsteps & 1) return eager_steps(h, 1);
+    return LB_OK;
+}
+
+lb_status lb_batch_record_bodies(lb_batch_handle h, int every, int capacity) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (every < 0 || (every > 0 && capacity < 1)) return bfail(h, LB_ERR_ARG, "every >= 0 and capacity >= 1");
+    if (every > 0 && h->hb.empty()) return bfail(h, LB_ERR_ARG, "no bodies to record");
+    if (h->rec) {
+        BCUDA(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->rec);
+        h->dev_bytes -= sizeof(double) * 7 * (size_t)h->rec_cap * h->hb.size();
+        h->rec = nullptr;
+    }
+    h->rec_every = h->rec_cap = 0;
+    if (h->gexec) {                        // the captured steps hold the old recorder
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    if (every == 0) return LB_OK;
+    lb_status s = upload(h);               // the body set is fixed from here on
+    if (s != LB_OK) return s;
+    if ((s = balloc(h, &h->rec, sizeof(double) * 7 * (size_t)capacity * h->hb.size())) != LB_OK) return s;
+    h->rec_every = every;
+    h->rec_cap = capacity;
+    h->rec_k0 = h->step / every + 1;
+    return LB_OK;
+}
+
+lb_status lb_batch_get_trajectory(lb_batch_handle h, int k, int body, int max_records, long long *steps, double *X,
+                                  double *q, int *count) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    if (!count || max_records < 0) return bfail(h, LB_ERR_ARG, "count must not be NULL, max_records >= 0");
+    if (body < 0 || body >= (int)h->inst_bodies[k].size()) return bfail(h, LB_ERR_ARG, "bad body id");
+    cudaError_t e = lbk::copy_records(h->rec, h->rec_every, h->rec_cap, h->rec_k0, h->step, (int)h->hb.size(),
+                                      h->inst_bodies[k][body], max_records, steps, X, q, count, h->stream);
+    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("lb_batch_get_trajectory: ") + cudaGetErrorString(e));
     return LB_OK;
 }
 
@@ -1052,6 +1098,11 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     const long long step_host = h->step;
     const bool timing = h->timing;
     h->timing = false;
+    // trial steps record nothing (the ring keeps the simulation's records;
+    // each schedule change drops the captured graph, so no trial graph
+    // outlives this)
+    double *rec_saved = h->rec;
+    h->rec = nullptr;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1083,7 +1134,14 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     cudaEventDestroy(e1);
     release();
     h->timing = timing;
-    if (s != LB_OK) return s;
+    h->rec = rec_saved;
+    if (s != LB_OK) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        return s;
+    }
     s = lb_batch_set_schedule(h, bt, bb, bo);
     if (chosen) { chosen[0] = bt; chosen[1] = bb; chosen[2] = bo; }
     if (best_ms_per_step) *best_ms_per_step = best;

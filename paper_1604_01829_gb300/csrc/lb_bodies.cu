@@ -19,7 +19,7 @@ namespace {
 // flagged 4x4x4 tiles of this step's spread-force buffer.
 template <typename T>
 __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
-                           const int *tcount, Geom g, int ntx, int nty) {
+                           const int *tcount, Geom g, int ntx, int nty, Recorder rec) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     // one body per block, so the FP64 work of the bodies spreads over SMs;
     // a private copy means one read and one write of the record
@@ -28,6 +28,7 @@ __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *til
         if (finish_prev) kick2(B);
         kick_drift(B);
         bodies[blockIdx.x] = B;
+        record_body(rec, B, blockIdx.x, nb);
     }
     if (!tiles) return;
     // one thread per (listed tile, node of the tile): zero the force, drop the flag
@@ -66,14 +67,15 @@ __global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
 }  // namespace
 
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
-                            const int *tcount, int list_cap, const Geom &g, int ntx, int nty, cudaStream_t s) {
+                            const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
+                            cudaStream_t s) {
     // enough threads for the bodies and for a full list (grid-stride beyond)
     long long n = 64LL * list_cap;
     if (n > 152LL * 2048) n = 152LL * 2048;
     unsigned grid = (unsigned)((n + 255) / 256);
     if (grid < (unsigned)nbodies) grid = (unsigned)nbodies;
-    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty);
-    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty);
+    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec);
+    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,11 @@ struct lb_ctx {
     double *partials = nullptr;
     double *out4 = nullptr;
     int red_blocks = 0;
+    // trajectory recorder: ring [rec_cap][nbodies][7] (X, q), one record
+    // every rec_every steps; records k >= rec_k0 (k = step / rec_every)
+    double *rec = nullptr;
+    int rec_every = 0, rec_cap = 0;
+    long long rec_k0 = 0;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;   // pairs

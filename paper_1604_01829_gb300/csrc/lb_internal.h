@@ -102,8 +102,29 @@ cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, do
                            int nblocks, double *out4, cudaStream_t s);
 cudaError_t launch_advance(unsigned long long *step, unsigned int by, cudaStream_t s);
 
+// Trajectory recorder: after the drift of step t, if (t + 1) % every == 0,
+// the step prologue writes every body's centre and orientation (7 doubles,
+// X then q) into record slot ((t + 1) / every - 1) % cap of `ring`
+// ([cap][nbodies][7]). ring == nullptr: off.
+struct Recorder {
+    double *ring;
+    int every, cap;
+    const unsigned long long *step_base;
+    uint32_t step_off;
+};
+
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
-                            const int *tcount, int list_cap, const Geom &g, int ntx, int nty, cudaStream_t s);
+                            const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
+                            cudaStream_t s);
+
+// The valid records of body `id` in a recorder ring, oldest first (host
+// arrays; lb_traj.cu).
+cudaError_t copy_records(const double *ring, int every, int cap, long long k0, long long step, int nb, int id,
+                         int max_records, long long *steps, double *X, double *q, int *count, cudaStream_t s);
+
+// MSD analysis of recorded trajectories (lb_traj.cu); all pointers device
+cudaError_t launch_msd(const double *X, const double *q, int nrec, int nbodies, int max_lag, const double *p_ref,
+                       double *work, double *out, cudaStream_t s);
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
 cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s);
 

@@ -99,4 +99,20 @@ __device__ __forceinline__ void kick_drift(Body &B) {
     for (int a = 0; a < 6; ++a) B.acc[a] = 0.0;
 }
 
+// Trajectory record of body b after the drift of step *step_base + step_off.
+__device__ __forceinline__ void record_body(const Recorder &r, const Body &B, int b, int nb) {
+    if (!r.ring) return;
+    const unsigned long long t1 = *r.step_base + r.step_off + 1ull;
+    if (t1 % (unsigned long long)r.every) return;
+    const unsigned long long slot = (t1 / (unsigned long long)r.every - 1ull) % (unsigned long long)r.cap;
+    double *o = r.ring + (slot * (unsigned long long)nb + (unsigned long long)b) * 7ull;
+    o[0] = B.X[0];
+    o[1] = B.X[1];
+    o[2] = B.X[2];
+    o[3] = B.q[0];
+    o[4] = B.q[1];
+    o[5] = B.q[2];
+    o[6] = B.q[3];
+}
+
 }  // namespace lbk

@@ -67,6 +67,8 @@ _SIGS = {
     "lb_set_kernel_variant": [C.c_void_p, C.c_int, C.c_int, C.c_int],
     "lb_adjoint_drag": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
+    "lb_record_bodies": [C.c_void_p, C.c_int, C.c_int],
+    "lb_get_trajectory": [C.c_void_p, C.c_int, C.c_int, _llp, _dp, _dp, _ip],
 }
 
 _BSIGS = {
@@ -84,11 +86,14 @@ _BSIGS = {
     "lb_batch_info": [C.c_void_p, _llp, _llp, _ip],
     "lb_batch_set_timing": [C.c_void_p, C.c_int],
     "lb_batch_kernel_time": [C.c_void_p, _dp, _llp],
+    "lb_batch_record_bodies": [C.c_void_p, C.c_int, C.c_int],
+    "lb_batch_get_trajectory": [C.c_void_p, C.c_int, C.c_int, C.c_int, _llp, _dp, _dp, _ip],
 }
 
 # every symbol include/lb.h declares
 EXPORTS = sorted(list(_SIGS) + list(_BSIGS) + ["lb_last_error", "lb_status_string", "lb_lattice",
-                                                "lb_moments_noalloc", "lb_batch_last_error"])
+                                                "lb_moments_noalloc", "lb_batch_last_error",
+                                                "lb_msd_trajectory"])
 
 
 def load():
@@ -117,6 +122,9 @@ def load():
                                              C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                              C.c_char_p, C.c_size_t]
             L.lb_moments_noalloc.restype = C.c_int
+            L.lb_msd_trajectory.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_void_p,
+                                            C.c_char_p, C.c_size_t]
+            L.lb_msd_trajectory.restype = C.c_int
             _lib = L
     return _lib
 
@@ -166,6 +174,31 @@ def lb_moments_noalloc(d_populations, precision, nx, ny, nz, odd_parity, rho0, d
                                    C.c_void_p(d_out), C.c_void_p(stream) if stream else None, err, 256)
     if st != LB_OK:
         raise LBError(st, err.value.decode())
+
+
+MSD_COLS = 10
+MSD_COLUMNS = ("lab_x", "lab_y", "lab_z", "body_x", "body_y", "body_z", "rot_lab",
+               "rot_body_x", "rot_body_y", "rot_body_z")
+
+
+def lb_msd_trajectory(X, q, max_lag, p_ref=(1.0, 0.0, 0.0), stream=None):
+    """Mean squared displacements of recorded trajectories on the GPU (see
+    include/lb.h). X: [nbodies, nrec, 3], q: [nbodies, nrec, 4] (or one body
+    without the leading axis). Returns [nbodies, max_lag, MSD_COLS]."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if X.ndim == 2:
+        X, q = X[None], q[None]
+    nb, nrec = X.shape[0], X.shape[1]
+    if X.shape != (nb, nrec, 3) or q.shape != (nb, nrec, 4):
+        raise ValueError("X must be [nbodies, nrec, 3] and q [nbodies, nrec, 4]")
+    out = np.zeros((nb, int(max_lag), MSD_COLS))
+    err = C.create_string_buffer(256)
+    st = load().lb_msd_trajectory(_d(X), _d(q), nrec, nb, int(max_lag), _d(_vec(p_ref, 3)), _d(out),
+                                  C.c_void_p(stream) if stream else None, err, 256)
+    if st != LB_OK:
+        raise LBError(st, err.value.decode())
+    return out
 
 
 def make_params(nx, ny, nz, precision=64, collision=0, tau=1.0, gamma_shear=0.0, gamma_bulk=0.0,
@@ -306,6 +339,20 @@ class LB:
         _check(self.h, load().lb_kernel_time(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
+    def lb_record_bodies(self, every, capacity=4096):
+        _check(self.h, load().lb_record_bodies(self.h, int(every), int(capacity)))
+        self._rec_cap = int(capacity)
+
+    def lb_get_trajectory(self, body=0, max_records=None):
+        """(steps, X [n, 3], q [n, 4]) of the records still in the ring."""
+        m = int(max_records if max_records is not None else getattr(self, "_rec_cap", 0))
+        steps, X, q = np.zeros(m, np.int64), np.zeros((m, 3)), np.zeros((m, 4))
+        n = C.c_int()
+        _check(self.h, load().lb_get_trajectory(self.h, int(body), m, steps.ctypes.data_as(_llp), _d(X), _d(q),
+                                                C.byref(n)))
+        k = n.value
+        return steps[:k], X[:k], q[:k]
+
 
 def from_workload(w, stream=None, precision=None):
     """Create an LB handle holding a workloads.Workload (pore and bodies)."""
@@ -407,6 +454,19 @@ class LBBatch:
         ms, n = C.c_double(), C.c_longlong()
         _bcheck(self.h, load().lb_batch_kernel_time(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def lb_batch_record_bodies(self, every, capacity=4096):
+        _bcheck(self.h, load().lb_batch_record_bodies(self.h, int(every), int(capacity)))
+        self._rec_cap = int(capacity)
+
+    def lb_batch_get_trajectory(self, inst, body=0, max_records=None):
+        m = int(max_records if max_records is not None else getattr(self, "_rec_cap", 0))
+        steps, X, q = np.zeros(m, np.int64), np.zeros((m, 3)), np.zeros((m, 4))
+        n = C.c_int()
+        _bcheck(self.h, load().lb_batch_get_trajectory(self.h, int(inst), int(body), m,
+                                                       steps.ctypes.data_as(_llp), _d(X), _d(q), C.byref(n)))
+        k = n.value
+        return steps[:k], X[:k], q[:k]
 
 
 def batch_from_workloads(workloads, stream=None, precision=None):
