@@ -359,7 +359,11 @@ def measure_batched(args, torch, lb, barrier_max, ws):
     ws_list = W.batched_instances(args.batch_instances)
     stream = torch.cuda.Stream()
     B = lb.batch_from_workloads(ws_list, stream=stream.cuda_stream)
-    chosen, _ = B.lb_batch_autotune(10)
+    if args.batch_schedule:
+        chosen = [int(v) for v in args.batch_schedule.split(",")]
+        B.lb_batch_set_schedule(*chosen)
+    else:
+        chosen, _ = B.lb_batch_autotune(10)
     nodes = B.lb_batch_info()["total_nodes"]
     K = args.batch_steps
     B.lb_batch_step(4)
@@ -376,6 +380,21 @@ def measure_batched(args, torch, lb, barrier_max, ws):
     B.lb_batch_step(20)
     kms, kn = B.lb_batch_kernel_time()
     B.lb_batch_set_timing(False)
+    # the same steps with the trajectory recorder on (every 10 steps, all
+    # bodies), then the GPU MSD analysis of trajectories of the analysis scale
+    B.lb_batch_record_bodies(10, 1024)
+    B.lb_batch_step(4)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.lb_batch_step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_rec = barrier_max(e0.elapsed_time(e1))
+    nrec = len(B.lb_batch_get_trajectory(0, 0)[0])
+    traj = measure_msd(torch, lb)
+    traj.update({"record_every": 10, "records_per_body": nrec,
+                 "ms_per_step_recording": round(ms_rec / K, 4),
+                 "recording_overhead_pct": round(100.0 * (ms_rec - ms) / ms, 2)})
     fluid = 0
     for w in ws_list:
         if w.pore is None:
@@ -417,7 +436,32 @@ def measure_batched(args, torch, lb, barrier_max, ws):
             "speedup_vs_one_by_one": round((ms1 / K1) / (ms / K), 2),
             "schedule": {"tile_nodes": chosen[0], "blocks_per_sm": chosen[1], "order": chosen[2]},
             "fluid_kernel": {"ms": round(kms / max(kn, 1), 4), "achieved_gbs": round(ach, 1),
-                             "frac": round(ach / peak, 4), "peak_kind": kind}}
+                             "frac": round(ach / peak, 4), "peak_kind": kind},
+            "trajectory": traj}
+
+
+def measure_msd(torch, lb, nbodies=256, nrec=4000, max_lag=400, seed=1610):
+    """GPU MSD analysis (lab- and body-frame translation and rotation) of
+    seeded random-walk trajectories: 256 bodies x 4000 records x 400 lags,
+    host arrays in and out (copies included)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    X = np.cumsum(rng.normal(scale=0.2, size=(nbodies, nrec, 3)), axis=1)
+    d = np.concatenate([np.ones((nbodies, nrec, 1)), rng.normal(scale=0.05, size=(nbodies, nrec, 3))], axis=2)
+    d /= np.linalg.norm(d, axis=2, keepdims=True)
+    q = np.empty_like(d)                    # random walk of orientations: q_k = q_{k-1} (x) d_k
+    q[:, 0] = d[:, 0]
+    for k in range(1, nrec):
+        a, b = q[:, k - 1], d[:, k]
+        q[:, k, 0] = a[:, 0] * b[:, 0] - (a[:, 1:] * b[:, 1:]).sum(1)
+        q[:, k, 1:] = a[:, :1] * b[:, 1:] + b[:, :1] * a[:, 1:] + np.cross(a[:, 1:], b[:, 1:])
+    lb.lb_msd_trajectory(X[:2, :100], q[:2, :100], 10)          # warm-up
+    t0 = time.perf_counter()
+    lb.lb_msd_trajectory(X, q, max_lag)
+    sec = time.perf_counter() - t0
+    pairs = nbodies * sum(nrec - l for l in range(1, max_lag + 1))
+    return {"msd_bodies": nbodies, "msd_records": nrec, "msd_lags": max_lag, "msd_ms": round(sec * 1e3, 2),
+            "msd_pairs_per_s": round(pairs / sec, 1)}
 
 
 def measure_adjoint(args, torch, lb):
@@ -545,6 +589,8 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--batch-schedule", default=None,
+                    help="tile_nodes,blocks_per_sm,order for the batched leg instead of the autotuner")
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     args = ap.parse_args()

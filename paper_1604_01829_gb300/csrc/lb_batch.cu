@@ -37,6 +37,7 @@ struct BInst {
     long long off;               // element offset of plane 0 in the population pool
     long long foff;              // offset of this instance's [3][N] block in a force pool
     long long toff;              // offset of its tile flags
+    long long moff;              // pore instances: offset of the cross-section wall masks, else -1
     int ntx, nty, ntz;
     uint32_t key0, key1, instance;
     double rho0, gamma, noise_amp;
@@ -56,6 +57,7 @@ struct BatchArgs {
     void *pool;
     const void *F;               // spread force of this step (pool, storage precision), nullptr without bodies
     const int *tiles;
+    const uint32_t *masks;       // per pore cross-section position: bit 31 wall node, bit i upstream of link i is wall
     const unsigned long long *step_base;
     uint32_t step_off;
 };
@@ -76,9 +78,8 @@ __constant__ signed char kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1
                                        {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
                                        {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
-// 18-bit mask of the links whose upstream node is a wall node (rolled loop:
-// only nodes next to a pore wall come here)
-__device__ __noinline__ uint32_t upstream_wall_mask(const Geom &g, int x, int y, int z) {
+// 18-bit mask of the links whose upstream node is a wall node
+__device__ uint32_t upstream_wall_mask(const Geom &g, int x, int y, int z) {
     uint32_t m = 0;
 #pragma unroll 1
     for (int i = 1; i < 19; ++i) {
@@ -86,6 +87,17 @@ __device__ __noinline__ uint32_t upstream_wall_mask(const Geom &g, int x, int y,
         if (pore_r2(g, xs, ys, zs) >= g.pore_t) m |= 1u << i;
     }
     return m;
+}
+
+// wall masks of one pore instance, one thread per position across the axis
+__global__ void k_build_masks(Geom g, uint32_t *out, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int x = 0, y = 0, z = 0;
+    if (g.pore_axis == 2) { x = t % g.nx; y = t / g.nx; }
+    else if (g.pore_axis == 1) { x = t % g.nx; z = t / g.nx; }
+    else { y = t % g.ny; z = t / g.ny; }
+    out[t] = pore_r2(g, x, y, z) >= g.pore_t ? (1u << 31) : upstream_wall_mask(g, x, y, z);
 }
 
 template <typename T, int COLL, bool NOISE, bool ODD, bool COMMON>
@@ -115,12 +127,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
             z = r / (uint32_t)g.ny;
         }
         const int x = (int)(n - r * (uint32_t)g.nx), y = (int)(r - z * (uint32_t)g.ny);
-        // bit i set: the upstream neighbour x - c_i is a wall node
+        // bit i set: the upstream neighbour x - c_i is a wall node; the
+        // masks depend only on the position across the pore axis and are
+        // tabulated once per instance (bit 31: the node itself is a wall)
         uint32_t wall_up = 0;
         if (g.pore_axis >= 0) {
-            const long long r2 = pore_r2(g, x, y, (int)z);
-            if (r2 >= g.pore_t) continue;
-            if (ODD && r2 >= g.pore_in) wall_up = upstream_wall_mask(g, x, y, (int)z);
+            const uint32_t cs = g.pore_axis == 2 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)y
+                              : (g.pore_axis == 1 ? (uint32_t)x + (uint32_t)g.nx * z
+                                                  : (uint32_t)y + (uint32_t)g.ny * z);
+            const uint32_t m = __ldg(a.masks + I.moff + cs);
+            if (m >> 31) continue;
+            if (ODD) wall_up = m;
         }
         // 32-bit element indices into the pool (the pool holds < 2^32 elements)
         T *P = static_cast<T *>(a.pool);
@@ -167,12 +184,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
 #pragma unroll
             for (int i = 0; i < 19; ++i) at2(opp(i), n) = f[i];
         } else {
+            // the wall mask again from the table (L1) rather than held in a
+            // register across the collision
+            uint32_t wall_dn = 0;
+            const int axis2 = *(const volatile int *)&a.inst[k].g.pore_axis;
+            if (axis2 >= 0) {
+                const long long moff2 = *(const volatile long long *)&a.inst[k].moff;
+                uint32_t cs;
+                if (axis2 == 2) cs = (uint32_t)(xo[1] + yo[1]);
+                else if (axis2 == 1) cs = (uint32_t)(xo[1] + zo[1] / *(const volatile int *)&a.inst[k].g.ny);
+                else cs = (uint32_t)((yo[1] + zo[1]) / *(const volatile int *)&a.inst[k].g.nx);
+                wall_dn = __ldg(a.masks + moff2 + cs);
+            }
             at2(0, n) = f[0];
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
                 const uint32_t dst = (uint32_t)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
                 // downstream node x + c_i is upstream node x - c_opp(i)
-                if ((wall_up >> opp(i)) & 1u) at2(opp(i), n) = f[i];
+                if ((wall_dn >> opp(i)) & 1u) at2(opp(i), n) = f[i];
                 else at2(i, dst) = f[i];
             }
         }
@@ -363,6 +392,8 @@ struct lb_batch_ctx {
     int resident = 0;                       // resident CTAs per SM of the fluid kernel at TS threads
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
+    // wall masks of the pore instances (BInst::moff)
+    uint32_t *dmask = nullptr;
     // trajectory recorder ([rec_cap][nbodies][7], records k >= rec_k0)
     double *rec = nullptr;
     int rec_every = 0, rec_cap = 0;
@@ -511,6 +542,27 @@ lb_status rebuild_schedule(lb_batch_ctx *h) {
 
 lb_status upload(lb_batch_ctx *h) {
     if (h->uploaded) return LB_OK;
+    // wall masks of the pore instances, one per position across the axis
+    long long mtot = 0;
+    for (int k = 0; k < h->n; ++k) {
+        BInst &I = h->hinst[k];
+        I.moff = -1;
+        if (I.g.pore_axis < 0) continue;
+        I.moff = mtot;
+        mtot += I.g.pore_axis == 2 ? (long long)I.g.nx * I.g.ny
+              : (I.g.pore_axis == 1 ? (long long)I.g.nx * I.g.nz : (long long)I.g.ny * I.g.nz);
+    }
+    if (mtot > 0) {
+        lb_status s = balloc(h, &h->dmask, sizeof(uint32_t) * (size_t)mtot);
+        if (s != LB_OK) return s;
+        for (int k = 0; k < h->n; ++k) {
+            const BInst &I = h->hinst[k];
+            if (I.moff < 0) continue;
+            const int n = I.g.pore_axis == 2 ? I.g.nx * I.g.ny : (I.g.pore_axis == 1 ? I.g.nx * I.g.nz : I.g.ny * I.g.nz);
+            lbk::k_build_masks<<<(n + 255) / 256, 256, 0, h->stream>>>(I.g, h->dmask + I.moff, n);
+            BCUDA(h, cudaGetLastError());
+        }
+    }
     // instance table with final body forces / compensation
     for (int k = 0; k < h->n; ++k) {
         double g[3];
@@ -613,6 +665,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     a.order = h->order == 1 ? 1 : 0;
     a.chunk = (h->ntiles + grid - 1) / grid;
     a.pool = h->pool;
+    a.masks = h->dmask;
     a.F = coupled ? h->Fbuf[cur] : nullptr;
     a.tiles = coupled ? h->tiles[cur] : nullptr;
     a.step_base = h->step_dev;
@@ -823,7 +876,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead, h->rec};
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
