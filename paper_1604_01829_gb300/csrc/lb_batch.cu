@@ -38,6 +38,15 @@ struct BInst {
     long long foff;              // offset of this instance's [3][N] block in a force pool
     long long toff;              // offset of its tile flags
     long long moff;              // pore instances: offset of the cross-section wall masks, else -1
+    // work items of the fluid kernel: all N nodes of a periodic instance; the
+    // fluid nodes only of a pore instance, as (position across the axis j,
+    // coordinate along it a): node = fluid[loff + j] + a * astride, with j
+    // fastest (a fastest for an x-axis pore, so that x stays contiguous)
+    long long loff;              // offset in the fluid-position pool, -1: no compaction
+    uint32_t nwork;              // work items
+    uint32_t ncs, nax, astride;  // fluid positions across the axis, nodes along it, node stride along it
+    uint32_t mw;                 // ceil(2^32 / divisor) for exact quotients when wfast
+    int wfast;
     int ntx, nty, ntz;
     uint32_t key0, key1, instance;
     double rho0, gamma, noise_amp;
@@ -58,6 +67,7 @@ struct BatchArgs {
     const void *F;               // spread force of this step (pool, storage precision), nullptr without bodies
     const int *tiles;
     const uint32_t *masks;       // per pore cross-section position: bit 31 wall node, bit i upstream of link i is wall
+    const uint32_t *fluid;       // fluid positions across the axis of the pore instances (BInst::loff)
     const unsigned long long *step_base;
     uint32_t step_off;
 };
@@ -116,8 +126,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         const BInst &I = a.inst[k];
         const Geom g = I.g;
         const uint32_t N = (uint32_t)g.N;
-        const uint32_t n = (uint32_t)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
-        if (n >= N) continue;
+        const uint32_t w = (uint32_t)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
+        if (w >= I.nwork) continue;
+        uint32_t n = w;
+        if (I.loff >= 0) {                   // compacted pore instance: fluid nodes only
+            const uint32_t d = g.pore_axis == 0 ? I.nax : I.ncs;
+            const uint32_t q = I.wfast ? __umulhi(w, I.mw) : w / d;
+            const uint32_t rm = w - q * d;
+            const uint32_t j = g.pore_axis == 0 ? q : rm, ax = g.pore_axis == 0 ? rm : q;
+            n = __ldg(a.fluid + I.loff + j) + ax * I.astride;
+        }
         uint32_t r, z;
         if (I.fastdiv) {
             r = __umulhi(n, I.mx);
@@ -392,8 +410,9 @@ struct lb_batch_ctx {
     int resident = 0;                       // resident CTAs per SM of the fluid kernel at TS threads
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
-    // wall masks of the pore instances (BInst::moff)
+    // wall masks (BInst::moff) and fluid positions (BInst::loff) of the pore instances
     uint32_t *dmask = nullptr;
+    uint32_t *dfluid = nullptr;
     // trajectory recorder ([rec_cap][nbodies][7], records k >= rec_k0)
     double *rec = nullptr;
     int rec_every = 0, rec_cap = 0;
@@ -497,7 +516,7 @@ lb_status rebuild_schedule(lb_batch_ctx *h) {
     long long acc = 0;
     for (int k = 0; k < h->n; ++k) {
         ts[k] = (int)acc;
-        acc += (h->hinst[k].g.N + h->TS - 1) / h->TS;
+        acc += ((long long)h->hinst[k].nwork + h->TS - 1) / h->TS;
     }
     ts[h->n] = (int)acc;
     if (acc > 2000000000LL) return bfail(h, LB_ERR_ARG, "too many work tiles");
@@ -562,6 +581,41 @@ lb_status upload(lb_batch_ctx *h) {
             lbk::k_build_masks<<<(n + 255) / 256, 256, 0, h->stream>>>(I.g, h->dmask + I.moff, n);
             BCUDA(h, cudaGetLastError());
         }
+    }
+    // fluid positions across the axis of each pore instance: the fluid
+    // kernel's work items are its fluid nodes only
+    std::vector<uint32_t> fl;
+    for (int k = 0; k < h->n; ++k) {
+        BInst &I = h->hinst[k];
+        if (I.g.pore_axis < 0) continue;
+        const int ax = I.g.pore_axis;
+        const int na = ax == 0 ? I.g.ny : I.g.nx, nb = ax == 2 ? I.g.ny : I.g.nz;   // across, first fastest
+        I.loff = (long long)fl.size();
+        for (int b = 0; b < nb; ++b)
+            for (int a = 0; a < na; ++a) {
+                const long long da = 2LL * a + 1 - na, db = 2LL * b + 1 - nb;
+                if (da * da + db * db >= I.g.pore_t) continue;          // wall node (same test as the kernels)
+                const long long node = ax == 2 ? a + (long long)I.g.nx * b
+                                     : (ax == 1 ? a + (long long)I.g.nx * I.g.ny * b
+                                                : (long long)I.g.nx * (a + (long long)I.g.ny * b));
+                fl.push_back((uint32_t)node);
+            }
+        I.ncs = (uint32_t)((long long)fl.size() - I.loff);
+        I.nax = (uint32_t)(ax == 0 ? I.g.nx : (ax == 1 ? I.g.ny : I.g.nz));
+        I.astride = (uint32_t)(ax == 0 ? 1 : (ax == 1 ? I.g.nx : I.g.nx * I.g.ny));
+        I.nwork = I.ncs * I.nax;
+        const uint32_t d = ax == 0 ? I.nax : I.ncs;
+        I.mw = d > 1 ? (uint32_t)((0x100000000ULL + d - 1) / d) : 0u;
+        // exact while w * d < 2^32 for every work item w
+        I.wfast = (d > 1 && (double)I.nwork * d < 4294967296.0) ? 1 : 0;
+    }
+    if (!fl.empty()) {
+        lb_status s = balloc(h, &h->dfluid, sizeof(uint32_t) * fl.size());
+        if (s != LB_OK) return s;
+        BCUDA(h, cudaMemcpyAsync(h->dfluid, fl.data(), sizeof(uint32_t) * fl.size(), cudaMemcpyHostToDevice,
+                                 h->stream));
+        BCUDA(h, cudaStreamSynchronize(h->stream));
+        if ((s = rebuild_schedule(h)) != LB_OK) return s;   // tile counts follow the work items
     }
     // instance table with final body forces / compensation
     for (int k = 0; k < h->n; ++k) {
@@ -666,6 +720,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     a.chunk = (h->ntiles + grid - 1) / grid;
     a.pool = h->pool;
     a.masks = h->dmask;
+    a.fluid = h->dfluid;
     a.F = coupled ? h->Fbuf[cur] : nullptr;
     a.tiles = coupled ? h->tiles[cur] : nullptr;
     a.step_base = h->step_dev;
@@ -793,6 +848,9 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         I.g.nx = p.nx; I.g.ny = p.ny; I.g.nz = p.nz;
         I.g.N = (long long)p.nx * p.ny * p.nz;
         I.g.pore_axis = -1;
+        I.moff = -1;
+        I.loff = -1;
+        I.nwork = (uint32_t)I.g.N;
         I.off = off;
         I.foff = foff;
         I.toff = toff;
@@ -876,7 +934,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask};
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask, h->dfluid};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);

@@ -22,7 +22,7 @@ def _built():
 
 
 def _cases(noise):
-    """(params, pore, bodies) of five uneven instances."""
+    """(params, pore, bodies) of six uneven instances (pores along z, x and y)."""
     kT = dict(kT=1e-4) if noise else {}
     g = Wl.paper_gamma_to_lattice(50.0)
     sph = Wl.sphere_raspberry(2.0)
@@ -38,6 +38,8 @@ def _cases(noise):
         (dict(nx=24, ny=8, nz=12, seed=5, gamma_bead=g, **MRT, **kT), None,
          [dict(beads=sph, X=[5.1, 4.3, 6.2], fixed=True, V=(0, 0, 0)),
           dict(beads=sph, X=[17.3, 4.1, 5.8], mass=34.0, inertia=(50, 50, 50), F_ext=(0, 1e-3, 0))]),
+        (dict(nx=15, ny=11, nz=13, seed=6, gamma_bead=g, **MRT, **kT), (5.6, 1),
+         [dict(beads=sph, X=[7.6, 5.2, 6.9], mass=34.0, inertia=(50, 50, 50), F_ext=(0, 1e-3, 0))]),
     ]
 
 
