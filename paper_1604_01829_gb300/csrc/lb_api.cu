@@ -86,11 +86,14 @@ lb_status upload_bodies(lb_ctx *h) {
         lb_status s;
         if ((s = dev_alloc(h, &h->db, sizeof(Body) * nb)) != LB_OK) return s;
         if ((s = dev_alloc(h, &h->ds, sizeof(double) * 3 * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
+        if ((s = dev_alloc(h, &h->dsf, sizeof(float) * 3 * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
         if ((s = dev_alloc(h, &h->dbody_of, sizeof(int) * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
         if ((s = dev_alloc(h, &h->dFbead, sizeof(double) * 3 * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
         LB_CUDA(h, cudaMemcpyAsync(h->db, h->hb.data(), sizeof(Body) * nb, cudaMemcpyHostToDevice, h->stream));
         if (nbeads > 0) {
             LB_CUDA(h, cudaMemcpyAsync(h->ds, h->hs.data(), sizeof(double) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
+            h->hsf.assign(h->hs.begin(), h->hs.end());
+            LB_CUDA(h, cudaMemcpyAsync(h->dsf, h->hsf.data(), sizeof(float) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
             LB_CUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
         }
         LB_CUDA(h, cudaMemsetAsync(h->dFbead, 0, sizeof(double) * 3 * (size_t)std::max(nbeads, 1), h->stream));
@@ -360,7 +363,7 @@ lb_status lb_destroy(lb_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
-                    h->db, h->ds, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec};
+                    h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -506,6 +509,9 @@ lb_status lb_step(lb_handle h, int nsteps) {
             c.ntx = h->ntx;
             c.nty = h->nty;
             c.s = h->ds;
+            c.sf = h->dsf;
+            c.gamma_f = (float)c.gamma;
+            c.noise_amp_f = (float)c.noise_amp;
             c.bead_body = h->dbody_of;
             c.bodies = h->db;
             c.F_bead = h->dFbead;

@@ -50,6 +50,7 @@ struct BInst {
     int ntx, nty, ntz;
     uint32_t key0, key1, instance;
     double rho0, gamma, noise_amp;
+    float gamma_f, noise_amp_f;
     double gd[3];                // uniform force density
     float gf[3];
     CollParams<double> pd;
@@ -73,15 +74,6 @@ struct BatchArgs {
 };
 
 namespace {
-
-__device__ __forceinline__ int find_instance(const int *start, int n, int t) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(start + mid) <= t) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 __constant__ signed char kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
                                        {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
@@ -236,6 +228,7 @@ struct BatchCouple {
     int *tlist;
     int *tcount;
     const double *s;
+    const float *sf;
     const int *bead_body;
     const int *bead_rng;          // bead index within its own lattice
     Body *bodies;
@@ -272,6 +265,9 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.ntx = I.ntx;
     a.nty = I.nty;
     a.s = b.s;
+    a.sf = b.sf;
+    a.gamma_f = I.gamma_f;
+    a.noise_amp_f = I.noise_amp_f;
     a.bead_body = b.bead_body;
     a.bodies = b.bodies;
     a.F_bead = b.F_bead;
@@ -402,6 +398,8 @@ struct lb_batch_ctx {
     std::vector<int> inst_beads;                   // beads per instance so far
     Body *db = nullptr;
     double *ds = nullptr;
+    float *dsf = nullptr;
+    std::vector<float> hsf;
     int *dbody_of = nullptr, *dbead_rng = nullptr;
     double *dFbead = nullptr;
     bool uploaded = false;
@@ -632,12 +630,15 @@ lb_status upload(lb_batch_ctx *h) {
     if (nb > 0) {
         if ((s = balloc(h, &h->db, sizeof(Body) * nb)) != LB_OK) return s;
         if ((s = balloc(h, &h->ds, sizeof(double) * 3 * (size_t)nbeads)) != LB_OK) return s;
+        if ((s = balloc(h, &h->dsf, sizeof(float) * 3 * (size_t)nbeads)) != LB_OK) return s;
         if ((s = balloc(h, &h->dbody_of, sizeof(int) * (size_t)nbeads)) != LB_OK) return s;
         if ((s = balloc(h, &h->dbead_rng, sizeof(int) * (size_t)nbeads)) != LB_OK) return s;
         if ((s = balloc(h, &h->dFbead, sizeof(double) * 3 * (size_t)nbeads)) != LB_OK) return s;
         BCUDA(h, cudaMemcpyAsync(h->db, h->hb.data(), sizeof(Body) * nb, cudaMemcpyHostToDevice, h->stream));
         if (nbeads > 0) {
             BCUDA(h, cudaMemcpyAsync(h->ds, h->hs.data(), sizeof(double) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
+            h->hsf.assign(h->hs.begin(), h->hs.end());
+            BCUDA(h, cudaMemcpyAsync(h->dsf, h->hsf.data(), sizeof(float) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
             BCUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
             BCUDA(h, cudaMemcpyAsync(h->dbead_rng, h->hbead_rng.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
         }
@@ -692,6 +693,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
         c.tlist = h->tlist[cur];
         c.tcount = h->tcount[cur];
         c.s = h->ds;
+        c.sf = h->dsf;
         c.bead_body = h->dbody_of;
         c.bead_rng = h->dbead_rng;
         c.bodies = h->db;
@@ -861,6 +863,8 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         I.rho0 = p.rho0;
         I.gamma = p.gamma_bead;
         I.noise_amp = p.kT > 0.0 ? std::sqrt(2.0 * p.kT * p.gamma_bead) : 0.0;
+        I.gamma_f = (float)I.gamma;
+        I.noise_amp_f = (float)I.noise_amp;
         fill_coll(p, I);
         I.mx = (uint32_t)((0x100000000ULL + p.nx - 1) / p.nx);
         I.my = (uint32_t)((0x100000000ULL + p.ny - 1) / p.ny);
@@ -934,7 +938,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask, h->dfluid};
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask, h->dfluid};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);

@@ -24,15 +24,122 @@ __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int
     j[0] = jx; j[1] = jy; j[2] = jz;
 }
 
+// FP32 storage: the same coupling with every per-bead quantity in FP32
+// (GB300's FP64 pipe is narrow and one bead's FP64 work, done by one lane,
+// would bound the kernel). The virtual site is formed relative to the body:
+// floor and fraction of X - 1/2 come from the body (FP64, once per step),
+// the offset R s in FP32 (|s| of a few units: 1e-6 absolute), so positions
+// keep their resolution for any box size. Body sums are accumulated in FP64.
+__device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int k_rng, int c, int lane,
+                                                bool active) {
+    const Geom &g = a.g;
+    const float *A = static_cast<const float *>(a.f);
+    const int body = active ? a.bead_body[k] : -1;
+    const Body *Bp = active ? &a.bodies[body] : nullptr;
+
+    float rel[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
+    if (active && c == 0) {
+        const float s0 = a.sf[3 * k], s1 = a.sf[3 * k + 1], s2 = a.sf[3 * k + 2];
+        for (int q = 0; q < 3; ++q) rel[q] = Bp->Rf[3 * q] * s0 + Bp->Rf[3 * q + 1] * s1 + Bp->Rf[3 * q + 2] * s2;
+        const float *w = Bp->wlf;
+        v[0] = Bp->Vf[0] + (w[1] * rel[2] - w[2] * rel[1]);
+        v[1] = Bp->Vf[1] + (w[2] * rel[0] - w[0] * rel[2]);
+        v[2] = Bp->Vf[2] + (w[0] * rel[1] - w[1] * rel[0]);
+    }
+    for (int q = 0; q < 3; ++q) rel[q] = __shfl_sync(0xffffffffu, rel[q], 0, 8);
+
+    const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    int xyz[3] = {0, 0, 0};
+    float wt = 1.f;
+    if (active) {
+        for (int q = 0; q < 3; ++q) {
+            const float tq = Bp->Xf[q] + rel[q];          // r - 1/2 - floor(X - 1/2)
+            const float fl = floorf(tq);
+            const float fr = tq - fl;
+            int b0 = (Bp->Xi[q] + (int)fl) % n3[q];
+            if (b0 < 0) b0 += n3[q];
+            xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
+            wt *= o[q] ? fr : 1.f - fr;
+        }
+    }
+    const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
+    const bool fluid = active && !is_wall(g, xyz[0], xyz[1], xyz[2]);
+    float ub[3] = {0.f, 0.f, 0.f};
+    if (fluid) {                         // wall nodes carry u = 0
+        float rho, j[3];
+        node_rho_j<float>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (float)a.rho0, rho, j);
+        const float ir = 1.f / rho;
+        const float *Fp = static_cast<const float *>(a.Fprev);
+        ub[0] = wt * ((j[0] + 0.5f * (a.gforce_f[0] + Fp[n])) * ir);
+        ub[1] = wt * ((j[1] + 0.5f * (a.gforce_f[1] + Fp[g.N + n])) * ir);
+        ub[2] = wt * ((j[2] + 0.5f * (a.gforce_f[2] + Fp[2 * g.N + n])) * ir);
+    }
+    for (int off = 1; off < 8; off <<= 1)
+        for (int q = 0; q < 3; ++q) ub[q] += __shfl_xor_sync(0xffffffffu, ub[q], off, 8);
+
+    // Eq. (latticeboltzmannfriction): F_b = -gamma (v - u(r)) + f_s
+    float Fb[3] = {0.f, 0.f, 0.f};
+    if (active && c == 0) {
+        float fs[3] = {0.f, 0.f, 0.f};
+        if (a.noise_amp_f > 0.f) {
+            const uint32_t step = (uint32_t)(*a.step_base) + a.step_off;
+            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k_rng, step, a.instance, 4u), make_uint2(a.key0, a.key1));
+            fs[0] = a.noise_amp_f * unit_uniform_f(rr.x);
+            fs[1] = a.noise_amp_f * unit_uniform_f(rr.y);
+            fs[2] = a.noise_amp_f * unit_uniform_f(rr.z);
+        }
+        for (int q = 0; q < 3; ++q) Fb[q] = -a.gamma_f * (v[q] - ub[q]) + fs[q];
+        for (int q = 0; q < 3; ++q) a.F_bead[3 * k + q] = (double)Fb[q];
+    }
+    for (int q = 0; q < 3; ++q) Fb[q] = __shfl_sync(0xffffffffu, Fb[q], 0, 8);
+
+    if (fluid) {
+        float *Fc = static_cast<float *>(a.Fcur);
+        atomicAdd(&Fc[n], -wt * Fb[0]);
+        atomicAdd(&Fc[g.N + n], -wt * Fb[1]);
+        atomicAdd(&Fc[2 * g.N + n], -wt * Fb[2]);
+        const int tile = (int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty);
+        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0) a.tlist[atomicAdd(a.tcount, 1)] = a.tile_base + tile;
+    }
+
+    // force and torque: FP32 sums over the (up to 4) beads of the warp's first
+    // body, FP64 accumulation on the body
+    float FT[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (active && c == 0) {
+        FT[0] = Fb[0]; FT[1] = Fb[1]; FT[2] = Fb[2];
+        FT[3] = rel[1] * Fb[2] - rel[2] * Fb[1];
+        FT[4] = rel[2] * Fb[0] - rel[0] * Fb[2];
+        FT[5] = rel[0] * Fb[1] - rel[1] * Fb[0];
+    }
+    const int b_first = __shfl_sync(0xffffffffu, body, 0);
+    const bool lead = active && c == 0;
+    const bool same = lead && body == b_first;
+    float red[6];
+    for (int q = 0; q < 6; ++q) red[q] = same ? FT[q] : 0.f;
+    for (int q = 0; q < 6; ++q) {
+        red[q] += __shfl_xor_sync(0xffffffffu, red[q], 8);
+        red[q] += __shfl_xor_sync(0xffffffffu, red[q], 16);
+    }
+    if (lane == 0 && b_first >= 0)
+        for (int q = 0; q < 6; ++q) atomicAdd(&a.bodies[b_first].acc[q], (double)red[q]);
+    if (lead && !same)
+        for (int q = 0; q < 6; ++q) atomicAdd(&a.bodies[body].acc[q], (double)FT[q]);
+}
+
 // Eight lanes per bead, one per surrounding node: lane 0 of the group forms
 // the virtual site, every lane interpolates its node's velocity and spreads
-// its share of -F_b, the group reduces by shuffles. Node arithmetic runs in
-// the storage precision (FP32 deviations or FP64), bead and body sums in FP64.
+// its share of -F_b, the group reduces by shuffles. FP64 storage: node, bead
+// and body arithmetic in FP64; FP32 storage: couple_bead_f32.
 // k: bead index into a.s / a.bead_body / a.F_bead; k_rng: the bead's index
 // within its own lattice (Philox counter word); c: this lane's corner 0-7.
 // All 32 lanes of the warp must call it (shuffles), active or not.
 template <typename T>
 __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rng, int c, int lane, bool active) {
+    if constexpr (sizeof(T) == 4) {
+        couple_bead_f32(a, k, k_rng, c, lane, active);
+        return;
+    }
     using R = T;
     const Geom &g = a.g;
     const T *A = static_cast<const T *>(a.f);

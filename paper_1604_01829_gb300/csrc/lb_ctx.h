@@ -36,10 +36,12 @@ struct lb_ctx {
     // bodies
     std::vector<Body> hb;
     std::vector<double> hs;
+    std::vector<float> hsf;                  // bead offsets in FP32 (kept for the async upload)
     std::vector<int> hbody_of;
     std::vector<int> bead_start{0};
     Body *db = nullptr;
     double *ds = nullptr;
+    float *dsf = nullptr;
     int *dbody_of = nullptr;
     double *dFbead = nullptr;
     bool uploaded = false;

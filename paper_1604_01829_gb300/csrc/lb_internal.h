@@ -53,6 +53,10 @@ struct Body {
     double wl[3];                    // lab-frame omega of the running step
     double mass, I[3];
     double inv_mass, inv_I[3];       // reciprocals, so the step divides nothing
+    // the running step's state in FP32 for the FP32 coupling: rotation,
+    // velocity, lab omega, and X - 1/2 split into floor (Xi) and fraction (Xf)
+    float Rf[9], Vf[3], wlf[3], Xf[3];
+    int Xi[3];
     int fixed;
     int inst;                        // instance of a batch (0 for a single lattice)
 };
@@ -75,6 +79,8 @@ struct CoupleArgs {
     int tile_base;               // added to tile indices recorded in tlist (batch pools)
     int ntx, nty;
     const double *s;             // body-frame bead offsets [3*nbeads]
+    const float *sf;             // the same in FP32 (FP32 coupling)
+    float gamma_f, noise_amp_f;  // gamma and noise_amp in FP32
     const int *bead_body;        // body index of each bead
     Body *bodies;
     double *F_bead;              // out: bead forces [3*nbeads]

@@ -97,6 +97,14 @@ __device__ __forceinline__ void kick_drift(Body &B) {
     quat_to_R(B.q, B.R);
     for (int a = 0; a < 3; ++a) B.wl[a] = B.R[3 * a] * B.w[0] + B.R[3 * a + 1] * B.w[1] + B.R[3 * a + 2] * B.w[2];
     for (int a = 0; a < 6; ++a) B.acc[a] = 0.0;
+    for (int a = 0; a < 9; ++a) B.Rf[a] = (float)B.R[a];
+    for (int a = 0; a < 3; ++a) {
+        B.Vf[a] = (float)B.V[a];
+        B.wlf[a] = (float)B.wl[a];
+        const double h = B.X[a] - 0.5, fl = floor(h);
+        B.Xi[a] = (int)fl;
+        B.Xf[a] = (float)(h - fl);
+    }
 }
 
 // Trajectory record of body b after the drift of step *step_base + step_off.
