@@ -95,6 +95,22 @@ lb_status lb_destroy(lb_handle h);
  * the first lb_step. Errors: LB_ERR_ARG, LB_ERR_STATE. */
 lb_status lb_set_pore(lb_handle h, double radius, int axis);
 
+/* Repulsive pore wall for the raspberries (Sec. 2.3: beads placed around the
+ * pore surface, a given distance apart, interacting with the colloid beads by
+ * a purely repulsive WCA potential with sigma = r_bead + r_pore_bead).
+ * Reading: the wall beads sit on the cylinder of radius R_pore + r_pore_bead
+ * around the pore axis (so that they touch the hydrodynamic wall), in rings
+ * of round(2 pi (R_pore + r_pore_bead) / spacing) beads at
+ * (k + 1/2) L / round(L / spacing) along the axis (L the box length along
+ * it). Each colloid bead at distance d < 2^(1/6) sigma from a wall bead gets
+ * F = 24 epsilon (2 (sigma/d)^12 - (sigma/d)^6) d_vec / d^2 (minimum image
+ * along the axis); the force and its torque go to the body, not to the
+ * fluid, and are not part of lb_forces' per-bead friction forces. Needs a
+ * pore (else LB_ERR_STATE); spacing = 0 removes the wall beads; LB_ERR_ARG
+ * for spacing < 0, negative radii or a zero sigma, epsilon < 0. Lattice units
+ * (the paper's 5 nm spacing, r_p = 6.25 nm, r_r = 0.5 nm, epsilon = kT). */
+lb_status lb_set_pore_beads(lb_handle h, double spacing, double r_pore_bead, double r_bead, double epsilon);
+
 /* Adds a rigid raspberry (Sec. 1.2): nbeads body-frame bead offsets
  * beads_body_xyz[3*nbeads] relative to the centre of mass X[3], orientation
  * q[4] = (w, x, y, z) (normalised by the library), mass and principal
@@ -216,6 +232,10 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
 lb_status lb_batch_destroy(lb_batch_handle h);
 /* As lb_set_pore / lb_add_raspberry for instance `inst` (before the first
  * step); *body_id is the body's index within its instance. */
+/* Pore-wall beads of one instance, as lb_set_pore_beads (after its pore,
+ * before the first step). */
+lb_status lb_batch_set_pore_beads(lb_batch_handle h, int inst, double spacing, double r_pore_bead,
+                                  double r_bead, double epsilon);
 lb_status lb_batch_set_pore(lb_batch_handle h, int inst, double radius, int axis);
 lb_status lb_batch_add_raspberry(lb_batch_handle h, int inst, const double *beads_body_xyz, int nbeads,
                                  const double X[3], const double q[4], double mass, const double inertia[3],

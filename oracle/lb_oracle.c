@@ -188,6 +188,13 @@ typedef struct {
     uint32_t instance;      /* third Philox counter word */
     double body_force[3];   /* uniform force density on the fluid */
     int compensate_force;   /* add -sum(F_ext)/N_fluid to the fluid */
+    /* repulsive pore-wall beads (Sec. 2.3): beads on the cylinder of radius
+       wall_R + wall_rp around the pore axis, wall_spacing apart around and
+       along it, WCA with sigma = wall_rr + wall_rp, epsilon = wall_eps,
+       acting on every colloid bead; their force goes to the body only */
+    int wall_beads;
+    int wall_axis;
+    double wall_R, wall_spacing, wall_rp, wall_rr, wall_eps;
 } orc_params;
 
 typedef struct {
@@ -358,6 +365,88 @@ static void euler_half_kick_implicit(double w[3], const double I[3], const doubl
         cross(w, Iw, wxIw);
         for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * (T[a] - wxIw[a]) / I[a];
     }
+}
+
+/* ------------------------------------------------------- pore-wall beads */
+
+#define ORC_PI 3.14159265358979323846
+
+/* Ring and row counts of the wall-bead lattice and the pore-bead position
+ * (j around, k along the axis). The axis passes through the box centre; the
+ * beads sit at (k + 1/2) L / n_rows along it. */
+static void wall_lattice(const orc_params *p, int *nth, int *nrow)
+{
+    int n[3] = {p->nx, p->ny, p->nz};
+    double Rc = p->wall_R + p->wall_rp;
+    *nth = (int)lround(2.0 * ORC_PI * Rc / p->wall_spacing);
+    if (*nth < 3) *nth = 3;
+    *nrow = (int)lround(n[p->wall_axis] / p->wall_spacing);
+    if (*nrow < 1) *nrow = 1;
+}
+
+/* WCA force on a colloid bead at r (lab frame) from every wall bead, with
+ * the minimum image along the periodic axis:
+ *   U(d) = 4 eps ((sigma/d)^12 - (sigma/d)^6) + eps for d < 2^(1/6) sigma,
+ *   F = -dU/dd along d = r - r_wall: 24 eps (2 (sigma/d)^12 - (sigma/d)^6) d / d^2. */
+static void wall_bead_force(const orc_params *p, const double r[3], double F[3])
+{
+    F[0] = F[1] = F[2] = 0.0;
+    if (!p->wall_beads) return;
+    int n[3] = {p->nx, p->ny, p->nz};
+    int ax = p->wall_axis, a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+    int nth, nrow;
+    wall_lattice(p, &nth, &nrow);
+    double Rc = p->wall_R + p->wall_rp, L = n[ax];
+    double sigma = p->wall_rr + p->wall_rp;
+    double rcut2 = pow(2.0, 1.0 / 3.0) * sigma * sigma;
+    for (int k = 0; k < nrow; ++k)
+        for (int j = 0; j < nth; ++j) {
+            double pw[3];
+            double th = 2.0 * ORC_PI * j / nth;
+            pw[a1] = 0.5 * n[a1] + Rc * cos(th);
+            pw[a2] = 0.5 * n[a2] + Rc * sin(th);
+            pw[ax] = (k + 0.5) * L / nrow;
+            double d[3];
+            for (int a = 0; a < 3; ++a) d[a] = r[a] - pw[a];
+            d[ax] -= L * floor(d[ax] / L + 0.5);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rcut2) continue;
+            double sr2 = sigma * sigma / r2, sr6 = sr2 * sr2 * sr2;
+            double fm = 24.0 * p->wall_eps * (2.0 * sr6 * sr6 - sr6) / r2;
+            for (int a = 0; a < 3; ++a) F[a] += fm * d[a];
+        }
+}
+
+/* Exposed for tests: the wall force on one bead, and the potential. */
+void orc_wall_bead_force(const orc_params *p, const double r[3], double F[3]) { wall_bead_force(p, r, F); }
+
+double orc_wall_bead_energy(const orc_params *p, const double r[3])
+{
+    if (!p->wall_beads) return 0.0;
+    int n[3] = {p->nx, p->ny, p->nz};
+    int ax = p->wall_axis, a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+    int nth, nrow;
+    wall_lattice(p, &nth, &nrow);
+    double Rc = p->wall_R + p->wall_rp, L = n[ax];
+    double sigma = p->wall_rr + p->wall_rp;
+    double rcut2 = pow(2.0, 1.0 / 3.0) * sigma * sigma;
+    double U = 0.0;
+    for (int k = 0; k < nrow; ++k)
+        for (int j = 0; j < nth; ++j) {
+            double pw[3];
+            double th = 2.0 * ORC_PI * j / nth;
+            pw[a1] = 0.5 * n[a1] + Rc * cos(th);
+            pw[a2] = 0.5 * n[a2] + Rc * sin(th);
+            pw[ax] = (k + 0.5) * L / nrow;
+            double d[3];
+            for (int a = 0; a < 3; ++a) d[a] = r[a] - pw[a];
+            d[ax] -= L * floor(d[ax] / L + 0.5);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rcut2) continue;
+            double sr2 = sigma * sigma / r2, sr6 = sr2 * sr2 * sr2;
+            U += 4.0 * p->wall_eps * (sr6 * sr6 - sr6) + p->wall_eps;
+        }
+    return U;
 }
 
 /* ------------------------------------------------------------- public API */
@@ -629,6 +718,14 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
             for (int a = 0; a < 3; ++a) {
                 b->F_bead[3 * k + a] = Fb[a];
                 Ft[a] += Fb[a];
+                Tt[a] += tq[a];
+            }
+            /* pore-wall beads act on the bead, not on the fluid */
+            double Fw[3];
+            wall_bead_force(p, r, Fw);
+            cross(rel, Fw, tq);
+            for (int a = 0; a < 3; ++a) {
+                Ft[a] += Fw[a];
                 Tt[a] += tq[a];
             }
         }

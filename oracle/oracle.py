@@ -45,7 +45,10 @@ class Params(C.Structure):
                 ("rho0", C.c_double), ("kT", C.c_double), ("gamma_bead", C.c_double),
                 ("seed", C.c_uint64), ("instance", C.c_uint32),
                 ("body_force", C.c_double * 3),
-                ("compensate_force", C.c_int)]
+                ("compensate_force", C.c_int),
+                ("wall_beads", C.c_int), ("wall_axis", C.c_int),
+                ("wall_R", C.c_double), ("wall_spacing", C.c_double), ("wall_rp", C.c_double),
+                ("wall_rr", C.c_double), ("wall_eps", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -68,6 +71,9 @@ def lib():
             L.orc_step.argtypes = [C.POINTER(Params), _dp, C.c_void_p, _dp, C.c_void_p, C.c_int64]
             L.orc_step.restype = C.c_int
             L.orc_init.argtypes = [C.POINTER(Params), _dp]
+            L.orc_wall_bead_force.argtypes = [C.POINTER(Params), _dp, _dp]
+            L.orc_wall_bead_energy.argtypes = [C.POINTER(Params), _dp]
+            L.orc_wall_bead_energy.restype = C.c_double
             L.orc_moments_sum.argtypes = [C.POINTER(Params), _dp, C.c_void_p, _dp]
             L.orc_node_velocity.argtypes = [C.POINTER(Params), _dp, C.c_void_p, _dp, _dp]
             L.orc_lattice.argtypes = [_ip, _dp, _ip]
@@ -204,6 +210,24 @@ class OracleLB:
     # geometry ---------------------------------------------------------------
     def set_pore(self, R, axis=2):
         self.mask = pore_mask(self.p.nx, self.p.ny, self.p.nz, R, axis)
+
+    def set_pore_beads(self, R, axis, spacing, r_pore_bead, r_bead, eps):
+        """Repulsive pore-wall beads (see wall_bead_force in lb_oracle.c)."""
+        self.p.wall_beads = 1
+        self.p.wall_axis = int(axis)
+        self.p.wall_R = float(R)
+        self.p.wall_spacing = float(spacing)
+        self.p.wall_rp = float(r_pore_bead)
+        self.p.wall_rr = float(r_bead)
+        self.p.wall_eps = float(eps)
+
+    def wall_force(self, r):
+        F = np.zeros(3)
+        lib().orc_wall_bead_force(C.byref(self.p), _d(np.ascontiguousarray(r, np.float64)), _d(F))
+        return F
+
+    def wall_energy(self, r):
+        return lib().orc_wall_bead_energy(C.byref(self.p), _d(np.ascontiguousarray(r, np.float64)))
 
     def set_mask(self, mask):
         self.mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)

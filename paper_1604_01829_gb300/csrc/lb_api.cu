@@ -150,6 +150,7 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
     lbk::FluidArgs a{};
     a.g = h->g;
     a.f = h->f;
+    a.masks = h->dmask;
     // MRT coefficients with c_k = w_diag / b_k = (1/36) / b_k folded in
     static const double bk[19] = {1.0, 1.0 / 3, 1.0 / 3, 1.0 / 3, 2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9,
                                   1.0 / 9, 2.0 / 3, 2.0 / 3, 2.0 / 3, 2.0 / 9, 2.0 / 9, 2.0 / 9, 2.0, 4.0 / 3,
@@ -363,7 +364,7 @@ lb_status lb_destroy(lb_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
-                    h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec};
+                    h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec, h->dmask};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -382,10 +383,33 @@ lb_status lb_set_pore(lb_handle h, double radius, int axis) {
     const double t = std::ceil(4.0 * (radius * radius));
     h->g.pore_axis = axis;
     h->g.pore_t = (long long)t;
+    h->pore_R = radius;
+    h->wall = lbk::WallBeads{};
     const double inner = std::sqrt(t) - 2.0 * std::sqrt(2.0) - 0.01;
     h->g.pore_in = inner > 0 ? (long long)std::floor(inner * inner) : 0;
     h->nfluid = count_fluid(h);
+    // wall masks of the positions across the axis, read by the fluid kernel
+    if (h->dmask) {
+        LB_CUDA(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->dmask);
+        h->dmask = nullptr;
+    }
+    lb_status s = dev_alloc(h, &h->dmask, sizeof(uint32_t) * (size_t)lbk::pore_section_size(h->g));
+    if (s != LB_OK) return s;
+    LB_CUDA(h, lbk::launch_build_masks(h->g, h->dmask, h->stream));
     // populations of new wall nodes are never read; nothing else changes
+    return LB_OK;
+}
+
+lb_status lb_set_pore_beads(lb_handle h, double spacing, double r_pore_bead, double r_bead, double epsilon) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (h->g.pore_axis < 0) return fail(h, LB_ERR_STATE, "lb_set_pore_beads needs a pore (lb_set_pore)");
+    if (spacing == 0.0) {
+        h->wall = lbk::WallBeads{};
+        return LB_OK;
+    }
+    if (!lbk::make_wall_beads(h->g, h->pore_R, spacing, r_pore_bead, r_bead, epsilon, h->wall))
+        return fail(h, LB_ERR_ARG, "spacing > 0, radii >= 0 with a positive sum, epsilon >= 0");
     return LB_OK;
 }
 
@@ -493,6 +517,7 @@ lb_status lb_step(lb_handle h, int nsteps) {
         if (coupled) {
             lbk::CoupleArgs c{};
             c.g = h->g;
+            c.wall = h->wall;
             c.f = h->f;
             c.fp32 = h->fp32;
             c.odd = odd;

@@ -51,6 +51,8 @@ struct BInst {
     uint32_t key0, key1, instance;
     double rho0, gamma, noise_amp;
     float gamma_f, noise_amp_f;
+    double pore_R;
+    WallBeads wall;              // pore-wall beads
     double gd[3];                // uniform force density
     float gf[3];
     CollParams<double> pd;
@@ -74,33 +76,6 @@ struct BatchArgs {
 };
 
 namespace {
-
-__constant__ signed char kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
-                                       {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                                       {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                                       {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-
-// 18-bit mask of the links whose upstream node is a wall node
-__device__ uint32_t upstream_wall_mask(const Geom &g, int x, int y, int z) {
-    uint32_t m = 0;
-#pragma unroll 1
-    for (int i = 1; i < 19; ++i) {
-        const int xs = wrapm(x - kC[i][0], g.nx), ys = wrapm(y - kC[i][1], g.ny), zs = wrapm(z - kC[i][2], g.nz);
-        if (pore_r2(g, xs, ys, zs) >= g.pore_t) m |= 1u << i;
-    }
-    return m;
-}
-
-// wall masks of one pore instance, one thread per position across the axis
-__global__ void k_build_masks(Geom g, uint32_t *out, int n) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int x = 0, y = 0, z = 0;
-    if (g.pore_axis == 2) { x = t % g.nx; y = t / g.nx; }
-    else if (g.pore_axis == 1) { x = t % g.nx; z = t / g.nx; }
-    else { y = t % g.ny; z = t / g.ny; }
-    out[t] = pore_r2(g, x, y, z) >= g.pore_t ? (1u << 31) : upstream_wall_mask(g, x, y, z);
-}
 
 template <typename T, int COLL, bool NOISE, bool ODD, bool COMMON>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_batch_collide(const BatchArgs a) {
@@ -248,6 +223,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     const BInst &I = b.inst[b.bodies[b.bead_body[kk]].inst];
     CoupleArgs a;
     a.g = I.g;
+    a.wall = I.wall;
     a.f = static_cast<const T *>(b.pool) + I.off;
     a.fp32 = b.fp32;
     a.odd = b.odd;
@@ -575,9 +551,7 @@ lb_status upload(lb_batch_ctx *h) {
         for (int k = 0; k < h->n; ++k) {
             const BInst &I = h->hinst[k];
             if (I.moff < 0) continue;
-            const int n = I.g.pore_axis == 2 ? I.g.nx * I.g.ny : (I.g.pore_axis == 1 ? I.g.nx * I.g.nz : I.g.ny * I.g.nz);
-            lbk::k_build_masks<<<(n + 255) / 256, 256, 0, h->stream>>>(I.g, h->dmask + I.moff, n);
-            BCUDA(h, cudaGetLastError());
+            BCUDA(h, lbk::launch_build_masks(I.g, h->dmask + I.moff, h->stream));
         }
     }
     // fluid positions across the axis of each pore instance: the fluid
@@ -956,6 +930,8 @@ lb_status lb_batch_set_pore(lb_batch_handle h, int k, double radius, int axis) {
     const double t = std::ceil(4.0 * (radius * radius));
     I.g.pore_axis = axis;
     I.g.pore_t = (long long)t;
+    I.pore_R = radius;
+    I.wall = lbk::WallBeads{};
     const double inner = std::sqrt(t) - 2.0 * std::sqrt(2.0) - 0.01;
     I.g.pore_in = inner > 0 ? (long long)std::floor(inner * inner) : 0;
     const int na = axis == 0 ? I.g.ny : I.g.nx, nb = axis == 2 ? I.g.ny : I.g.nz;
@@ -967,6 +943,22 @@ lb_status lb_batch_set_pore(lb_batch_handle h, int k, double radius, int axis) {
             if (da * da + db * db < I.g.pore_t) ++c;
         }
     h->nfluid[k] = c * nl;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_pore_beads(lb_batch_handle h, int k, double spacing, double r_pore_bead, double r_bead,
+                                  double epsilon) {
+    lb_status s = check(h, k);
+    if (s != LB_OK) return s;
+    if (h->uploaded) return bfail(h, LB_ERR_STATE, "pore beads must be set before the first step");
+    BInst &I = h->hinst[k];
+    if (I.g.pore_axis < 0) return bfail(h, LB_ERR_STATE, "lb_batch_set_pore_beads needs a pore");
+    if (spacing == 0.0) {
+        I.wall = lbk::WallBeads{};
+        return LB_OK;
+    }
+    if (!lbk::make_wall_beads(I.g, I.pore_R, spacing, r_pore_bead, r_bead, epsilon, I.wall))
+        return bfail(h, LB_ERR_ARG, "spacing > 0, radii >= 0 with a positive sum, epsilon >= 0");
     return LB_OK;
 }
 

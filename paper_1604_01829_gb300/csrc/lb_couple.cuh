@@ -24,6 +24,46 @@ __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int
     j[0] = jx; j[1] = jy; j[2] = jz;
 }
 
+// WCA force of the pore-wall beads on a colloid bead at r (lab frame), from
+// the wall beads in a window around the nearest one (the window covers every
+// wall bead within the cutoff), minimum image along the periodic axis.
+__device__ __forceinline__ void wall_bead_force(const WallBeads &w, const double r[3], double F[3]) {
+    F[0] = F[1] = F[2] = 0.0;
+    const int ax = w.axis, a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+    const double du = r[a1] - w.cu, dv = r[a2] - w.cv;
+    const double rho2 = du * du + dv * dv;
+    const double reach = w.Rc - sqrt(w.rcut2);
+    if (reach > 0.0 && rho2 < reach * reach) return;          // no wall bead within the cutoff
+    const double twopi = 6.283185307179586;
+    const double phi = atan2(dv, du);
+    const int j0 = (int)lrint(phi * w.ntheta / twopi);
+    const int k0 = (int)lrint(r[ax] * w.nrow / w.L - 0.5);
+    const bool all_j = 2 * w.wt + 1 >= w.ntheta, all_k = 2 * w.wz + 1 >= w.nrow;
+    const int jlo = all_j ? 0 : j0 - w.wt, jhi = all_j ? w.ntheta - 1 : j0 + w.wt;
+    const int klo = all_k ? 0 : k0 - w.wz, khi = all_k ? w.nrow - 1 : k0 + w.wz;
+    for (int kk = klo; kk <= khi; ++kk) {
+        int k = kk % w.nrow;
+        if (k < 0) k += w.nrow;
+        for (int jj = jlo; jj <= jhi; ++jj) {
+            int j = jj % w.ntheta;
+            if (j < 0) j += w.ntheta;
+            double sn, cs;
+            sincos(twopi * j / w.ntheta, &sn, &cs);
+            double d[3];
+            d[a1] = du - w.Rc * cs;
+            d[a2] = dv - w.Rc * sn;
+            double dz = r[ax] - (k + 0.5) * w.L / w.nrow;
+            dz -= w.L * floor(dz / w.L + 0.5);
+            d[ax] = dz;
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (d2 >= w.rcut2) continue;
+            const double sr2 = w.sigma2 / d2, sr6 = sr2 * sr2 * sr2;
+            const double fm = 24.0 * w.eps * (2.0 * sr6 * sr6 - sr6) / d2;
+            for (int q = 0; q < 3; ++q) F[q] += fm * d[q];
+        }
+    }
+}
+
 // FP32 storage: the same coupling with every per-bead quantity in FP32
 // (GB300's FP64 pipe is narrow and one bead's FP64 work, done by one lane,
 // would bound the kernel). The virtual site is formed relative to the body:
@@ -107,10 +147,17 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
     // body, FP64 accumulation on the body
     float FT[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (active && c == 0) {
-        FT[0] = Fb[0]; FT[1] = Fb[1]; FT[2] = Fb[2];
-        FT[3] = rel[1] * Fb[2] - rel[2] * Fb[1];
-        FT[4] = rel[2] * Fb[0] - rel[0] * Fb[2];
-        FT[5] = rel[0] * Fb[1] - rel[1] * Fb[0];
+        float Ft[3] = {Fb[0], Fb[1], Fb[2]};
+        if (a.wall.on) {                 // pore-wall beads: on the body, not the fluid
+            const double r[3] = {Bp->X[0] + rel[0], Bp->X[1] + rel[1], Bp->X[2] + rel[2]};
+            double Fw[3];
+            wall_bead_force(a.wall, r, Fw);
+            for (int q = 0; q < 3; ++q) Ft[q] += (float)Fw[q];
+        }
+        FT[0] = Ft[0]; FT[1] = Ft[1]; FT[2] = Ft[2];
+        FT[3] = rel[1] * Ft[2] - rel[2] * Ft[1];
+        FT[4] = rel[2] * Ft[0] - rel[0] * Ft[2];
+        FT[5] = rel[0] * Ft[1] - rel[1] * Ft[0];
     }
     const int b_first = __shfl_sync(0xffffffffu, body, 0);
     const bool lead = active && c == 0;
@@ -227,6 +274,12 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
         double tq[3];
         cross3(rel, Fb, tq);
         for (int q = 0; q < 3; ++q) { FT[q] = Fb[q]; FT[3 + q] = tq[q]; }
+        if (a.wall.on) {                 // pore-wall beads: on the body, not the fluid
+            double Fw[3];
+            wall_bead_force(a.wall, r, Fw);
+            cross3(rel, Fw, tq);
+            for (int q = 0; q < 3; ++q) { FT[q] += Fw[q]; FT[3 + q] += tq[q]; }
+        }
     }
     const int b_first = __shfl_sync(0xffffffffu, body, 0);
     const bool lead = active && c == 0;

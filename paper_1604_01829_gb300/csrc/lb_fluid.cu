@@ -18,6 +18,9 @@
 // FP32 storage holds d_i = f_i - w_i rho0 and computes in FP32; all moments
 // but the density are unchanged by the shift, so only rho = rho0 + sum d_i
 // and the zeroth reconstruction coefficient see it.
+#include <algorithm>
+#include <cmath>
+
 #include "lb_collide.cuh"
 
 // Minimum resident blocks of 128 threads per SM requested for the FP32
@@ -30,7 +33,41 @@ namespace lbk {
 
 namespace {
 
+// ------------------------------------------------------------ pore wall masks
+__constant__ signed char kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                       {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                       {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                       {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+// One thread per position across the pore axis (the wall test ignores the
+// coordinate along it): bit 31 if the node is a wall node, else bit i for
+// every link whose upstream node x - c_i is a wall node.
+__global__ void k_build_masks(Geom g, uint32_t *out, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int x = 0, y = 0, z = 0;
+    if (g.pore_axis == 2) { x = t % g.nx; y = t / g.nx; }
+    else if (g.pore_axis == 1) { x = t % g.nx; z = t / g.nx; }
+    else { y = t % g.ny; z = t / g.ny; }
+    if (pore_r2(g, x, y, z) >= g.pore_t) {
+        out[t] = 1u << 31;
+        return;
+    }
+    uint32_t m = 0;
+    for (int i = 1; i < 19; ++i) {
+        const int xs = wrapm(x - kC[i][0], g.nx), ys = wrapm(y - kC[i][1], g.ny), zs = wrapm(z - kC[i][2], g.nz);
+        if (pore_r2(g, xs, ys, zs) >= g.pore_t) m |= 1u << i;
+    }
+    out[t] = m;
+}
+
+__device__ __forceinline__ uint32_t pore_section_index(const Geom &g, int x, int y, int z) {
+    return g.pore_axis == 2 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)y
+         : (g.pore_axis == 1 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)z : (uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
+}
+
 // ------------------------------------------------------- collide and stream
+
 template <typename T, int COLL, bool NOISE, bool ODD, bool PORE>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collide_stream(const FluidArgs a) {
     using R = T;
@@ -44,11 +81,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
     const long long N = g.N;
     const unsigned n = (unsigned)x + (unsigned)g.nx * ((unsigned)y + (unsigned)g.ny * (unsigned)z);
 
-    bool near_wall = false;
+    uint32_t wmask = 0;                      // bit i: the upstream node x - c_i is a wall node
     if (PORE) {
-        const long long r2 = pore_r2(g, x, y, z);
-        if (r2 >= g.pore_t) return;          // wall node: holds no fluid
-        near_wall = r2 >= g.pore_in;         // some neighbour may be a wall node
+        wmask = __ldg(a.masks + pore_section_index(g, x, y, z));
+        if (wmask >> 31) return;             // wall node: holds no fluid
     }
 
     // neighbour offsets with periodic wrap: node = xo[dx] + yo[dy] + zo[dz]
@@ -68,11 +104,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const unsigned src = (unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]);
-            if (PORE && near_wall) {
-                int xs = xo[1 - cx(i)], ys = (y - cy(i) + g.ny) % g.ny, zs = (z - cz(i) + g.nz) % g.nz;
-                if (pore_r2(g, xs, ys, zs) >= g.pore_t) { f[i] = plane(i)[n]; continue; }
-            }
-            f[i] = plane(opp(i))[src];
+            // halfway bounce-back: the population that left towards the wall
+            f[i] = (PORE && ((wmask >> i) & 1u)) ? plane(i)[n] : plane(opp(i))[src];
         }
     }
 
@@ -103,11 +136,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const unsigned dst = (unsigned)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
-            if (PORE && near_wall) {
-                int xd = xo[1 + cx(i)], yd = (y + cy(i) + g.ny) % g.ny, zd = (z + cz(i) + g.nz) % g.nz;
-                if (pore_r2(g, xd, yd, zd) >= g.pore_t) { plane(opp(i))[n] = f[i]; continue; }
-            }
-            plane(i)[dst] = f[i];
+            // downstream node x + c_i is the upstream node of link opp(i)
+            if (PORE && ((wmask >> opp(i)) & 1u)) plane(opp(i))[n] = f[i];
+            else plane(i)[dst] = f[i];
         }
     }
 }
@@ -265,6 +296,47 @@ cudaError_t launch_collide_stream(const FluidArgs &a, bool fp32, int collision, 
     if (collision == 0) return launch_cs_t<double, 0, false>(a, odd, block, s);
     if (noise) return launch_cs_t<double, 1, true>(a, odd, block, s);
     return launch_cs_t<double, 1, false>(a, odd, block, s);
+}
+
+bool make_wall_beads(const Geom &g, double pore_R, double spacing, double r_pore_bead, double r_bead, double eps,
+                     WallBeads &w) {
+    w = WallBeads{};
+    if (g.pore_axis < 0 || !(spacing > 0.0) || !(r_pore_bead >= 0.0) || !(r_bead >= 0.0) ||
+        !(r_pore_bead + r_bead > 0.0) || !(eps >= 0.0) || !std::isfinite(spacing) || !std::isfinite(eps))
+        return false;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const int ax = g.pore_axis, a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+    const double twopi = 6.283185307179586;
+    w.on = 1;
+    w.axis = ax;
+    w.Rc = pore_R + r_pore_bead;
+    w.L = n[ax];
+    w.cu = 0.5 * n[a1];
+    w.cv = 0.5 * n[a2];
+    w.ntheta = std::max(3, (int)std::lround(twopi * w.Rc / spacing));
+    w.nrow = std::max(1, (int)std::lround(w.L / spacing));
+    const double sigma = r_pore_bead + r_bead;
+    w.sigma2 = sigma * sigma;
+    w.rcut2 = std::pow(2.0, 1.0 / 3.0) * w.sigma2;
+    w.eps = eps;
+    // a bead at radius rho >= Rc - rcut is at distance >= 2 sqrt(rho Rc) sin(dphi / 2)
+    // from a wall bead dphi away around the axis, and >= |dz| along it
+    const double rcut = std::sqrt(w.rcut2), rmin = w.Rc - rcut;
+    const double x = rmin > 0.0 ? rcut / (2.0 * std::sqrt(rmin * w.Rc)) : 2.0;
+    w.wt = x >= 1.0 ? w.ntheta : (int)std::ceil(2.0 * std::asin(x) * w.ntheta / twopi + 0.5) + 1;
+    w.wz = (int)std::ceil(rcut / (w.L / w.nrow) + 0.5) + 1;
+    return true;
+}
+
+long long pore_section_size(const Geom &g) {
+    return g.pore_axis == 2 ? (long long)g.nx * g.ny
+         : (g.pore_axis == 1 ? (long long)g.nx * g.nz : (long long)g.ny * g.nz);
+}
+
+cudaError_t launch_build_masks(const Geom &g, uint32_t *out, cudaStream_t s) {
+    const int n = (int)pore_section_size(g);
+    k_build_masks<<<(n + 255) / 256, 256, 0, s>>>(g, out, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const void *f, bool fp32, const Geom &g, bool odd, double rho0, double *out,

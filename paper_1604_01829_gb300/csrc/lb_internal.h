@@ -40,6 +40,8 @@ struct FluidArgs {
     uint32_t step_off;
     int *err;                    // device error word (a bounded wait ran out), may be null
     void *plane[19];             // base of each population plane (f + i N), uniform per launch
+    const uint32_t *masks;       // pore: per position across the axis, bit 31 wall node, bit i the
+                                 // upstream node of link i is a wall (launch_build_masks)
 };
 
 // Rigid bodies (FP64, array of structs; few bodies, one thread each).
@@ -61,8 +63,25 @@ struct Body {
     int inst;                        // instance of a batch (0 for a single lattice)
 };
 
+// Repulsive pore-wall beads (Sec. 2.3): beads on the cylinder of radius Rc
+// (pore radius + pore-bead radius) around the pore axis, ntheta around and
+// nrow along it, WCA with sigma^2 = sigma2 and epsilon = eps up to
+// rcut2 = 2^(1/3) sigma^2, acting on colloid beads only. wt, wz: half
+// widths of the window of wall beads around a bead's nearest one that can
+// lie within the cutoff (host-computed; the whole ring or row when large).
+struct WallBeads {
+    int on, axis, ntheta, nrow, wt, wz;
+    double cu, cv;               // axis position across it (box centre)
+    double Rc, L, sigma2, rcut2, eps;
+};
+
+// wall-bead parameters from the user's (host; lb_fluid.cu); false if invalid
+bool make_wall_beads(const Geom &g, double pore_R, double spacing, double r_pore_bead, double r_bead, double eps,
+                     WallBeads &w);
+
 struct CoupleArgs {
     Geom g;
+    WallBeads wall;
     const void *f;               // populations (pre-collision of this step)
     bool fp32;                   // deviation storage
     bool odd;                    // parity of the step count
@@ -96,6 +115,10 @@ cudaError_t launch_collide_stream(const FluidArgs &a, bool fp32, int collision, 
                                   dim3 block, cudaStream_t s);
 // TMA-staged variant (FP32 storage, periodic, nx % 4 == 0); cudaErrorNotSupported otherwise
 bool tma_collide_supported(const Geom &g, bool fp32);
+// positions across the pore axis: nx*ny (axis z), nx*nz (axis y), ny*nz (axis x)
+long long pore_section_size(const Geom &g);
+// wall masks of a pore geometry into out[pore_section_size(g)]
+cudaError_t launch_build_masks(const Geom &g, uint32_t *out, cudaStream_t s);
 cudaError_t launch_collide_stream_tma(const FluidArgs &a, int collision, bool noise, bool odd, int stages_hint,
                                       int ctas_per_sm_hint, cudaStream_t s);
 cudaError_t launch_gather(const void *f, bool fp32, const Geom &g, bool odd, double rho0, double *out,

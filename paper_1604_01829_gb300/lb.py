@@ -50,6 +50,7 @@ _SIGS = {
     "lb_create": [C.POINTER(lb_params), C.c_void_p, C.POINTER(C.c_void_p)],
     "lb_destroy": [C.c_void_p],
     "lb_set_pore": [C.c_void_p, C.c_double, C.c_int],
+    "lb_set_pore_beads": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double],
     "lb_add_raspberry": [C.c_void_p, _dp, C.c_int, _dp, _dp, C.c_double, _dp, _dp, _dp, C.c_int, _ip],
     "lb_set_body_state": [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp],
     "lb_set_external_forces": [C.c_void_p, C.c_int, _dp, _dp],
@@ -75,6 +76,7 @@ _BSIGS = {
     "lb_batch_create": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)],
     "lb_batch_destroy": [C.c_void_p],
     "lb_batch_set_pore": [C.c_void_p, C.c_int, C.c_double, C.c_int],
+    "lb_batch_set_pore_beads": [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double],
     "lb_batch_add_raspberry": [C.c_void_p, C.c_int, _dp, C.c_int, _dp, _dp, C.c_double, _dp, _dp, _dp, C.c_int, _ip],
     "lb_batch_step": [C.c_void_p, C.c_int],
     "lb_batch_forces": [C.c_void_p, C.c_int, C.c_int, _dp, _dp],
@@ -244,6 +246,10 @@ class LB:
     def lb_set_pore(self, radius, axis=2):
         _check(self.h, load().lb_set_pore(self.h, float(radius), int(axis)))
 
+    def lb_set_pore_beads(self, spacing, r_pore_bead, r_bead, epsilon):
+        _check(self.h, load().lb_set_pore_beads(self.h, float(spacing), float(r_pore_bead), float(r_bead),
+                                                float(epsilon)))
+
     def lb_add_raspberry(self, beads, X, q=(1, 0, 0, 0), mass=1.0, inertia=(1, 1, 1),
                          F_ext=None, T_ext=None, fixed=False):
         b = np.ascontiguousarray(beads, dtype=np.float64).reshape(-1)
@@ -400,6 +406,10 @@ class LBBatch:
 
     def lb_batch_set_pore(self, inst, radius, axis=2):
         _bcheck(self.h, load().lb_batch_set_pore(self.h, int(inst), float(radius), int(axis)))
+
+    def lb_batch_set_pore_beads(self, inst, spacing, r_pore_bead, r_bead, epsilon):
+        _bcheck(self.h, load().lb_batch_set_pore_beads(self.h, int(inst), float(spacing), float(r_pore_bead),
+                                                       float(r_bead), float(epsilon)))
 
     def lb_batch_add_raspberry(self, inst, beads, X, q=(1, 0, 0, 0), mass=1.0, inertia=(1, 1, 1),
                                F_ext=None, T_ext=None, fixed=False):

@@ -138,3 +138,39 @@ def test_batch_instance_equals_single_handle():
     S.lb_step(6)
     assert np.abs(B.lb_batch_get_populations(k) - S.lb_get_populations()).max() <= 1e-13
     assert np.abs(B.lb_batch_get_body(k)["X"] - S.lb_get_body(0)["X"]).max() <= 1e-13
+
+
+def test_pore_wall_beads_in_a_batch():
+    """Two pore instances with wall beads (one along z, one along x) and a
+    periodic one; each equals the oracle run on that instance alone."""
+    from paper_1604_01829_gb300 import lb
+    g = Wl.paper_gamma_to_lattice(50.0)
+    sph = Wl.sphere_raspberry(2.0)
+    cases = [(dict(nx=20, ny=20, nz=14, seed=1, gamma_bead=g, kT=1e-4, **MRT), (7.5, 2), (10 + 4.9, 10.3, 6.1),
+              (2e-3, 0, 0)),
+             (dict(nx=12, ny=10, nz=9, seed=2, kT=1e-4, **MRT), None, None, None),
+             (dict(nx=14, ny=18, nz=18, seed=3, gamma_bead=g, kT=1e-4, **MRT), (7.0, 0), (7.2, 9.1, 9 - 4.4),
+              (0, 0, -2e-3))]
+    B = lb.LBBatch([dict(c[0], precision=64) for c in cases])
+    orcs = []
+    for k, (p, pore, X, F) in enumerate(cases):
+        o = O.OracleLB(p["nx"], p["ny"], p["nz"], **oracle_kw(p))
+        if pore is not None:
+            B.lb_batch_set_pore(k, *pore)
+            o.set_pore(*pore)
+            B.lb_batch_set_pore_beads(k, 2.0, 2.5, 0.5, 2e-3)
+            o.set_pore_beads(pore[0], pore[1], 2.0, 2.5, 0.5, 2e-3)
+            B.lb_batch_add_raspberry(k, sph, X, [1, 0, 0, 0], 34.0, (50, 50, 50), F, None, False)
+            o.add_raspberry(sph, X, (1, 0, 0, 0), 34.0, (50, 50, 50), F, (0, 0, 0), False)
+        orcs.append(o)
+    for _ in range(3):
+        B.lb_batch_step(3)
+        for o in orcs:
+            o.step(3)
+        for k in (0, 2):
+            F, T = B.lb_batch_forces(k, 0)
+            Fo, To = orcs[k].body(0)["F"], orcs[k].body(0)["T"]
+            assert np.abs(F - Fo).max() <= 1e-11 * np.abs(Fo).max(), (k, F, Fo)
+            assert np.abs(T - To).max() <= 1e-11 * np.abs(To).max(), (k, T, To)
+            Xg = B.lb_batch_get_body(k, 0)["X"]
+            assert np.abs(Xg - orcs[k].body(0)["X"]).max() <= 1e-11

@@ -184,6 +184,43 @@ def test_tma_ring_depths_with_coupling(stages, ctas):
         assert e["bead"] <= 5e-5 and e["F"] <= 5e-5, e
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("spacing,R,rp,rs,off", [(2.0, 7.5, 2.5, 2.0, 4.9), (0.9, 7.5, 2.5, 2.0, 4.9),
+                                                 (2.0, 3.0, 4.0, 1.5, 0.9)])
+def test_pore_wall_beads_match_oracle(precision, spacing, R, rp, rs, off):
+    """Repulsive pore-wall beads (WCA, Sec. 2.3) on a sphere raspberry pushed
+    towards the wall of a z pore: body force, torque and trajectory as the
+    oracle's sum over every wall bead (the GPU sums a window around the
+    nearest one). Dense wall beads and a narrow pore with a wide cutoff."""
+    params = dict(MRT, kT=1e-4, seed=31, gamma_bead=Wl.paper_gamma_to_lattice(50.0))
+    P = Pair(20, 20, 16, precision=precision, pore=(R, 2), **params)
+    P.gpu.lb_set_pore_beads(spacing, rp, 0.5, 2e-3)
+    P.orc.set_pore_beads(R, 2, spacing, rp, 0.5, 2e-3)
+    P.add_body(Wl.sphere_raspberry(rs), [10 + off, 10.3, 7.1], mass=34.0, inertia=(50, 50, 50),
+               F_ext=(2e-3, 0, 0))
+    # the wall beads do act on some of the colloid beads at this position
+    X = np.array([10 + off, 10.3, 7.1]) + Wl.sphere_raspberry(rs)
+    assert max(np.linalg.norm(P.orc.wall_force(x)) for x in X) > 1e-4
+    for _ in range(3):
+        P.step(3)
+        assert P.pop_error() <= TOL[precision]
+        e = P.body_errors(0)
+        tb = 1e-11 if precision == 64 else 5e-5
+        assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb and e["X"] <= tb, e
+
+
+def test_pore_beads_need_a_pore():
+    from paper_1604_01829_gb300 import lb
+    g = lb.LB(8, 8, 8)
+    with pytest.raises(lb.LBError) as ei:
+        g.lb_set_pore_beads(2.0, 2.5, 0.5, 1e-3)
+    assert ei.value.status == lb.LB_ERR_STATE
+    g.lb_set_pore(3.0, 2)
+    with pytest.raises(lb.LBError) as ei:
+        g.lb_set_pore_beads(-1.0, 2.5, 0.5, 1e-3)
+    assert ei.value.status == lb.LB_ERR_ARG
+
+
 def test_kernel_variant_rejects_unsupported_shapes():
     from paper_1604_01829_gb300 import lb
     g = lb.LB(37, 8, 8, precision=32)
