@@ -310,6 +310,7 @@ def run_ours(args, ws, rank, local):
                 "achieved_tflops": round(flops, 3), "nominal_tflops": FP64_NOMINAL_TFLOPS}
 
     batched = None if args.skip_batched else measure_batched(args, torch, lb, barrier_max, ws)
+    pore = None if args.skip_pore else measure_pore(torch, lb)
     adjoint = None if args.skip_adjoint else measure_adjoint(args, torch, lb)
 
     cpu = None
@@ -349,6 +350,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": 3 * K + 2,
             "fp64": fp64_line,
             "batched": batched,
+            "pore": pore,
             "adjoint": adjoint,
             "clocks": main["clocks"],
             "cpu_baseline": cpu,
@@ -446,6 +448,50 @@ def measure_batched(args, torch, lb, barrier_max, ws):
             "fluid_kernel": {"ms": round(kms / max(kn, 1), 4), "achieved_gbs": round(ach, 1),
                              "frac": round(ach / peak, 4), "peak_kind": kind},
             "trajectory": traj}
+
+
+def measure_pore(torch, lb, steps=2000):
+    """The confinement workload: 48x48x96 pore R = 20 along z, sphere R = 4
+    off the axis, FP32 MRT with fluctuations, repulsive wall beads (5 apart,
+    r_p = 6.25, r_r = 0.5, epsilon = kT, all in lattice units = nm), centre
+    recorded every 200 steps; then the binned pore-frame MSD of a trajectory
+    of 1.2e6 records (20 radial bins, 25 lags)."""
+    import numpy as np
+    from paper_1604_01829_gb300 import workloads as W
+    w = W.pore_48(offset_frac=0.4)
+    stream = torch.cuda.Stream()
+    L = lb.from_workload(w, stream=stream.cuda_stream)
+    L.lb_set_pore_beads(5.0, 6.25, 0.5, w.params["kT"])
+    L.lb_record_bodies(200, 64)
+    L.lb_step(10)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.lb_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rec = len(L.lb_get_trajectory(0)[0])
+    L.close()
+    rng = np.random.default_rng(1611)
+    n = 1_200_000
+    X = np.empty((n, 3))
+    X[:, 2] = np.cumsum(rng.normal(scale=0.3, size=n)) + 48.0
+    ang = np.cumsum(rng.normal(scale=0.02, size=n))
+    rad = 8.0 + 4.0 * np.sin(np.cumsum(rng.normal(scale=0.01, size=n)))
+    X[:, 0] = 24.0 + rad * np.cos(ang)
+    X[:, 1] = 24.0 + rad * np.sin(ang)
+    lb.lb_pore_msd(X[:1000], (48, 48, 96), 2, 20.0, 20, 25)          # warm-up
+    t0 = time.perf_counter()
+    lb.lb_pore_msd(X, (48, 48, 96), 2, 20.0, 20, 25)
+    sec = time.perf_counter() - t0
+    return {"workload": w.name + " FP32 MRT kT=1e-4, WCA wall beads 5 apart (r_p 6.25, r_r 0.5, eps kT), "
+                                 "record every 200 steps",
+            "nodes": w.nodes, "steps": steps, "ms_per_step": round(ms / steps, 4),
+            "value": round(w.nodes * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "l2": "state 34 MB fits in L2: MLUPS only", "records": rec,
+            "pore_msd": {"records": n, "bins": 20, "lags": 25, "ms": round(sec * 1e3, 2)}}
 
 
 def measure_msd(torch, lb, nbodies=256, nrec=4000, max_lag=400, seed=1610):
@@ -600,6 +646,7 @@ def main():
     ap.add_argument("--batch-schedule", default=None,
                     help="tile_nodes,blocks_per_sm,order for the batched leg instead of the autotuner")
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--skip-pore", action="store_true", help="skip the confinement leg")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     args = ap.parse_args()
     global ARGS

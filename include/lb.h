@@ -347,6 +347,24 @@ lb_status lb_batch_get_trajectory(lb_batch_handle h, int inst, int body_id, int 
 lb_status lb_msd_trajectory(const double *X, const double *q, int nrec, int nbodies, int max_lag,
                             const double p_ref[3], double *out, void *cuda_stream, char *err, size_t err_len);
 
+/* Pore-frame mean squared displacements of one trajectory on the GPU
+ * (Sec. 2.8 and the SI "Pore-frame coordinate determination"). X: host
+ * [nrec][3] centres at a fixed interval in a box nx*ny*nz with a pore of
+ * radius R_pore along `axis` through the box centre. Centres relative to the
+ * axis give x^c, y^c (across it, in the order x, y, z of the remaining two
+ * axes) and theta = atan2(y^c, x^c); each interval's displacement is rotated
+ * by P(theta) = [[cos, sin, 0], [-sin, cos, 0], [0, 0, 1]] at the start of
+ * the interval (x^p radial, y^p azimuthal, z^p axial) and summed, Eq.
+ * (poreframedisplacement). Every record t with radial coordinate r(t) <
+ * R_pore falls in bin floor(r(t) / R_pore * nbins) and its sub-trajectory
+ * adds (X^p(t + l) - X^p(t))^2 to that bin, Eq. (poreframetrajectory):
+ * out[(b*max_lag + l-1)*3 + c] is the mean over the counts[b*max_lag + l-1]
+ * origins of bin b (0 where there are none). Readings: theta at the start
+ * of the interval; the matrix's x_1 = y_1 = 1. Errors as lb_msd_trajectory
+ * (nbins 1-4096); allocates its own device memory. */
+lb_status lb_pore_msd(const double *X, int nrec, int nx, int ny, int nz, int axis, double R_pore, int nbins,
+                      int max_lag, double *out, long long *counts, void *cuda_stream, char *err, size_t err_len);
+
 /* Host-only: the velocity set c[19*3], weights w[19] and opposite-link table
  * opp[19] the library uses. Needs no GPU. Returns 19. */
 int lb_lattice(int *c, double *w, int *opp);

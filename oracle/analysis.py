@@ -120,3 +120,52 @@ def diffusivities(msd_row, tau):
     the (3/2) 2 tau denominator)."""
     return dict(D_t=msd_row[0:3].sum() / (6 * tau), D_t_body=msd_row[3:6] / (2 * tau),
                 D_r=msd_row[6] / (6 * tau), D_r_body=msd_row[7:10] / (3 * tau))
+
+
+# ------------------------------------------------------------ pore frame
+def pore_frame_trajectory(X, shape, axis=2):
+    """Sec. 2.8 and the SI "Pore-frame coordinate determination": centres
+    relative to the pore axis (x^c, y^c across it, z along it), the angle
+    theta = arctan(y^c / x^c) (read as atan2), one interval's displacement
+    rotated by P(theta) = [[cos, sin, 0], [-sin, cos, 0], [0, 0, 1]] with
+    theta at the start of the interval (x^p radial, y^p azimuthal, z^p
+    axial), summed from the first record, Eq. (poreframedisplacement).
+    Returns (X^p [n, 3], radial coordinate r [n])."""
+    X = np.asarray(X, float)
+    a1, a2 = (1, 2) if axis == 0 else ((0, 2) if axis == 1 else (0, 1))
+    xc = X[:, a1] - 0.5 * shape[a1]
+    yc = X[:, a2] - 0.5 * shape[a2]
+    zc = X[:, axis]
+    n = len(X)
+    Xp = np.zeros((n, 3))
+    for k in range(1, n):
+        th = np.arctan2(yc[k - 1], xc[k - 1])
+        P = np.array([[np.cos(th), np.sin(th), 0.0], [-np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
+        dXc = np.array([xc[k] - xc[k - 1], yc[k] - yc[k - 1], zc[k] - zc[k - 1]])
+        Xp[k] = Xp[k - 1] + P @ dXc
+    # r = sqrt(x^2 + y^2) in this order of operations: the bin decisions
+    # below depend on its last bit
+    return Xp, np.sqrt(xc * xc + yc * yc)
+
+
+def pore_msd(X, shape, axis, R_pore, nbins, max_lag):
+    """Binned pore-frame MSD (Sec. 2.8): each record t is binned by its
+    radial coordinate, bin = floor(r(t) / R_pore * nbins) (records with
+    r >= R_pore are left out), and the sub-trajectory starting there adds
+    (X^p(t + l) - X^p(t))^2 per pore-frame axis to that bin, Eq.
+    (poreframetrajectory). Returns (msd [nbins, max_lag, 3] averaged over
+    the origins in each bin, counts [nbins, max_lag])."""
+    Xp, r = pore_frame_trajectory(X, shape, axis)
+    n = len(Xp)
+    out = np.zeros((nbins, max_lag, 3))
+    cnt = np.zeros((nbins, max_lag), np.int64)
+    for lag in range(1, max_lag + 1):
+        for t in range(n - lag):
+            b = int(np.floor(r[t] / R_pore * nbins))      # same operations as the GPU
+            if b < 0 or b >= nbins:
+                continue
+            out[b, lag - 1] += (Xp[t + lag] - Xp[t]) ** 2
+            cnt[b, lag - 1] += 1
+    nz = cnt > 0
+    out[nz] /= cnt[nz][:, None]
+    return out, cnt

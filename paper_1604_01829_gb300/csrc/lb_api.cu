@@ -195,6 +195,15 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
     return a;
 }
 
+// the captured step pair holds launch arguments by value: drop it whenever
+// one of them changes
+void drop_graph(lb_ctx *h) {
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+}
+
 lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
     const bool noise = h->p.collision == 1 && h->p.kT > 0.0;
     if (h->timing) {
@@ -362,6 +371,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
 lb_status lb_destroy(lb_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
                     h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec, h->dmask};
@@ -375,6 +385,7 @@ lb_status lb_destroy(lb_handle h) {
 
 lb_status lb_set_pore(lb_handle h, double radius, int axis) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    drop_graph(h);
     if (h->step > 0 || h->uploaded) return fail(h, LB_ERR_STATE, "lb_set_pore must come before the first lb_step");
     if (axis < 0 || axis > 2) return fail(h, LB_ERR_ARG, "axis must be 0, 1 or 2");
     if (!(radius > 0.0) || !std::isfinite(radius)) return fail(h, LB_ERR_ARG, "radius must be > 0");
@@ -403,6 +414,7 @@ lb_status lb_set_pore(lb_handle h, double radius, int axis) {
 
 lb_status lb_set_pore_beads(lb_handle h, double spacing, double r_pore_bead, double r_bead, double epsilon) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    drop_graph(h);
     if (h->g.pore_axis < 0) return fail(h, LB_ERR_STATE, "lb_set_pore_beads needs a pore (lb_set_pore)");
     if (spacing == 0.0) {
         h->wall = lbk::WallBeads{};
@@ -491,74 +503,126 @@ lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, 
     return LB_OK;
 }
 
+namespace {
+
+// Launches step h->step + k (k-th of a group; the step counter on the device
+// is advanced once per group, so kernels read *step_dev + k): the previous
+// step's second half kick if finish_prev, this step's kick and drift with the
+// clearing of its spread-force tiles, the coupling, the fluid kernel.
+lb_status launch_one_step(lb_ctx *h, int k, bool finish_prev) {
+    const int nb = (int)h->hb.size();
+    const int nbeads = (int)h->hbody_of.size();
+    const bool coupled = nb > 0 && nbeads > 0;
+    const long long t = h->step + k;
+    const bool odd = (t & 1) != 0;
+    const int cur = (int)(t & 1), prev = cur ^ 1;
+    if (nb > 0) {
+        const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
+        cudaError_t e = lbk::launch_step_pre(h->db, nb, finish_prev, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
+                                             coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
+                                             h->list_cap, h->g, h->ntx, h->nty, rec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
+        // the list of this buffer restarts empty for this step's coupling
+        if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
+    }
+    if (coupled) {
+        lbk::CoupleArgs c{};
+        c.g = h->g;
+        c.wall = h->wall;
+        c.f = h->f;
+        c.fp32 = h->fp32;
+        c.odd = odd;
+        c.rho0 = h->p.rho0;
+        c.gamma = h->p.gamma_bead;
+        c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
+        c.gforce = h->gforce;
+        c.gforce_f = h->gforce_f;
+        c.Fprev = h->Fbuf[prev];
+        c.Fcur = h->Fbuf[cur];
+        c.tiles_cur = h->tiles[cur];
+        c.tlist = h->tlist[cur];
+        c.tcount = h->tcount[cur];
+        c.ntx = h->ntx;
+        c.nty = h->nty;
+        c.s = h->ds;
+        c.sf = h->dsf;
+        c.gamma_f = (float)c.gamma;
+        c.noise_amp_f = (float)c.noise_amp;
+        c.bead_body = h->dbody_of;
+        c.bodies = h->db;
+        c.F_bead = h->dFbead;
+        c.nbeads = nbeads;
+        c.key0 = (uint32_t)h->p.seed;
+        c.key1 = (uint32_t)(h->p.seed >> 32);
+        c.instance = h->p.instance;
+        c.step_base = h->step_dev;
+        c.step_off = (uint32_t)k;
+        cudaError_t e = lbk::launch_couple(c, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
+    }
+    return timed_collide(h, fluid_args(h, cur, (uint32_t)k), odd);
+}
+
+// end of a group of n steps: the last step's second half kick, counter advance
+lb_status finish_group(lb_ctx *h, int n) {
+    if (!h->hb.empty()) {
+        cudaError_t e = lbk::launch_kick2(h->db, (int)h->hb.size(), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
+    }
+    cudaError_t e = lbk::launch_advance(h->step_dev, (unsigned)n, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "advance launch");
+    return LB_OK;
+}
+
+lb_status eager_steps(lb_ctx *h, int n) {
+    for (int k = 0; k < n; ++k) {
+        lb_status s = launch_one_step(h, k, k > 0);
+        if (s != LB_OK) return s;
+    }
+    lb_status s = finish_group(h, n);
+    h->step += n;
+    return s;
+}
+
+// an even and an odd step as one CUDA graph, replayed from even step counts
+lb_status ensure_graph(lb_ctx *h) {
+    if (h->gexec) return LB_OK;
+    cudaGraph_t graph = nullptr;
+    LB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lb_status s = launch_one_step(h, 0, false);
+    if (s == LB_OK) s = launch_one_step(h, 1, true);
+    if (s == LB_OK) s = finish_group(h, 2);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (s != LB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    return LB_OK;
+}
+
+}  // namespace
+
 lb_status lb_step(lb_handle h, int nsteps) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
     if (nsteps < 0) return fail(h, LB_ERR_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return LB_OK;
     lb_status s = upload_bodies(h);
     if (s != LB_OK) return s;
-    const int nb = (int)h->hb.size();
-    const int nbeads = (int)h->hbody_of.size();
-    const bool coupled = nb > 0 && nbeads > 0;
-    for (int k = 0; k < nsteps; ++k) {
-        const bool odd = (h->step & 1) != 0;
-        const int cur = (int)(h->step & 1), prev = cur ^ 1;
-        if (nb > 0) {
-            // previous step's second half kick (k > 0), this step's kick and
-            // drift, and the clearing of this step's spread-force tiles
-            const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
-            cudaError_t e = lbk::launch_step_pre(h->db, nb, k > 0, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
-                                                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
-                                                 h->list_cap, h->g, h->ntx, h->nty, rec, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
-            // the list of this buffer restarts empty for this step's coupling
-            if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
-        }
-        if (coupled) {
-            lbk::CoupleArgs c{};
-            c.g = h->g;
-            c.wall = h->wall;
-            c.f = h->f;
-            c.fp32 = h->fp32;
-            c.odd = odd;
-            c.rho0 = h->p.rho0;
-            c.gamma = h->p.gamma_bead;
-            c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
-            c.gforce = h->gforce;
-            c.gforce_f = h->gforce_f;
-            c.Fprev = h->Fbuf[prev];
-            c.Fcur = h->Fbuf[cur];
-            c.tiles_cur = h->tiles[cur];
-            c.tlist = h->tlist[cur];
-            c.tcount = h->tcount[cur];
-            c.ntx = h->ntx;
-            c.nty = h->nty;
-            c.s = h->ds;
-            c.sf = h->dsf;
-            c.gamma_f = (float)c.gamma;
-            c.noise_amp_f = (float)c.noise_amp;
-            c.bead_body = h->dbody_of;
-            c.bodies = h->db;
-            c.F_bead = h->dFbead;
-            c.nbeads = nbeads;
-            c.key0 = (uint32_t)h->p.seed;
-            c.key1 = (uint32_t)(h->p.seed >> 32);
-            c.instance = h->p.instance;
-            c.step_base = h->step_dev;
-            c.step_off = (uint32_t)k;
-            cudaError_t e = lbk::launch_couple(c, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
-        }
-        s = timed_collide(h, fluid_args(h, cur, (uint32_t)k), odd);
-        if (s != LB_OK) return s;
-        ++h->step;
+    // short calls, timed kernels and the TMA variant launch step by step
+    if (nsteps < 4 || h->timing || h->cs_variant == 2) return eager_steps(h, nsteps);
+    if (h->step & 1) {
+        if ((s = eager_steps(h, 1)) != LB_OK) return s;
+        --nsteps;
     }
-    if (nb > 0) {
-        cudaError_t e = lbk::launch_kick2(h->db, nb, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
-    }
-    cudaError_t e = lbk::launch_advance(h->step_dev, (unsigned)nsteps, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "advance launch");
+    const int pairs = nsteps / 2;
+    if ((s = ensure_graph(h)) != LB_OK) return s;
+    for (int r = 0; r < pairs; ++r) LB_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+    h->step += 2LL * pairs;
+    if (nsteps & 1) return eager_steps(h, 1);
     return LB_OK;
 }
 
@@ -726,6 +790,7 @@ lb_status lb_info(lb_handle h, lb_info_t *info) {
 
 lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_per_sm) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    drop_graph(h);
     if (variant < 0 || variant > 2 || stages < 0 || stages > 6 || ctas_per_sm < 0 || ctas_per_sm > 8)
         return fail(h, LB_ERR_ARG, "variant 0-2, stages 0-6, ctas_per_sm 0-8");
     if (variant == 2 && !lbk::tma_collide_supported(h->g, h->fp32))
@@ -738,6 +803,7 @@ lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_p
 
 lb_status lb_record_bodies(lb_handle h, int every, int capacity) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    drop_graph(h);
     if (every < 0 || (every > 0 && capacity < 1)) return fail(h, LB_ERR_ARG, "every >= 0 and capacity >= 1");
     if (every > 0 && h->hb.empty()) return fail(h, LB_ERR_ARG, "no bodies to record");
     if (h->rec) {

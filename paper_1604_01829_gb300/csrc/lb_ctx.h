@@ -60,6 +60,7 @@ struct lb_ctx {
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;   // pairs
+    cudaGraphExec_t gexec = nullptr;   // an even and an odd step (lb_step)
     size_t ev_used = 0;
     double timed_ms = 0.0;
     long long timed_n = 0;

@@ -218,3 +218,138 @@ extern "C" lb_status lb_msd_trajectory(const double *X, const double *q, int nre
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("lb_msd_trajectory: ") + cudaGetErrorString(e));
     return LB_OK;
 }
+
+// --------------------------------------------------------------- pore frame
+// Pore-frame analysis (Sec. 2.8 and the SI "Pore-frame coordinate
+// determination"): centres relative to the pore axis (x^c, y^c across it, z
+// along it); one interval's displacement rotated into the frame of its start
+// (x^p radial, y^p azimuthal, z^p axial; cos and sin of theta as x^c / r and
+// y^c / r) and summed; the MSD of the sub-trajectories binned by the radial
+// coordinate of their first record.
+namespace lbk {
+namespace {
+
+struct PoreFrame {
+    int a1, a2, ax;
+    double c1, c2;
+};
+
+__device__ __forceinline__ double radial(double xc, double yc) {
+    return sqrt(__dadd_rn(__dmul_rn(xc, xc), __dmul_rn(yc, yc)));   // no contraction: bins depend on it
+}
+
+// one thread per record: increment over [k-1, k] (zero for k = 0) and r_k
+__global__ void k_pore_prep(const double *X, int nrec, PoreFrame pf, double *work) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrec) return;
+    const double *x = X + 3ll * k;
+    const double xc = x[pf.a1] - pf.c1, yc = x[pf.a2] - pf.c2;
+    double *w = work + 4ll * k;
+    w[3] = radial(xc, yc);
+    if (k == 0) {
+        w[0] = w[1] = w[2] = 0.0;
+        return;
+    }
+    const double *xp = x - 3;
+    const double xp1 = xp[pf.a1] - pf.c1, yp1 = xp[pf.a2] - pf.c2;
+    const double r0 = radial(xp1, yp1);
+    const double c = r0 > 0.0 ? xp1 / r0 : 1.0, s = r0 > 0.0 ? yp1 / r0 : 0.0;
+    const double dx = xc - xp1, dy = yc - yp1, dz = x[pf.ax] - xp[pf.ax];
+    w[0] = c * dx + s * dy;
+    w[1] = -s * dx + c * dy;
+    w[2] = dz;
+}
+
+__global__ void k_pore_scan(int nrec, double *work) {
+    const int c = threadIdx.x;
+    if (c >= 3) return;
+    double acc = 0.0;
+    for (int k = 0; k < nrec; ++k) {
+        acc += work[4ll * k + c];
+        work[4ll * k + c] = acc;
+    }
+}
+
+// one block per lag: per-bin sums in shared memory
+__global__ void k_pore_lags(int nrec, int nbins, double R, int max_lag, const double *work, double *out,
+                            long long *counts) {
+    extern __shared__ double sm[];
+    double *acc = sm;                                            // [nbins][3]
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(sm + 3 * nbins);
+    for (int i = threadIdx.x; i < 4 * nbins; i += blockDim.x) sm[i] = 0.0;
+    __syncthreads();
+    const int l = blockIdx.x + 1;
+    for (int t = threadIdx.x; t < nrec - l; t += blockDim.x) {
+        const double *w0 = work + 4ll * t, *w1 = work + 4ll * (t + l);
+        const double fb = floor(__dmul_rn(w0[3] / R, (double)nbins));
+        if (!(fb >= 0.0 && fb < (double)nbins)) continue;
+        const int b = (int)fb;
+        for (int c = 0; c < 3; ++c) {
+            const double d = w1[c] - w0[c];
+            atomicAdd(&acc[3 * b + c], d * d);
+        }
+        atomicAdd(&cnt[b], 1ull);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const unsigned long long n = cnt[b];
+        for (int c = 0; c < 3; ++c)
+            out[((long long)b * max_lag + (l - 1)) * 3 + c] = n ? acc[3 * b + c] / (double)n : 0.0;
+        counts[(long long)b * max_lag + (l - 1)] = (long long)n;
+    }
+}
+
+}  // namespace
+}  // namespace lbk
+
+extern "C" lb_status lb_pore_msd(const double *X, int nrec, int nx, int ny, int nz, int axis, double R_pore,
+                                 int nbins, int max_lag, double *out, long long *counts, void *cuda_stream,
+                                 char *err, size_t err_len) {
+    auto fail = [&](lb_status st, const std::string &m) {
+        if (err && err_len) {
+            std::strncpy(err, m.c_str(), err_len - 1);
+            err[err_len - 1] = 0;
+        }
+        return st;
+    };
+    if (!X || !out || !counts) return fail(LB_ERR_ARG, "null pointer");
+    if (nrec < 2 || max_lag < 1 || max_lag >= nrec || nbins < 1 || nbins > 4096 || axis < 0 || axis > 2 ||
+        !(R_pore > 0.0) || nx < 1 || ny < 1 || nz < 1)
+        return fail(LB_ERR_ARG, "need nrec >= 2, 1 <= max_lag < nrec, 1 <= nbins <= 4096, axis 0-2, R_pore > 0");
+    const int n[3] = {nx, ny, nz};
+    lbk::PoreFrame pf;
+    pf.ax = axis;
+    pf.a1 = axis == 0 ? 1 : 0;
+    pf.a2 = axis == 2 ? 1 : 2;
+    pf.c1 = 0.5 * n[pf.a1];
+    pf.c2 = 0.5 * n[pf.a2];
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t nX = 3ull * nrec, nw = 4ull * nrec, no = 3ull * nbins * max_lag, nc = (size_t)nbins * max_lag;
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc((void **)&d, (nX + nw + no + nc) * sizeof(double));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(LB_ERR_OOM, "device allocation for the trajectory failed");
+    }
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    double *dX = d, *dw = dX + nX, *dout = dw + nw;
+    long long *dcnt = reinterpret_cast<long long *>(dout + no);
+    const size_t smem = 4ull * nbins * sizeof(double);
+    e = cudaMemcpyAsync(dX, X, nX * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        lbk::k_pore_prep<<<(nrec + 255) / 256, 256, 0, s>>>(dX, nrec, pf, dw);
+        lbk::k_pore_scan<<<1, 32, 0, s>>>(nrec, dw);
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(lbk::k_pore_lags, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            lbk::k_pore_lags<<<max_lag, 256, smem, s>>>(nrec, nbins, R_pore, max_lag, dw, dout, dcnt);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, no * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, dcnt, nc * sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("lb_pore_msd: ") + cudaGetErrorString(e));
+    return LB_OK;
+}

@@ -95,7 +95,7 @@ _BSIGS = {
 # every symbol include/lb.h declares
 EXPORTS = sorted(list(_SIGS) + list(_BSIGS) + ["lb_last_error", "lb_status_string", "lb_lattice",
                                                 "lb_moments_noalloc", "lb_batch_last_error",
-                                                "lb_msd_trajectory"])
+                                                "lb_msd_trajectory", "lb_pore_msd"])
 
 
 def load():
@@ -127,6 +127,9 @@ def load():
             L.lb_msd_trajectory.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_void_p,
                                             C.c_char_p, C.c_size_t]
             L.lb_msd_trajectory.restype = C.c_int
+            L.lb_pore_msd.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                      C.c_int, _dp, _llp, C.c_void_p, C.c_char_p, C.c_size_t]
+            L.lb_pore_msd.restype = C.c_int
             _lib = L
     return _lib
 
@@ -201,6 +204,21 @@ def lb_msd_trajectory(X, q, max_lag, p_ref=(1.0, 0.0, 0.0), stream=None):
     if st != LB_OK:
         raise LBError(st, err.value.decode())
     return out
+
+
+def lb_pore_msd(X, shape, axis, R_pore, nbins, max_lag, stream=None):
+    """Binned pore-frame MSD of one trajectory on the GPU (see include/lb.h):
+    returns (msd [nbins, max_lag, 3], counts [nbins, max_lag])."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((int(nbins), int(max_lag), 3))
+    cnt = np.zeros((int(nbins), int(max_lag)), np.int64)
+    err = C.create_string_buffer(256)
+    st = load().lb_pore_msd(_d(X), len(X), int(shape[0]), int(shape[1]), int(shape[2]), int(axis),
+                            float(R_pore), int(nbins), int(max_lag), _d(out), cnt.ctypes.data_as(_llp),
+                            C.c_void_p(stream) if stream else None, err, 256)
+    if st != LB_OK:
+        raise LBError(st, err.value.decode())
+    return out, cnt
 
 
 def make_params(nx, ny, nz, precision=64, collision=0, tau=1.0, gamma_shear=0.0, gamma_bulk=0.0,

@@ -129,3 +129,55 @@ def test_lab_angle_equals_arccos_of_unit_vectors():
         a, b = rng.normal(size=3), rng.normal(size=3)
         ref = math.acos(np.dot(a, b) / np.linalg.norm(a) / np.linalg.norm(b))
         assert A.lab_angle(a, b) == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+# ---------------------------------------------------------------- pore frame
+SHAPE = (40, 40, 60)
+
+
+def test_pore_frame_radial_motion():
+    """Motion along a fixed radial direction: all of it is x^p (radial)."""
+    phi, dr, n = 0.7, 0.05, 30
+    r = 3.0 + dr * np.arange(n)
+    X = np.stack([20 + r * np.cos(phi), 20 + r * np.sin(phi), np.full(n, 5.0)], axis=1)
+    Xp, rr = A.pore_frame_trajectory(X, SHAPE, 2)
+    assert np.allclose(Xp[:, 0], dr * np.arange(n), atol=1e-12)
+    assert np.allclose(Xp[:, 1:], 0.0, atol=1e-12)
+    assert np.allclose(rr, r, rtol=1e-12)
+
+
+def test_pore_frame_circular_and_axial_motion():
+    """Uniform circular motion at radius rho, dphi per record, plus a constant
+    axial step: every interval adds (rho (cos dphi - 1), rho sin dphi, dz) in
+    the frame of its start, so the MSD at lag l is l^2 times their squares."""
+    rho, dphi, dz, n, L = 6.6, 0.05, 0.02, 200, 10
+    k = np.arange(n)
+    X = np.stack([20 + rho * np.cos(dphi * k), 20 + rho * np.sin(dphi * k), 30 + dz * k], axis=1)
+    msd, cnt = A.pore_msd(X, SHAPE, 2, 12.0, 4, L)
+    lags = np.arange(1, L + 1)[:, None]
+    step = np.array([rho * (np.cos(dphi) - 1), rho * np.sin(dphi), dz])
+    b = int(rho / 12.0 * 4)
+    assert np.allclose(msd[b], (lags * step) ** 2, rtol=1e-10)
+    assert np.array_equal(cnt[b], n - lags[:, 0])
+    assert np.all(cnt[[i for i in range(4) if i != b]] == 0)
+
+
+def test_pore_frame_bins_and_axes():
+    """Binning by the radial coordinate at the start of each sub-trajectory:
+    counts add up to the origins inside the pore; a pore along x uses (y, z)
+    across it and x along it."""
+    rng = np.random.default_rng(3)
+    n, L, R = 400, 6, 15.0
+    X = np.empty((n, 3))
+    X[0] = [20.0, 20.0, 20.0]
+    for k in range(1, n):
+        X[k] = X[k - 1] + rng.normal(scale=0.4, size=3)
+    r = np.hypot(X[:, 0] - 20, X[:, 1] - 20)
+    msd, cnt = A.pore_msd(X, SHAPE, 2, R, 5, L)
+    for lag in range(1, L + 1):
+        assert cnt[:, lag - 1].sum() == np.sum(r[: n - lag] < R)
+    # the same walk with the pore along x: swap the roles of the coordinates
+    Xx = X[:, [2, 0, 1]]
+    msd_x, cnt_x = A.pore_msd(Xx, (60, 40, 40), 0, R, 5, L)
+    assert np.array_equal(cnt, cnt_x)
+    assert np.allclose(msd, msd_x, rtol=1e-12, atol=1e-15)

@@ -221,6 +221,36 @@ def test_pore_beads_need_a_pore():
     assert ei.value.status == lb.LB_ERR_ARG
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_step_pairs_replayed_from_a_graph(precision):
+    """lb_step with four or more steps replays an even and an odd step from a
+    CUDA graph (odd starting counts take one step eagerly first): a pore with
+    wall beads, a free ellipsoid, thermal noise and the recorder; the graph
+    is rebuilt after the wall beads and the recorder change."""
+    params = dict(MRT, kT=1e-4, seed=61, gamma_bead=Wl.paper_gamma_to_lattice(50.0))
+    P = Pair(22, 22, 18, precision=precision, pore=(9.5, 2), **params)
+    P.set_populations(perturbed_populations(P.N, seed=6))
+    P.gpu.lb_set_pore_beads(2.0, 2.5, 0.5, 1e-3)
+    P.orc.set_pore_beads(9.5, 2, 2.0, 2.5, 0.5, 1e-3)
+    ell = Wl.ellipsoid_raspberry(4.0, 2.0, 2.0, seed=2)
+    P.add_body(ell, [11.3, 11.8, 9.2], [0.9, 0.2, -0.3, 0.1], mass=80.0, inertia=(40, 120, 120),
+               F_ext=(1e-3, 5e-4, 0))
+    P.gpu.lb_record_bodies(3, 50)
+    tb = 1e-11 if precision == 64 else 5e-5
+    for n in (9, 6, 4, 5):
+        if n == 4:
+            P.gpu.lb_set_pore_beads(2.5, 2.5, 0.5, 2e-3)
+            P.orc.set_pore_beads(9.5, 2, 2.5, 2.5, 0.5, 2e-3)
+            P.gpu.lb_record_bodies(2, 50)
+        P.step(n)
+        assert P.pop_error() <= TOL[precision]
+        e = P.body_errors(0)
+        assert e["bead"] <= tb and e["F"] <= tb and e["X"] <= tb, (n, e)
+    steps, X, q = P.gpu.lb_get_trajectory(0)          # recorder restarted at step 15, every 2
+    assert list(steps) == [16, 18, 20, 22, 24]
+    assert np.array_equal(X[-1], P.gpu.lb_get_body(0)["X"])
+
+
 def test_kernel_variant_rejects_unsupported_shapes():
     from paper_1604_01829_gb300 import lb
     g = lb.LB(37, 8, 8, precision=32)

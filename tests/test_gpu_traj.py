@@ -163,3 +163,45 @@ def test_batched_recorder_with_graph_replays_and_autotune():
             if (s, i, b) in expect:
                 Xg, qg = expect[(s, i, b)]
                 assert np.array_equal(X[kk], Xg) and np.array_equal(q[kk], qg), (s, i, b)
+
+
+@pytest.mark.parametrize("axis", [2, 0])
+def test_pore_msd_matches_oracle(axis):
+    """Binned pore-frame MSD of a random walk inside a pore: equal to the
+    oracle's analysis of the same trajectory (bins decided identically:
+    exact counts; sums to 1e-12)."""
+    from paper_1604_01829_gb300 import lb
+    rng = np.random.default_rng(7 + axis)
+    shape = (40, 40, 60) if axis == 2 else (60, 40, 40)
+    n, R = 600, 15.0
+    X = np.empty((n, 3))
+    X[0] = [s / 2 + 0.3 for s in shape]
+    for k in range(1, n):
+        X[k] = X[k - 1] + rng.normal(scale=0.5, size=3)
+    got, cnt = lb.lb_pore_msd(X, shape, axis, R, 6, 40)
+    ref, rcnt = A.pore_msd(X, shape, axis, R, 6, 40)
+    assert np.array_equal(cnt, rcnt)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def test_pore_msd_of_a_recorded_confined_trajectory():
+    """A thermal sphere raspberry in a pore with repulsive wall beads, its
+    centre recorded on the GPU every 5 steps, analysed by lb_pore_msd and by
+    the oracle analysis: same result; and the colloid stays inside the pore."""
+    from paper_1604_01829_gb300 import lb
+    params = dict(MRT, kT=1e-3, seed=44, gamma_bead=Wl.paper_gamma_to_lattice(50.0), precision=32)
+    h = lb.LB(24, 24, 32, **params)
+    h.lb_set_pore(9.0, 2)
+    h.lb_set_pore_beads(2.0, 2.5, 0.5, 1e-3)
+    h.lb_add_raspberry(Wl.sphere_raspberry(2.0), [12.0 + 3.0, 12.0, 16.0], mass=34.0, inertia=(50, 50, 50),
+                       F_ext=(5e-4, 0, 0))
+    h.lb_record_bodies(5, 400)
+    h.lb_step(2000)
+    steps, X, q = h.lb_get_trajectory(0)
+    assert len(steps) == 400
+    r = np.hypot(X[:, 0] - 12, X[:, 1] - 12)
+    assert r.max() < 9.0 - 2.0                         # the wall beads keep the sphere inside
+    got, cnt = lb.lb_pore_msd(X, (24, 24, 32), 2, 9.0, 3, 20)
+    ref, rcnt = A.pore_msd(X, (24, 24, 32), 2, 9.0, 3, 20)
+    assert np.array_equal(cnt, rcnt)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
