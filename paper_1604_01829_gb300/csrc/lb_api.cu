@@ -528,7 +528,6 @@ lb_status launch_one_step(lb_ctx *h, int k, bool finish_prev) {
     if (coupled) {
         lbk::CoupleArgs c{};
         c.g = h->g;
-        c.wall = h->wall;
         c.f = h->f;
         c.fp32 = h->fp32;
         c.odd = odd;
@@ -559,6 +558,8 @@ lb_status launch_one_step(lb_ctx *h, int k, bool finish_prev) {
         c.step_off = (uint32_t)k;
         cudaError_t e = lbk::launch_couple(c, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
+        e = lbk::launch_wall_beads(h->wall, h->db, h->ds, h->dbody_of, nbeads, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "wall beads launch");
     }
     return timed_collide(h, fluid_args(h, cur, (uint32_t)k), odd);
 }

@@ -223,7 +223,6 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     const BInst &I = b.inst[b.bodies[b.bead_body[kk]].inst];
     CoupleArgs a;
     a.g = I.g;
-    a.wall = I.wall;
     a.f = static_cast<const T *>(b.pool) + I.off;
     a.fp32 = b.fp32;
     a.odd = b.odd;
@@ -254,6 +253,16 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.step_base = b.step_base;
     a.step_off = b.step_off;
     couple_bead<T>(a, k, active ? b.bead_rng[k] : 0, t & 7, threadIdx.x & 31, active);
+}
+
+// pore-wall beads of each bead's instance (one thread per bead)
+__global__ void k_batch_wall(const BInst *inst, Body *bodies, const double *s, const int *bead_body, int nbeads) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nbeads) return;
+    const BInst &I = inst[bodies[bead_body[k]].inst];
+    if (!I.wall.on) return;
+    const WallBeads w = I.wall;
+    wall_bead_body(w, bodies, s, bead_body, k);
 }
 
 // previous step's second half kick (optional), this step's kick and drift,
@@ -384,6 +393,7 @@ struct lb_batch_ctx {
     int resident = 0;                       // resident CTAs per SM of the fluid kernel at TS threads
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
+    bool any_wall = false;                  // some instance has pore-wall beads
     // wall masks (BInst::moff) and fluid positions (BInst::loff) of the pore instances
     uint32_t *dmask = nullptr;
     uint32_t *dfluid = nullptr;
@@ -679,6 +689,10 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
         if (h->fp32) lbk::k_batch_couple<float><<<grid, 128, 0, h->stream>>>(c);
         else lbk::k_batch_couple<double><<<grid, 128, 0, h->stream>>>(c);
         BCUDA(h, cudaGetLastError());
+        if (h->any_wall) {
+            lbk::k_batch_wall<<<(nbeads + 127) / 128, 128, 0, h->stream>>>(h->dinst, h->db, h->ds, h->dbody_of, nbeads);
+            BCUDA(h, cudaGetLastError());
+        }
     }
     lbk::BatchArgs a{};
     a.inst = h->dinst;
@@ -959,6 +973,7 @@ lb_status lb_batch_set_pore_beads(lb_batch_handle h, int k, double spacing, doub
     }
     if (!lbk::make_wall_beads(I.g, I.pore_R, spacing, r_pore_bead, r_bead, epsilon, I.wall))
         return bfail(h, LB_ERR_ARG, "spacing > 0, radii >= 0 with a positive sum, epsilon >= 0");
+    h->any_wall = true;
     return LB_OK;
 }
 

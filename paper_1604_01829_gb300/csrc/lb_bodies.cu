@@ -57,6 +57,11 @@ __global__ void k_kick2(Body *bodies, int nb) {
     }
 }
 
+__global__ void k_wall_beads(const WallBeads w, Body *bodies, const double *s, const int *bead_body, int nbeads) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nbeads) wall_bead_body(w, bodies, s, bead_body, k);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,6 +89,13 @@ cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s) {
     const unsigned grid = (unsigned)((8LL * a.nbeads + 127) / 128);
     if (a.fp32) k_couple<float><<<grid, 128, 0, s>>>(a);
     else k_couple<double><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, const int *bead_body, int nbeads,
+                              cudaStream_t st) {
+    if (!w.on || nbeads <= 0) return cudaSuccess;
+    k_wall_beads<<<(nbeads + 127) / 128, 128, 0, st>>>(w, b, s, bead_body, nbeads);
     return cudaGetLastError();
 }
 

@@ -27,17 +27,19 @@ __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int
 // WCA force of the pore-wall beads on a colloid bead at r (lab frame), from
 // the wall beads in a window around the nearest one (the window covers every
 // wall bead within the cutoff), minimum image along the periodic axis.
+// Components are selected, not indexed, so nothing goes to local memory.
 __device__ __forceinline__ void wall_bead_force(const WallBeads &w, const double r[3], double F[3]) {
     F[0] = F[1] = F[2] = 0.0;
-    const int ax = w.axis, a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
-    const double du = r[a1] - w.cu, dv = r[a2] - w.cv;
+    const int ax = w.axis;
+    const double ru = ax == 0 ? r[1] : r[0], rv = ax == 2 ? r[1] : r[2], rz = ax == 0 ? r[0] : (ax == 1 ? r[1] : r[2]);
+    const double du = ru - w.cu, dv = rv - w.cv;
     const double rho2 = du * du + dv * dv;
     const double reach = w.Rc - sqrt(w.rcut2);
     if (reach > 0.0 && rho2 < reach * reach) return;          // no wall bead within the cutoff
     const double twopi = 6.283185307179586;
     const double phi = atan2(dv, du);
     const int j0 = (int)lrint(phi * w.ntheta / twopi);
-    const int k0 = (int)lrint(r[ax] * w.nrow / w.L - 0.5);
+    const int k0 = (int)lrint(rz * w.nrow / w.L - 0.5);
     const bool all_j = 2 * w.wt + 1 >= w.ntheta, all_k = 2 * w.wz + 1 >= w.nrow;
     const int jlo = all_j ? 0 : j0 - w.wt, jhi = all_j ? w.ntheta - 1 : j0 + w.wt;
     const int klo = all_k ? 0 : k0 - w.wz, khi = all_k ? w.nrow - 1 : k0 + w.wz;
@@ -49,18 +51,38 @@ __device__ __forceinline__ void wall_bead_force(const WallBeads &w, const double
             if (j < 0) j += w.ntheta;
             double sn, cs;
             sincos(twopi * j / w.ntheta, &sn, &cs);
-            double d[3];
-            d[a1] = du - w.Rc * cs;
-            d[a2] = dv - w.Rc * sn;
-            double dz = r[ax] - (k + 0.5) * w.L / w.nrow;
-            dz -= w.L * floor(dz / w.L + 0.5);
-            d[ax] = dz;
-            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const double eu = du - w.Rc * cs, ev = dv - w.Rc * sn;
+            double ez = rz - (k + 0.5) * w.L / w.nrow;
+            ez -= w.L * floor(ez / w.L + 0.5);
+            const double d2 = eu * eu + ev * ev + ez * ez;
             if (d2 >= w.rcut2) continue;
             const double sr2 = w.sigma2 / d2, sr6 = sr2 * sr2 * sr2;
             const double fm = 24.0 * w.eps * (2.0 * sr6 * sr6 - sr6) / d2;
-            for (int q = 0; q < 3; ++q) F[q] += fm * d[q];
+            // back to x, y, z: (u, v, axis) = (y, z, x), (x, z, y) or (x, y, z)
+            if (ax == 0) { F[1] += fm * eu; F[2] += fm * ev; F[0] += fm * ez; }
+            else if (ax == 1) { F[0] += fm * eu; F[2] += fm * ev; F[1] += fm * ez; }
+            else { F[0] += fm * eu; F[1] += fm * ev; F[2] += fm * ez; }
         }
+    }
+}
+
+// Force and torque of the pore-wall beads on every bead of a body (one
+// thread per bead, FP64): added to the body's accumulators, not the fluid.
+__device__ __forceinline__ void wall_bead_body(const WallBeads &w, Body *bodies, const double *s,
+                                               const int *bead_body, int k) {
+    Body &B = bodies[bead_body[k]];
+    const double s0 = s[3 * k], s1 = s[3 * k + 1], s2 = s[3 * k + 2];
+    double rel[3], r[3], F[3], tq[3];
+    for (int q = 0; q < 3; ++q) {
+        rel[q] = B.R[3 * q] * s0 + B.R[3 * q + 1] * s1 + B.R[3 * q + 2] * s2;
+        r[q] = B.X[q] + rel[q];
+    }
+    wall_bead_force(w, r, F);
+    if (F[0] == 0.0 && F[1] == 0.0 && F[2] == 0.0) return;
+    cross3(rel, F, tq);
+    for (int q = 0; q < 3; ++q) {
+        atomicAdd(&B.acc[q], F[q]);
+        atomicAdd(&B.acc[3 + q], tq[q]);
     }
 }
 
@@ -147,17 +169,10 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
     // body, FP64 accumulation on the body
     float FT[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (active && c == 0) {
-        float Ft[3] = {Fb[0], Fb[1], Fb[2]};
-        if (a.wall.on) {                 // pore-wall beads: on the body, not the fluid
-            const double r[3] = {Bp->X[0] + rel[0], Bp->X[1] + rel[1], Bp->X[2] + rel[2]};
-            double Fw[3];
-            wall_bead_force(a.wall, r, Fw);
-            for (int q = 0; q < 3; ++q) Ft[q] += (float)Fw[q];
-        }
-        FT[0] = Ft[0]; FT[1] = Ft[1]; FT[2] = Ft[2];
-        FT[3] = rel[1] * Ft[2] - rel[2] * Ft[1];
-        FT[4] = rel[2] * Ft[0] - rel[0] * Ft[2];
-        FT[5] = rel[0] * Ft[1] - rel[1] * Ft[0];
+        FT[0] = Fb[0]; FT[1] = Fb[1]; FT[2] = Fb[2];
+        FT[3] = rel[1] * Fb[2] - rel[2] * Fb[1];
+        FT[4] = rel[2] * Fb[0] - rel[0] * Fb[2];
+        FT[5] = rel[0] * Fb[1] - rel[1] * Fb[0];
     }
     const int b_first = __shfl_sync(0xffffffffu, body, 0);
     const bool lead = active && c == 0;
@@ -274,12 +289,6 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
         double tq[3];
         cross3(rel, Fb, tq);
         for (int q = 0; q < 3; ++q) { FT[q] = Fb[q]; FT[3 + q] = tq[q]; }
-        if (a.wall.on) {                 // pore-wall beads: on the body, not the fluid
-            double Fw[3];
-            wall_bead_force(a.wall, r, Fw);
-            cross3(rel, Fw, tq);
-            for (int q = 0; q < 3; ++q) { FT[q] += Fw[q]; FT[3 + q] += tq[q]; }
-        }
     }
     const int b_first = __shfl_sync(0xffffffffu, body, 0);
     const bool lead = active && c == 0;

@@ -81,7 +81,6 @@ bool make_wall_beads(const Geom &g, double pore_R, double spacing, double r_pore
 
 struct CoupleArgs {
     Geom g;
-    WallBeads wall;
     const void *f;               // populations (pre-collision of this step)
     bool fp32;                   // deviation storage
     bool odd;                    // parity of the step count
@@ -156,5 +155,8 @@ cudaError_t launch_msd(const double *X, const double *q, int nrec, int nbodies, 
                        double *work, double *out, cudaStream_t s);
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
 cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s);
+// force and torque of the pore-wall beads on every bead (after the coupling)
+cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, const int *bead_body, int nbeads,
+                              cudaStream_t st);
 
 }  // namespace lbk
