@@ -95,6 +95,19 @@ lb_status lb_destroy(lb_handle h);
  * the first lb_step. Errors: LB_ERR_ARG, LB_ERR_STATE. */
 lb_status lb_set_pore(lb_handle h, double radius, int axis);
 
+/* Moving walls for the Stokes-flow resistance set-up (Sec. 2.3: boundary
+ * nodes along the +y and -y faces with an imposed fluid velocity, the colloid
+ * held fixed in between): the planes y = -1/2 and y = ny - 1/2 bound the
+ * fluid and move with the tangential velocities u_lo[3] and u_hi[3] (y
+ * components must be 0); the box stays periodic in x and z. A population
+ * streaming into a wall returns reversed with the wall's momentum,
+ * f_opp(i) = f*_i - 6 w_i rho0 (c_i . u_wall) (moving-wall halfway
+ * bounce-back); a node beyond a wall carries the wall's velocity in the bead
+ * interpolation and takes no spread force. Mass stays exact. Only before the
+ * first lb_step and without a pore (LB_ERR_STATE); LB_ERR_ARG for a normal
+ * velocity component or ny < 2. Not available to lb_adjoint_drag. */
+lb_status lb_set_channel_walls(lb_handle h, const double u_lo[3], const double u_hi[3]);
+
 /* Repulsive pore wall for the raspberries (Sec. 2.3: beads placed around the
  * pore surface, a given distance apart, interacting with the colloid beads by
  * a purely repulsive WCA potential with sigma = r_bead + r_pore_bead).

@@ -195,6 +195,11 @@ typedef struct {
     int wall_beads;
     int wall_axis;
     double wall_R, wall_spacing, wall_rp, wall_rr, wall_eps;
+    /* moving walls normal to y (Sec. 2.3, the Stokes-flow set-up): the
+       planes y = -1/2 and y = ny - 1/2 bound the fluid, moving with the
+       tangential velocities uw_lo and uw_hi; the box is not periodic in y */
+    int ywalls;
+    double uw_lo[3], uw_hi[3];
 } orc_params;
 
 typedef struct {
@@ -683,10 +688,19 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
                 int o[3] = {cidx & 1, (cidx >> 1) & 1, (cidx >> 2) & 1};
                 double wt = 1.0;
                 for (int a = 0; a < 3; ++a) wt *= o[a] ? frac[a] : 1.0 - frac[a];
-                int xx = wrap(base[0] + o[0], nx), yy = wrap(base[1] + o[1], ny), zz = wrap(base[2] + o[2], nz);
+                int yraw = base[1] + o[1];
+                wgt[cidx] = wt;
+                if (p->ywalls && (yraw < 0 || yraw >= ny)) {
+                    /* a node beyond a moving wall carries the wall's velocity */
+                    const double *uw = yraw < 0 ? p->uw_lo : p->uw_hi;
+                    for (int a = 0; a < 3; ++a) ub[a] += wt * uw[a];
+                    fluid[cidx] = 0;
+                    node[cidx] = 0;
+                    continue;
+                }
+                int xx = wrap(base[0] + o[0], nx), yy = wrap(yraw, ny), zz = wrap(base[2] + o[2], nz);
                 size_t n = nidx(p, xx, yy, zz);
                 node[cidx] = n;
-                wgt[cidx] = wt;
                 fluid[cidx] = !(mask && mask[n]);
                 if (!fluid[cidx]) continue; /* wall nodes carry u = 0 */
                 double rho = 0.0, j[3] = {0, 0, 0};
@@ -758,7 +772,17 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
                 size_t n = nidx(p, x, y, z);
                 if (mask && mask[n]) continue;
                 for (int i = 0; i < NQ; ++i) {
-                    size_t to = nidx(p, wrap(x + CV[i][0], nx), wrap(y + CV[i][1], ny), wrap(z + CV[i][2], nz));
+                    int ty = y + CV[i][1];
+                    if (p->ywalls && (ty < 0 || ty >= ny)) {
+                        /* halfway bounce-back on a moving wall: the population
+                           returns reversed and takes the wall's momentum,
+                           f_opp(i) = f*_i - 6 w_i rho0 (c_i . u_wall) */
+                        const double *uw = ty < 0 ? p->uw_lo : p->uw_hi;
+                        double cu = CV[i][0] * uw[0] + CV[i][1] * uw[1] + CV[i][2] * uw[2];
+                        f[(size_t)OPP[i] * N + n] = fpost[(size_t)i * N + n] - 6.0 * WQ[i] * p->rho0 * cu;
+                        continue;
+                    }
+                    size_t to = nidx(p, wrap(x + CV[i][0], nx), wrap(ty, ny), wrap(z + CV[i][2], nz));
                     if (mask && mask[to])
                         f[(size_t)OPP[i] * N + n] = fpost[(size_t)i * N + n];
                     else
@@ -876,8 +900,8 @@ int orc_adjoint_drag(const orc_params *p, double *f, const unsigned char *mask, 
 {
     init_tables();
     if (p->kT > 0.0 || nsteps < 1 || window < 1 || window > nsteps || !b || jb < 0 || jb >= b->nbodies ||
-        axis < 0 || axis > 2)
-        return -2;
+        axis < 0 || axis > 2 || p->ywalls || p->wall_beads)
+        return -2;      /* the reverse pass covers pores and periodic boxes, without walls or wall beads */
     if (b->nbodies > 64) return -2;
     for (int bi = 0; bi < b->nbodies; ++bi)
         if (b->fixed[bi] != 1 && b->fixed[bi] != 2) return -2;

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("compensate_force", C.c_int),
                 ("wall_beads", C.c_int), ("wall_axis", C.c_int),
                 ("wall_R", C.c_double), ("wall_spacing", C.c_double), ("wall_rp", C.c_double),
-                ("wall_rr", C.c_double), ("wall_eps", C.c_double)]
+                ("wall_rr", C.c_double), ("wall_eps", C.c_double),
+                ("ywalls", C.c_int), ("uw_lo", C.c_double * 3), ("uw_hi", C.c_double * 3)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -210,6 +211,13 @@ class OracleLB:
     # geometry ---------------------------------------------------------------
     def set_pore(self, R, axis=2):
         self.mask = pore_mask(self.p.nx, self.p.ny, self.p.nz, R, axis)
+
+    def set_channel_walls(self, u_lo, u_hi):
+        """Moving walls at y = -1/2 and y = ny - 1/2 (see orc_params)."""
+        self.p.ywalls = 1
+        for a in range(3):
+            self.p.uw_lo[a] = float(u_lo[a])
+            self.p.uw_hi[a] = float(u_hi[a])
 
     def set_pore_beads(self, R, axis, spacing, r_pore_bead, r_bead, eps):
         """Repulsive pore-wall beads (see wall_bead_force in lb_oracle.c)."""

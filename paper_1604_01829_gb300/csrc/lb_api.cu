@@ -374,7 +374,7 @@ lb_status lb_destroy(lb_handle h) {
     drop_graph(h);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
-                    h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec, h->dmask};
+                    h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec, h->dmask, h->dwchan};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -385,6 +385,7 @@ lb_status lb_destroy(lb_handle h) {
 
 lb_status lb_set_pore(lb_handle h, double radius, int axis) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (h->g.chan) return fail(h, LB_ERR_STATE, "a lattice has either a pore or channel walls");
     drop_graph(h);
     if (h->step > 0 || h->uploaded) return fail(h, LB_ERR_STATE, "lb_set_pore must come before the first lb_step");
     if (axis < 0 || axis > 2) return fail(h, LB_ERR_ARG, "axis must be 0, 1 or 2");
@@ -409,6 +410,44 @@ lb_status lb_set_pore(lb_handle h, double radius, int axis) {
     if (s != LB_OK) return s;
     LB_CUDA(h, lbk::launch_build_masks(h->g, h->dmask, h->stream));
     // populations of new wall nodes are never read; nothing else changes
+    return LB_OK;
+}
+
+lb_status lb_set_channel_walls(lb_handle h, const double u_lo[3], const double u_hi[3]) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (h->step > 0 || h->uploaded) return fail(h, LB_ERR_STATE, "lb_set_channel_walls must come before the first lb_step");
+    if (h->g.pore_axis >= 0) return fail(h, LB_ERR_STATE, "a lattice has either a pore or channel walls");
+    if (!u_lo || !u_hi || u_lo[1] != 0.0 || u_hi[1] != 0.0 || h->g.ny < 2)
+        return fail(h, LB_ERR_ARG, "wall velocities must be tangential (y component 0), ny >= 2");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(u_lo[a]) || !std::isfinite(u_hi[a])) return fail(h, LB_ERR_ARG, "non-finite wall velocity");
+    drop_graph(h);
+    // bounce-back terms 6 w_i rho0 (c_i . u_wall) of both walls, then the velocities
+    static const int C[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                 {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                 {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                 {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    double tab[44];
+    for (int side = 0; side < 2; ++side) {
+        const double *u = side ? u_hi : u_lo;
+        for (int i = 0; i < 19; ++i) {
+            const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+            tab[19 * side + i] = 6.0 * w * h->p.rho0 * (C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2]);
+        }
+        for (int a = 0; a < 3; ++a) tab[38 + 3 * side + a] = u[a];
+    }
+    lb_status s;
+    if (!h->dwchan && (s = dev_alloc(h, &h->dwchan, sizeof(tab))) != LB_OK) return s;
+    LB_CUDA(h, cudaMemcpy(h->dwchan, tab, sizeof(tab), cudaMemcpyHostToDevice));
+    h->g.chan = 1;
+    h->g.wchan = h->dwchan;
+    if (h->dmask) {
+        cudaFree(h->dmask);
+        h->dmask = nullptr;
+    }
+    if ((s = dev_alloc(h, &h->dmask, sizeof(uint32_t) * (size_t)h->g.ny)) != LB_OK) return s;
+    LB_CUDA(h, lbk::launch_build_masks(h->g, h->dmask, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
 

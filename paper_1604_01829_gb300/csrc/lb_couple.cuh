@@ -113,21 +113,29 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
     const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
     const int n3[3] = {g.nx, g.ny, g.nz};
     int xyz[3] = {0, 0, 0};
+    int ywall = -1;                      // channel: this corner lies beyond the lower (0) or upper (1) wall
     float wt = 1.f;
     if (active) {
         for (int q = 0; q < 3; ++q) {
             const float tq = Bp->Xf[q] + rel[q];          // r - 1/2 - floor(X - 1/2)
             const float fl = floorf(tq);
             const float fr = tq - fl;
-            int b0 = (Bp->Xi[q] + (int)fl) % n3[q];
+            const int raw = Bp->Xi[q] + (int)fl;
+            if (q == 1 && g.chan) {
+                const int yr = raw + o[1];
+                ywall = yr < 0 ? 0 : (yr >= g.ny ? 1 : -1);
+            }
+            int b0 = raw % n3[q];
             if (b0 < 0) b0 += n3[q];
             xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
             wt *= o[q] ? fr : 1.f - fr;
         }
     }
     const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
-    const bool fluid = active && !is_wall(g, xyz[0], xyz[1], xyz[2]);
+    const bool fluid = active && ywall < 0 && !is_wall(g, xyz[0], xyz[1], xyz[2]);
     float ub[3] = {0.f, 0.f, 0.f};
+    if (active && ywall >= 0)            // a node beyond a moving wall carries the wall's velocity
+        for (int q = 0; q < 3; ++q) ub[q] = wt * (float)g.wchan[38 + 3 * ywall + q];
     if (fluid) {                         // wall nodes carry u = 0
         float rho, j[3];
         node_rho_j<float>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (float)a.rho0, rho, j);
@@ -225,18 +233,25 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
     int xyz[3];
     // positions in FP64; the weight and the node sums in the storage precision
     R wt = R(1);
+    int ywall = -1;                      // channel: this corner lies beyond the lower (0) or upper (1) wall
     for (int q = 0; q < 3; ++q) {
         const double tq = r[q] - 0.5;
         const double fl = floor(tq);
         const R fr = (R)(tq - fl);
+        if (q == 1 && g.chan) {
+            const int yr = (int)fl + o[1];
+            ywall = yr < 0 ? 0 : (yr >= g.ny ? 1 : -1);
+        }
         int b0 = (int)fl % n3[q];
         if (b0 < 0) b0 += n3[q];
         xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
         wt *= o[q] ? fr : R(1) - fr;
     }
     const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
-    const bool fluid = active && !is_wall(g, xyz[0], xyz[1], xyz[2]);
+    const bool fluid = active && ywall < 0 && !is_wall(g, xyz[0], xyz[1], xyz[2]);
     R ub[3] = {R(0), R(0), R(0)};
+    if (active && ywall >= 0)            // a node beyond a moving wall carries the wall's velocity
+        for (int q = 0; q < 3; ++q) ub[q] = wt * (R)g.wchan[38 + 3 * ywall + q];
     if (fluid) {                         // wall nodes carry u = 0
         R rho, j[3];
         node_rho_j<R>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (R)a.rho0, rho, j);

@@ -23,6 +23,7 @@ struct lb_ctx {
     int *err_dev = nullptr;                 // device error word of bounded waits
     uint32_t *dmask = nullptr;              // pore wall masks across the axis (launch_build_masks)
     double pore_R = 0.0;                    // pore radius (lb_set_pore)
+    double *dwchan = nullptr;               // channel walls: Geom::wchan
     lbk::WallBeads wall{};                  // pore-wall beads (lb_set_pore_beads)
     int cs_variant = 0;                     // collide kernel: 0 auto (plain), 1 plain, 2 TMA-staged
     int tma_stages = 0, tma_ctas = 0;       // 0 = library default

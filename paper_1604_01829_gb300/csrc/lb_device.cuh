@@ -65,6 +65,9 @@ struct Geom {
     int pore_axis;      // -1: periodic box without walls
     long long pore_t;   // wall iff (2a+1-na)^2 + (2b+1-nb)^2 >= pore_t (a, b: coordinates across the axis)
     long long pore_in;  // below this the node and all its neighbours are fluid
+    int chan;           // 1: moving walls at y = -1/2 and y = ny - 1/2, the box not periodic in y
+    const double *wchan;  // device, chan: [2][19] bounce-back terms 6 w_i rho0 (c_i . u_wall) of the
+                          // lower and upper wall, then [2][3] the wall velocities
 };
 
 __device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -87,15 +90,23 @@ __device__ __forceinline__ bool is_wall(const Geom &g, int x, int y, int z) {
     return g.pore_axis >= 0 && pore_r2(g, x, y, z) >= g.pore_t;
 }
 
+// Bounce-back term of a population of link i returning from the moving wall
+// on `side` (0 lower, 1 upper): f_i = f*_opp(i) + 6 w_i rho0 (c_i . u_wall).
+__device__ __forceinline__ double chan_term(const Geom &g, int side, int i) { return g.wchan[19 * side + i]; }
+
 // Pre-collision population i of node (x,y,z) under the AA pattern.
 // Even step count: stored in place, A[i][n]. Odd step count: the neighbour
 // upstream holds it in the opposite slot, A[opp i][n - c_i]; if that
-// neighbour is a wall node the population bounced back into A[i][n].
+// neighbour is a wall node the population bounced back into A[i][n] (plus
+// the moving-wall term when the wall is a channel wall).
 template <typename T>
 __device__ __forceinline__ T load_pre(const T *A, const Geom &g, int x, int y, int z, long long n,
                                       int i, bool odd) {
     if (!odd || i == 0) return A[(long long)i * g.N + n];
-    const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(y - cy(i), g.ny), zs = wrapm(z - cz(i), g.nz);
+    const int yr = y - cy(i);
+    if (g.chan && (yr < 0 || yr >= g.ny))
+        return (T)((double)A[(long long)i * g.N + n] + chan_term(g, yr < 0 ? 0 : 1, i));
+    const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(yr, g.ny), zs = wrapm(z - cz(i), g.nz);
     if (is_wall(g, xs, ys, zs)) return A[(long long)i * g.N + n];
     return A[(long long)opp(i) * g.N + nidx(g, xs, ys, zs)];
 }
@@ -105,7 +116,12 @@ template <typename T>
 __device__ __forceinline__ void store_pre(T *A, const Geom &g, int x, int y, int z, long long n,
                                           int i, bool odd, T v) {
     if (!odd || i == 0) { A[(long long)i * g.N + n] = v; return; }
-    const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(y - cy(i), g.ny), zs = wrapm(z - cz(i), g.nz);
+    const int yr = y - cy(i);
+    if (g.chan && (yr < 0 || yr >= g.ny)) {
+        A[(long long)i * g.N + n] = (T)((double)v - chan_term(g, yr < 0 ? 0 : 1, i));
+        return;
+    }
+    const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(yr, g.ny), zs = wrapm(z - cz(i), g.nz);
     if (is_wall(g, xs, ys, zs)) { A[(long long)i * g.N + n] = v; return; }
     A[(long long)opp(i) * g.N + nidx(g, xs, ys, zs)] = v;
 }

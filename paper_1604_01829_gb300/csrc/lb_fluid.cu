@@ -45,6 +45,15 @@ __constant__ signed char kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1
 __global__ void k_build_masks(Geom g, uint32_t *out, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    if (g.chan) {                        // channel walls: the mask depends on y only
+        uint32_t m = 0;
+        for (int i = 1; i < 19; ++i) {
+            const int ys = t - kC[i][1];
+            if (ys < 0 || ys >= g.ny) m |= 1u << i;
+        }
+        out[t] = m;
+        return;
+    }
     int x = 0, y = 0, z = 0;
     if (g.pore_axis == 2) { x = t % g.nx; y = t / g.nx; }
     else if (g.pore_axis == 1) { x = t % g.nx; z = t / g.nx; }
@@ -62,6 +71,7 @@ __global__ void k_build_masks(Geom g, uint32_t *out, int n) {
 }
 
 __device__ __forceinline__ uint32_t pore_section_index(const Geom &g, int x, int y, int z) {
+    if (g.chan) return (uint32_t)y;
     return g.pore_axis == 2 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)y
          : (g.pore_axis == 1 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)z : (uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
 }
@@ -105,7 +115,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
         for (int i = 1; i < 19; ++i) {
             const unsigned src = (unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]);
             // halfway bounce-back: the population that left towards the wall
-            f[i] = (PORE && ((wmask >> i) & 1u)) ? plane(i)[n] : plane(opp(i))[src];
+            // (plus the moving-wall term of a channel wall upstream)
+            if (PORE && ((wmask >> i) & 1u))
+                f[i] = g.chan ? (R)((double)plane(i)[n] + chan_term(g, cy(i) > 0 ? 0 : 1, i)) : (R)plane(i)[n];
+            else
+                f[i] = plane(opp(i))[src];
         }
     }
 
@@ -137,7 +151,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
         for (int i = 1; i < 19; ++i) {
             const unsigned dst = (unsigned)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
             // downstream node x + c_i is the upstream node of link opp(i)
-            if (PORE && ((wmask >> opp(i)) & 1u)) plane(opp(i))[n] = f[i];
+            if (PORE && ((wmask >> opp(i)) & 1u))
+                plane(opp(i))[n] = g.chan ? (T)((double)f[i] - chan_term(g, cy(i) < 0 ? 0 : 1, i)) : (T)f[i];
             else plane(i)[dst] = f[i];
         }
     }
@@ -146,7 +161,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
 template <typename T, int COLL, bool NOISE>
 cudaError_t launch_cs_t(const FluidArgs &a, bool odd, dim3 block, cudaStream_t s) {
     const dim3 grid((a.g.nx + block.x - 1) / block.x, (a.g.ny + block.y - 1) / block.y, a.g.nz);
-    const bool pore = a.g.pore_axis >= 0;
+    const bool pore = a.g.pore_axis >= 0 || a.g.chan;       // bounded: per-position wall masks
     if (odd) {
         if (pore) k_collide_stream<T, COLL, NOISE, true, true><<<grid, block, 0, s>>>(a);
         else k_collide_stream<T, COLL, NOISE, true, false><<<grid, block, 0, s>>>(a);
@@ -329,6 +344,7 @@ bool make_wall_beads(const Geom &g, double pore_R, double spacing, double r_pore
 }
 
 long long pore_section_size(const Geom &g) {
+    if (g.chan) return g.ny;
     return g.pore_axis == 2 ? (long long)g.nx * g.ny
          : (g.pore_axis == 1 ? (long long)g.nx * g.nz : (long long)g.ny * g.nz);
 }

@@ -51,6 +51,7 @@ _SIGS = {
     "lb_destroy": [C.c_void_p],
     "lb_set_pore": [C.c_void_p, C.c_double, C.c_int],
     "lb_set_pore_beads": [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double],
+    "lb_set_channel_walls": [C.c_void_p, _dp, _dp],
     "lb_add_raspberry": [C.c_void_p, _dp, C.c_int, _dp, _dp, C.c_double, _dp, _dp, _dp, C.c_int, _ip],
     "lb_set_body_state": [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp],
     "lb_set_external_forces": [C.c_void_p, C.c_int, _dp, _dp],
@@ -263,6 +264,9 @@ class LB:
     # set-up --------------------------------------------------------------
     def lb_set_pore(self, radius, axis=2):
         _check(self.h, load().lb_set_pore(self.h, float(radius), int(axis)))
+
+    def lb_set_channel_walls(self, u_lo, u_hi):
+        _check(self.h, load().lb_set_channel_walls(self.h, _d(_vec(u_lo, 3)), _d(_vec(u_hi, 3))))
 
     def lb_set_pore_beads(self, spacing, r_pore_bead, r_bead, epsilon):
         _check(self.h, load().lb_set_pore_beads(self.h, float(spacing), float(r_pore_bead), float(r_bead),

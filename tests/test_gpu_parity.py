@@ -251,6 +251,44 @@ def test_step_pairs_replayed_from_a_graph(precision):
     assert np.array_equal(X[-1], P.gpu.lb_get_body(0)["X"])
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nsteps", [(1, 2, 3), (5, 4)])
+def test_channel_walls_match_oracle(precision, nsteps):
+    """Moving walls at y = -1/2 and ny - 1/2 (the Stokes-flow set-up) with
+    different tangential velocities, thermal MRT fluid, a free sphere whose
+    beads reach beyond the lower wall plane's first node row; eager steps
+    and graph-replayed step pairs."""
+    params = dict(MRT, kT=1e-4, seed=19, gamma_bead=Wl.paper_gamma_to_lattice(50.0))
+    P = Pair(14, 12, 10, precision=precision, **params)
+    ulo, uhi = (1e-3, 0.0, -5e-4), (-2e-3, 0.0, 1e-3)
+    P.gpu.lb_set_channel_walls(ulo, uhi)
+    P.orc.set_channel_walls(ulo, uhi)
+    P.set_populations(perturbed_populations(P.N, seed=9))
+    P.add_body(Wl.sphere_raspberry(2.0), [6.3, 2.4, 4.8], mass=34.0, inertia=(50, 50, 50), F_ext=(0, -1e-3, 0))
+    tb = 1e-11 if precision == 64 else 5e-5
+    for n in nsteps:
+        P.step(n)
+        assert P.pop_error() <= TOL[precision]
+        e = P.body_errors(0)
+        assert e["bead"] <= tb and e["F"] <= tb and e["X"] <= tb, (n, e)
+    m, _ = P.gpu.lb_conservation()
+    mo, _ = P.orc.conservation()
+    assert abs(m - mo) <= (1e-12 if precision == 64 else 1e-8) * mo
+
+
+def test_channel_walls_exclude_a_pore():
+    from paper_1604_01829_gb300 import lb
+    g = lb.LB(8, 8, 8)
+    g.lb_set_pore(3.0, 2)
+    with pytest.raises(lb.LBError) as ei:
+        g.lb_set_channel_walls((0, 0, 1e-3), (0, 0, 1e-3))
+    assert ei.value.status == lb.LB_ERR_STATE
+    h = lb.LB(8, 8, 8)
+    with pytest.raises(lb.LBError) as ei:
+        h.lb_set_channel_walls((0, 1e-3, 0), (0, 0, 0))
+    assert ei.value.status == lb.LB_ERR_ARG
+
+
 def test_kernel_variant_rejects_unsupported_shapes():
     from paper_1604_01829_gb300 import lb
     g = lb.LB(37, 8, 8, precision=32)
