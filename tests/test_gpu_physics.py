@@ -10,7 +10,11 @@ ABI against closed forms of Stokes flow:
   Bohlin (1960) / Haberman & Sayre (1958), K(lambda) = 1 / (1 - 2.10444
   lambda + 2.08877 lambda^3 - 0.94813 lambda^5 - 1.372 lambda^6 + 3.87
   lambda^8 - 4.19 lambda^10), whose leading term is the 1 + 2.104 lambda of
-  the Faxen-type expansion.
+  the Faxen-type expansion;
+* the Stokes-flow resistance set-up (Sec. 2.3, Eq. (stokesflow)): a fixed
+  raspberry between moving walls gives, extrapolated in the box size, the
+  same unbounded drag as a pulled raspberry in a periodic box extrapolated
+  by Hasimoto's law.
 
 All runs: BGK tau = 1 (nu = 1/6), FP64, deterministic fluid (kT = 0)."""
 import math
@@ -161,3 +165,31 @@ def test_centreline_pore_drag_matches_bohlin():
     K = xi_pore / xi0
     assert abs(K / _bohlin(lam) - 1) < 0.02, (K, lam, _bohlin(lam))
     assert K > 1 + 2.104 * lam                               # beyond the leading term
+
+
+def test_stokes_flow_set_up_gives_the_unbounded_drag():
+    """Eq. (stokesflow): a fixed sphere raspberry (R = 2) at the centre of a
+    cubic box whose +y and -y walls move at U along z; the steady summed bead
+    force is xi_S(L) U. Fitting xi_S(L) = xi_0 (1 - c / L) over L = 32, 48, 64
+    gives xi_0 within 1 % of the pulled-body value extrapolated with
+    Hasimoto's law (measured: 0.1 %); xi_S grows with L toward it."""
+    from paper_1604_01829_gb300 import lb
+    beads = Wl.sphere_raspberry(2.0)
+    U = 1e-3
+    Ls = [32, 48, 64]
+    xs = []
+    for L in Ls:
+        h = lb.LB(L, L, L, precision=64, collision=0, tau=1.0, gamma_bead=0.3)
+        h.lb_set_channel_walls((0, 0, U), (0, 0, U))
+        h.lb_add_raspberry(beads, [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], fixed=1)
+        T = int(12 * L * L / (ETA * math.pi ** 2))        # 12 e-folds of the slowest channel mode
+        h.lb_step(T)
+        F, _ = h.lb_forces(0)
+        h.close()
+        xs.append(F[2] / U)
+    assert np.all(np.diff(xs) > 0)
+    A = np.stack([np.ones(3), -1.0 / np.asarray(Ls, float)], axis=1)
+    xi0_stokes = np.linalg.lstsq(A, np.asarray(xs), rcond=None)[0][0]
+    mass = 4.0 / 3.0 * math.pi * 8.0
+    xi0_pulled = _unbounded([_pulled_drag(L, beads, mass, 0) for L in Ls], Ls)
+    assert abs(xi0_stokes / xi0_pulled - 1) < 0.01, (xs, xi0_stokes, xi0_pulled)
