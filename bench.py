@@ -79,13 +79,17 @@ def copy_ceiling(torch, stream, nbytes=2 << 30, reps=10):
 
 
 def kernel_source_hash():
-    """Hash of what the collide-and-stream kernels are compiled from: their
-    source files and the parameter structs (CollParams, FluidArgs) of the
-    shared header, so that unrelated edits keep committed counters valid."""
+    """Hash of what the collide-and-stream kernels are compiled from: the
+    collision and device headers, the fluid-kernel part of lb_fluid.cu and
+    the parameter structs (CollParams, FluidArgs) of the shared header, so
+    that unrelated edits keep committed counters valid."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1604_01829_gb300", "csrc")
-    for f in ("lb_fluid.cu", "lb_collide.cuh", "lb_device.cuh"):
+    for f in ("lb_collide.cuh", "lb_device.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
+    # the fluid-kernel part of lb_fluid.cu (pore wall masks, collide and stream)
+    src = open(os.path.join(csrc, "lb_fluid.cu"), "rb").read()
+    h.update(src[:src.index(b"// ------------------------------------------------------------ population I/O")])
     hdr = open(os.path.join(csrc, "lb_internal.h"), "rb").read()
     start = hdr.index(b"struct CollParams")
     end = hdr.index(b"};", hdr.index(b"struct FluidArgs")) + 2

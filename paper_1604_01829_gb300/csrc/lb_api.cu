@@ -337,6 +337,14 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
         if (e != cudaSuccess) { lb_status s = cuda_fail(nullptr, e, "cudaStreamCreate"); delete h; return s; }
         h->own_stream = true;
     }
+    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lb_status s = cuda_fail(nullptr, e, "side stream");
+        lb_destroy(h);
+        return s;
+    }
     const size_t es = h->fp32 ? 4 : 8;
     lb_status s;
     if ((s = dev_alloc(h, &h->f, es * 19 * (size_t)h->g.N)) != LB_OK ||
@@ -378,6 +386,10 @@ lb_status lb_destroy(lb_handle h) {
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->side) cudaStreamSynchronize(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return LB_OK;
@@ -544,63 +556,98 @@ lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, 
 
 namespace {
 
-// Launches step h->step + k (k-th of a group; the step counter on the device
-// is advanced once per group, so kernels read *step_dev + k): the previous
-// step's second half kick if finish_prev, this step's kick and drift with the
-// clearing of its spread-force tiles, the coupling, the fluid kernel.
-lb_status launch_one_step(lb_ctx *h, int k, bool finish_prev) {
+// The body prologue of step h->step + k (k-th of a group; the device step
+// counter is advanced once per group, so kernels read *step_dev + k): the
+// previous step's second half kick if finish_prev, this step's kick and
+// drift, the clearing of its spread-force tiles. On stream `st`.
+lb_status launch_step_prologue(lb_ctx *h, int k, bool finish_prev, cudaStream_t st) {
     const int nb = (int)h->hb.size();
+    const bool coupled = nb > 0 && !h->hbody_of.empty();
+    const int cur = (int)((h->step + k) & 1);
+    const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
+    cudaError_t e = lbk::launch_step_pre(h->db, nb, finish_prev, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
+                                         coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
+                                         h->list_cap, h->g, h->ntx, h->nty, rec, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
+    // the list of this buffer restarts empty for this step's coupling
+    if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), st));
+    return LB_OK;
+}
+
+// The coupling of step h->step + k on the main stream.
+lb_status launch_step_coupling(lb_ctx *h, int k) {
     const int nbeads = (int)h->hbody_of.size();
-    const bool coupled = nb > 0 && nbeads > 0;
     const long long t = h->step + k;
     const bool odd = (t & 1) != 0;
     const int cur = (int)(t & 1), prev = cur ^ 1;
-    if (nb > 0) {
-        const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
-        cudaError_t e = lbk::launch_step_pre(h->db, nb, finish_prev, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
-                                             coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
-                                             h->list_cap, h->g, h->ntx, h->nty, rec, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
-        // the list of this buffer restarts empty for this step's coupling
-        if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
+    lbk::CoupleArgs c{};
+    c.g = h->g;
+    c.f = h->f;
+    c.fp32 = h->fp32;
+    c.odd = odd;
+    c.rho0 = h->p.rho0;
+    c.gamma = h->p.gamma_bead;
+    c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
+    c.gforce = h->gforce;
+    c.gforce_f = h->gforce_f;
+    c.Fprev = h->Fbuf[prev];
+    c.Fcur = h->Fbuf[cur];
+    c.tiles_cur = h->tiles[cur];
+    c.tlist = h->tlist[cur];
+    c.tcount = h->tcount[cur];
+    c.ntx = h->ntx;
+    c.nty = h->nty;
+    c.s = h->ds;
+    c.sf = h->dsf;
+    c.gamma_f = (float)c.gamma;
+    c.noise_amp_f = (float)c.noise_amp;
+    c.bead_body = h->dbody_of;
+    c.bodies = h->db;
+    c.F_bead = h->dFbead;
+    c.nbeads = nbeads;
+    c.key0 = (uint32_t)h->p.seed;
+    c.key1 = (uint32_t)(h->p.seed >> 32);
+    c.instance = h->p.instance;
+    c.step_base = h->step_dev;
+    c.step_off = (uint32_t)k;
+    cudaError_t e = lbk::launch_couple(c, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
+    e = lbk::launch_wall_beads(h->wall, h->db, h->ds, h->dbody_of, nbeads, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "wall beads launch");
+    return LB_OK;
+}
+
+// Launches n steps starting at step h->step (without finishing the group).
+// With bodies, the prologue of step k runs on the side stream beside the
+// fluid kernel of step k-1: it needs the coupling of k-1 (body sums, and it
+// clears the force buffer that coupling read as the previous step's) but
+// touches nothing that fluid kernel reads (the other force buffer); the
+// coupling of step k waits for it.
+lb_status launch_steps(lb_ctx *h, int n) {
+    const bool bodies = !h->hb.empty();
+    if (bodies) {
+        LB_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+        LB_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     }
-    if (coupled) {
-        lbk::CoupleArgs c{};
-        c.g = h->g;
-        c.f = h->f;
-        c.fp32 = h->fp32;
-        c.odd = odd;
-        c.rho0 = h->p.rho0;
-        c.gamma = h->p.gamma_bead;
-        c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
-        c.gforce = h->gforce;
-        c.gforce_f = h->gforce_f;
-        c.Fprev = h->Fbuf[prev];
-        c.Fcur = h->Fbuf[cur];
-        c.tiles_cur = h->tiles[cur];
-        c.tlist = h->tlist[cur];
-        c.tcount = h->tcount[cur];
-        c.ntx = h->ntx;
-        c.nty = h->nty;
-        c.s = h->ds;
-        c.sf = h->dsf;
-        c.gamma_f = (float)c.gamma;
-        c.noise_amp_f = (float)c.noise_amp;
-        c.bead_body = h->dbody_of;
-        c.bodies = h->db;
-        c.F_bead = h->dFbead;
-        c.nbeads = nbeads;
-        c.key0 = (uint32_t)h->p.seed;
-        c.key1 = (uint32_t)(h->p.seed >> 32);
-        c.instance = h->p.instance;
-        c.step_base = h->step_dev;
-        c.step_off = (uint32_t)k;
-        cudaError_t e = lbk::launch_couple(c, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
-        e = lbk::launch_wall_beads(h->wall, h->db, h->ds, h->dbody_of, nbeads, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "wall beads launch");
+    for (int k = 0; k < n; ++k) {
+        const long long t = h->step + k;
+        const int cur = (int)(t & 1);
+        lb_status s;
+        if (bodies) {
+            if ((s = launch_step_prologue(h, k, k > 0, h->side)) != LB_OK) return s;
+            LB_CUDA(h, cudaEventRecord(h->ev_join, h->side));
+            LB_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            if (!h->hbody_of.empty()) {
+                if ((s = launch_step_coupling(h, k)) != LB_OK) return s;
+            }
+            if (k + 1 < n) {                  // the next prologue may start now
+                LB_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+                LB_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            }
+        }
+        if ((s = timed_collide(h, fluid_args(h, cur, (uint32_t)k), (t & 1) != 0)) != LB_OK) return s;
     }
-    return timed_collide(h, fluid_args(h, cur, (uint32_t)k), odd);
+    return LB_OK;
 }
 
 // end of a group of n steps: the last step's second half kick, counter advance
@@ -615,11 +662,9 @@ lb_status finish_group(lb_ctx *h, int n) {
 }
 
 lb_status eager_steps(lb_ctx *h, int n) {
-    for (int k = 0; k < n; ++k) {
-        lb_status s = launch_one_step(h, k, k > 0);
-        if (s != LB_OK) return s;
-    }
-    lb_status s = finish_group(h, n);
+    lb_status s = launch_steps(h, n);
+    if (s != LB_OK) return s;
+    s = finish_group(h, n);
     h->step += n;
     return s;
 }
@@ -629,8 +674,7 @@ lb_status ensure_graph(lb_ctx *h) {
     if (h->gexec) return LB_OK;
     cudaGraph_t graph = nullptr;
     LB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    lb_status s = launch_one_step(h, 0, false);
-    if (s == LB_OK) s = launch_one_step(h, 1, true);
+    lb_status s = launch_steps(h, 2);
     if (s == LB_OK) s = finish_group(h, 2);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (s != LB_OK) {

@@ -15,6 +15,8 @@ struct lb_ctx {
     lbk::Geom g{};
     bool fp32 = false;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;            // body prologue of step t beside the fluid kernel of t-1
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool own_stream = false;
     void *f = nullptr;
     double *gforce = nullptr;               // device (3)

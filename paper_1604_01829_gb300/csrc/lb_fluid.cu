@@ -269,6 +269,47 @@ __global__ void __launch_bounds__(256) k_moments(const T *f, Geom g, bool odd, d
         for (int c = 0; c < 4; ++c) partials[4LL * blockIdx.x + c] = red[c][0];
 }
 
+// FP32 deviations in a periodic box: every population sits in exactly one
+// slot of one node, in slot i on an even step count and in slot opp(i) of
+// the upstream node on an odd one, so mass and momentum are plane sums:
+// M = sum over all slots, P = +/- sum_i c_i (sum of plane i). One coalesced
+// pass; each thread sums four nodes' 19 values in FP32 (deviations of
+// O(1e-2): rounding ~1e-9 per partial) and accumulates the partials in FP64.
+__global__ void __launch_bounds__(256) k_moments_periodic_f32(const float *f, long long N, bool odd,
+                                                            double *partials) {
+    double s[4] = {0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    while (n < N) {
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 4 && n < N; ++k, n += stride) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                const float v = __ldcs(f + (long long)i * N + n);
+                p[0] += v;
+                if (cx(i)) p[1] += cx(i) * v;
+                if (cy(i)) p[2] += cy(i) * v;
+                if (cz(i)) p[3] += cz(i) * v;
+            }
+        }
+        s[0] += (double)p[0];
+        for (int c = 1; c < 4; ++c) s[c] += odd ? -(double)p[c] : (double)p[c];
+    }
+    __shared__ double red[4][256];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) partials[4LL * blockIdx.x + c] = red[c][0];
+}
+
 __global__ void __launch_bounds__(256) k_moments_final(const double *partials, int nblocks, double *out) {
     __shared__ double red[4][256];
     double s[4] = {0, 0, 0, 0};
@@ -379,7 +420,9 @@ cudaError_t launch_sample(const void *f, bool fp32, const Geom &g, bool odd, dou
 
 cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, double *partials,
                            int nblocks, double *out4, cudaStream_t s) {
-    if (fp32) k_moments<float><<<nblocks, 256, 0, s>>>((const float *)f, g, odd, partials);
+    if (fp32 && g.pore_axis < 0 && !g.chan)
+        k_moments_periodic_f32<<<nblocks, 256, 0, s>>>((const float *)f, g.N, odd, partials);
+    else if (fp32) k_moments<float><<<nblocks, 256, 0, s>>>((const float *)f, g, odd, partials);
     else k_moments<double><<<nblocks, 256, 0, s>>>((const double *)f, g, odd, partials);
     k_moments_final<<<1, 256, 0, s>>>(partials, nblocks, out4);
     return cudaGetLastError();

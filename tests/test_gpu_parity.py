@@ -122,6 +122,22 @@ def test_conservation_matches_oracle_and_is_exact():
     assert np.abs(p1 - p0).max() <= 1e-13 * m0
 
 
+@pytest.mark.parametrize("steps", [0, 3, 4])
+def test_fp32_periodic_conservation_matches_oracle(steps):
+    """FP32 deviations in a periodic box take the one-pass plane-sum
+    reduction (mass and momentum from the slots, the momentum sign flipped
+    on odd step counts): equal to the oracle's FP64 sums within the FP32
+    storage rounding, on even and odd step counts."""
+    params = dict(MRT, kT=1e-4, seed=15)
+    P = Pair(20, 18, 16, precision=32, **params)
+    P.set_populations(perturbed_populations(P.N, seed=3))
+    P.step(steps)
+    m, p = P.gpu.lb_conservation()
+    mo, po = P.orc.conservation()
+    assert abs(m - mo) <= 1e-9 * mo
+    assert np.abs(p - po).max() <= 2e-5 * np.sqrt(P.N) * 1e-2
+
+
 def test_sample_populations_matches_full_readback():
     P = Pair(17, 9, 6, precision=32, **MRT)
     P.set_populations(perturbed_populations(P.N, seed=2))
