@@ -26,7 +26,8 @@
  *   u = (j + F/2)/rho; orthogonal moment basis (Dunweg-Schiller-Ladd
  *   polynomials), m* = m_eq + g_k (m - m_eq) + (1+g_k)/2 S_k; fluctuating
  *   modes with amplitude sqrt(3 rho kT b_k (1-g_k^2)); Philox4x32-10
- *   uniform variates of unit variance; trilinear interpolation between the
+ *   uniform variates of unit variance (16-bit for the fluid modes, 32-bit
+ *   for the beads); trilinear interpolation between the
  *   8 nodes surrounding a bead and the transposed spread of -F; node centres
  *   at integer+1/2; a node is a wall node when its centre lies at distance
  *   >= R from the pore axis.
@@ -174,6 +175,13 @@ static double unit_uniform(uint32_t x)
     return sqrt(12.0) * (u - 0.5);
 }
 
+/* The same from 16 random bits (the fluid noise): u = (h + 1/2) 2^-16. */
+static double unit_uniform16(uint32_t h)
+{
+    double u = ((double)h + 0.5) * (1.0 / 65536.0);
+    return sqrt(12.0) * (u - 0.5);
+}
+
 /* ------------------------------------------------------------- parameters */
 
 typedef struct {
@@ -296,17 +304,22 @@ static void collide_node(const orc_params *p, const double f[NQ], const double F
     if (p->kT > 0.0) {
         /* Fluctuating modes: the 15 non-conserved moments get noise of
          * variance mu b_k (1 - g_k^2), mu = 3 rho kT, so that their
-         * stationary variance is mu b_k. */
+         * stationary variance is mu b_k. The variates are 16-bit: two
+         * Philox calls give 8 words = 16 half-words; mode k takes half-word
+         * j = k - 4, the high half of word j/2 for even j, the low half for
+         * odd j. */
         uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
-        uint32_t r[16];
-        for (int call = 0; call < 4; ++call) {
+        uint32_t r[8];
+        for (int call = 0; call < 2; ++call) {
             uint32_t ctr[4] = {node_id, step, p->instance, (uint32_t)call};
             philox4x32_10(ctr, key, &r[4 * call]);
         }
         double mu = 3.0 * rho * p->kT;
         for (int k = 4; k < NQ; ++k) {
             double g = mode_rate(p, k);
-            ms[k] += sqrt(mu * BK[k] * (1.0 - g * g)) * unit_uniform(r[k - 4]);
+            int j = k - 4;
+            uint32_t h = (j % 2 == 0) ? (r[j / 2] >> 16) : (r[j / 2] & 0xFFFFu);
+            ms[k] += sqrt(mu * BK[k] * (1.0 - g * g)) * unit_uniform16(h);
         }
     }
     for (int i = 0; i < NQ; ++i) {
@@ -486,6 +499,7 @@ void orc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
 }
 
 double orc_unit_uniform(uint32_t x) { return unit_uniform(x); }
+double orc_unit_uniform16(uint32_t h) { return unit_uniform16(h & 0xFFFFu); }
 
 void orc_equilibrium(double rho, const double *u, double *feq)
 {

@@ -82,6 +82,8 @@ def lib():
             L.orc_philox.argtypes = [C.POINTER(C.c_uint32)] * 3
             L.orc_unit_uniform.argtypes = [C.c_uint32]
             L.orc_unit_uniform.restype = C.c_double
+            L.orc_unit_uniform16.argtypes = [C.c_uint32]
+            L.orc_unit_uniform16.restype = C.c_double
             L.orc_equilibrium.argtypes = [C.c_double, _dp, _dp]
             L.orc_collide_node.argtypes = [C.POINTER(Params), _dp, _dp, C.c_uint32, C.c_uint32, _dp]
             L.orc_rotation.argtypes = [_dp, _dp]
@@ -131,6 +133,10 @@ def philox(ctr, key):
 
 def unit_uniform(x):
     return lib().orc_unit_uniform(int(x) & 0xFFFFFFFF)
+
+
+def unit_uniform16(h):
+    return lib().orc_unit_uniform16(int(h) & 0xFFFF)
 
 
 def equilibrium(rho, u):

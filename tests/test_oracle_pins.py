@@ -188,6 +188,26 @@ def test_unit_uniform_variates():
     assert abs(np.corrcoef(a[:, 0], a[:, 1])[0, 1]) < 0.03
 
 
+def test_unit_uniform16_variates_exact_moments():
+    """Fluid-noise variates from 16 bits: over all 65536 values the mean is 0
+    and the variance 1 - 2^-32 exactly (discrete uniform on a centred grid),
+    the extremes are mirror images, and the two halves of one Philox word
+    are uncorrelated."""
+    assert abs(O.unit_uniform16(0) - math.sqrt(12) * (0.5 / 65536 - 0.5)) < 1e-15
+    assert abs(O.unit_uniform16(65535) + O.unit_uniform16(0)) < 1e-15
+    v = np.array([O.unit_uniform16(h) for h in range(65536)])
+    assert abs(v.sum()) < 1e-9
+    assert abs((v * v).mean() - (1.0 - 2.0 ** -32)) < 1e-12
+    assert np.all(np.diff(v) > 0)
+    words = []
+    for i in range(20000):
+        words.extend(O.philox([i, 5, 0, 1], [3, 8]))
+    hi = np.array([O.unit_uniform16(w >> 16) for w in words])
+    lo = np.array([O.unit_uniform16(w & 0xFFFF) for w in words])
+    assert abs(np.corrcoef(hi, lo)[0, 1]) < 0.02
+    assert abs(hi.var() - 1.0) < 0.02 and abs(lo.var() - 1.0) < 0.02
+
+
 # ------------------------------------------------------------ fluid dynamics pins
 
 def _shear_wave_rate(nu_expected, **kw):
