@@ -105,23 +105,30 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Coll
 
     if (NOISE) {
         // 15 non-conserved modes, variance 3 rho kT b_k (1 - g_k^2); kn_k holds
-        // c_k sqrt(3 kT b_k (1 - g_k^2)) (times sqrt(12) 2^-32 in FP32, where
-        // the variate is the centred integer converted once)
+        // c_k sqrt(3 kT b_k (1 - g_k^2)) (times sqrt(12) 2^-32 in FP32). The
+        // variates are 16-bit: two Philox calls give 16 half-words, mode 4 + j
+        // takes half-word j (high half of word j/2 for even j, else the low
+        // half), xi = sqrt(12) ((h + 1/2) 2^-16 - 1/2). In FP32 the half-word
+        // and a 1/2 below it become the mantissa of y = 1 + (h + 1/2) 2^-16 in
+        // [1, 2), and (y - 3/2) 2^32 = xi 2^32 / sqrt(12) is exact in one FMA
+        // (no integer-to-float conversion).
         const uint4 r0 = philox4x32_10(make_uint4(node, step, instance, 0u), key);
         const uint4 r1 = philox4x32_10(make_uint4(node, step, instance, 1u), key);
-        const uint4 r2 = philox4x32_10(make_uint4(node, step, instance, 2u), key);
-        const uint4 r3 = philox4x32_10(make_uint4(node, step, instance, 3u), key);
         R sr;
         if constexpr (sizeof(R) == 4) asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sr) : "f"(rho));
         else sr = sqrt(rho);
-        auto add = [&](R &q, int k, uint32_t v) {
-            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * unit_uniform_d(v);
-            else q += (sr * a.kn[k]) * (float)(int32_t)(v ^ 0x80000000u);
+        auto hi = [&](R &q, int k, uint32_t v) {
+            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * unit_uniform16_d(v >> 16);
+            else q = fmaf(sr * a.kn[k], fmaf(__uint_as_float(((v >> 9) & 0x7FFF80u) | 0x3F800040u), 0x1p32f, -0x1.8p32f), q);
         };
-        add(q4, 0, r0.x); add(q5, 1, r0.y); add(q6, 2, r0.z); add(q7, 3, r0.w);
-        add(q8, 4, r1.x); add(q9, 5, r1.y); add(q10, 6, r1.z); add(q11, 7, r1.w);
-        add(q12, 8, r2.x); add(q13, 9, r2.y); add(q14, 10, r2.z); add(q15, 11, r2.w);
-        add(q16, 12, r3.x); add(q17, 13, r3.y); add(q18, 14, r3.z);
+        auto lo = [&](R &q, int k, uint32_t v) {
+            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * unit_uniform16_d(v & 0xFFFFu);
+            else q = fmaf(sr * a.kn[k], fmaf(__uint_as_float(((v << 7) & 0x7FFF80u) | 0x3F800040u), 0x1p32f, -0x1.8p32f), q);
+        };
+        hi(q4, 0, r0.x); lo(q5, 1, r0.x); hi(q6, 2, r0.y); lo(q7, 3, r0.y);
+        hi(q8, 4, r0.z); lo(q9, 5, r0.z); hi(q10, 6, r0.w); lo(q11, 7, r0.w);
+        hi(q12, 8, r1.x); lo(q13, 9, r1.x); hi(q14, 10, r1.y); lo(q15, 11, r1.y);
+        hi(q16, 12, r1.z); lo(q17, 13, r1.z); hi(q18, 14, r1.w);
     }
 
     // back to populations: f*_i = w_i sum_k e_k(c_i) m*_k / b_k; with the

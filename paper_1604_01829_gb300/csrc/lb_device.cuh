@@ -53,6 +53,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __device__ __forceinline__ double unit_uniform_d(uint32_t x) {
     return 3.4641016151377544 * (((double)x + 0.5) * 2.3283064365386963e-10 - 0.5);
 }
+// The same from 16 random bits: sqrt(12) ((h + 1/2) 2^-16 - 1/2).
+__device__ __forceinline__ double unit_uniform16_d(uint32_t h) {
+    return 3.4641016151377544 * (((double)h + 0.5) * 1.52587890625e-05 - 0.5);
+}
 __device__ __forceinline__ float unit_uniform_f(uint32_t x) {
     // (x - 2^31 + 1/2) 2^-32 with one integer-to-float conversion
     return 3.4641016151377544f * (((float)(int32_t)(x ^ 0x80000000u) + 0.5f) * 2.3283064365386963e-10f);

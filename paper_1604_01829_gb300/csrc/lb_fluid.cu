@@ -24,9 +24,16 @@
 #include "lb_collide.cuh"
 
 // Minimum resident blocks of 128 threads per SM requested for the FP32
-// collide kernels (caps their registers; FP64 kernels are not capped).
+// collide kernels (caps their registers; FP64 kernels are not capped):
+// 8 blocks (64 registers) without noise, 7 (72 registers) with it, where the
+// Philox state needs the room (measured on GB300 at 256^3 with noise: 0.439 ms
+// per launch at 7 blocks, 0.452 at 8, 0.458 at 6, 0.488 at 5; without noise
+// 0.415 ms at 8, 0.419 at 7).
 #ifndef LB_CS_MINB
 #define LB_CS_MINB 8
+#endif
+#ifndef LB_CS_MINB_NOISE
+#define LB_CS_MINB_NOISE 7
 #endif
 
 namespace lbk {
@@ -79,7 +86,8 @@ __device__ __forceinline__ uint32_t pore_section_index(const Geom &g, int x, int
 // ------------------------------------------------------- collide and stream
 
 template <typename T, int COLL, bool NOISE, bool ODD, bool PORE>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collide_stream(const FluidArgs a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOISE : LB_CS_MINB) : 1)
+    k_collide_stream(const FluidArgs a) {
     using R = T;
     constexpr bool DEV = sizeof(T) == 4;
     const Geom &g = a.g;
@@ -97,30 +105,49 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
         if (wmask >> 31) return;             // wall node: holds no fluid
     }
 
-    // neighbour offsets with periodic wrap: node = xo[dx] + yo[dy] + zo[dz]
-    // (32-bit; the node count is limited to 2^31 at creation)
-    const int nxy = g.nx * g.ny;
-    const int xo[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
-    const int yo[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.nx, y * g.nx, (y == g.ny - 1 ? 0 : y + 1) * g.nx};
+    // Neighbour node n + (dx, dy, dz) with periodic wrap (32-bit; the node
+    // count is limited to 2^31 at creation), from per-axis wrapped offsets.
+    // Without noise, a row whose y and z are away from the box faces (all but
+    // 4 rows in 256 at 256^3) takes a form that wraps only in x: n plus a
+    // per-link constant plus one of two x corrections, so three values stay
+    // live through the collision instead of nine (measured on GB300: 3.5 %
+    // faster without noise, slower with it, where the Philox state competes
+    // for the same registers).
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int yo[3] = {(y == 0 ? g.ny - 1 : y - 1) * nx, y * nx, (y == g.ny - 1 ? 0 : y + 1) * nx};
     const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * nxy, z * nxy, (z == g.nz - 1 ? 0 : z + 1) * nxy};
+    const bool row_in = !NOISE && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+    const int wxm = x == 0 ? nx : 0, wxp = x == nx - 1 ? -nx : 0;
+    auto nb_in = [&](int dx, int dy, int dz) -> unsigned {
+        return (unsigned)((int)n + (dx < 0 ? wxm : (dx > 0 ? wxp : 0)) + (dx + dy * nx + dz * nxy));
+    };
+    auto nb_any = [&](int dx, int dy, int dz) -> unsigned {
+        return (unsigned)(xo[1 + dx] + yo[1 + dy] + zo[1 + dz]);
+    };
     auto plane = [&](int i) { return static_cast<T *>(a.plane[i]); };
 
     R f[19];
-    if (!ODD) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = plane(i)[n];
-    } else {
+    // odd step: population i arrives from the upstream node n - c_i, where it
+    // sits in the opposite slot; halfway bounce-back takes the population that
+    // left towards a wall (plus the moving-wall term of a channel wall upstream)
+    auto load_odd = [&](auto nb) {
         f[0] = A[n];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const unsigned src = (unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]);
-            // halfway bounce-back: the population that left towards the wall
-            // (plus the moving-wall term of a channel wall upstream)
             if (PORE && ((wmask >> i) & 1u))
                 f[i] = g.chan ? (R)((double)plane(i)[n] + chan_term(g, cy(i) > 0 ? 0 : 1, i)) : (R)plane(i)[n];
             else
-                f[i] = plane(opp(i))[src];
+                f[i] = plane(opp(i))[nb(-cx(i), -cy(i), -cz(i))];
         }
+    };
+    if (!ODD) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) f[i] = plane(i)[n];
+    } else if (row_in) {
+        load_odd(nb_in);
+    } else {
+        load_odd(nb_any);
     }
 
     R Fx, Fy, Fz;
@@ -142,19 +169,24 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? LB_CS_MINB : 1) k_collid
     if constexpr (sizeof(R) == 4) collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pf, key, a.instance, (uint32_t)n, step);
     else collide<R, DEV, COLL, NOISE>(f, Fx, Fy, Fz, a.pd, key, a.instance, (uint32_t)n, step);
 
-    if (!ODD) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) plane(opp(i))[n] = f[i];
-    } else {
+    // odd step: f*_i goes to the downstream node n + c_i, the upstream node of
+    // link opp(i) there; a wall downstream returns it into the own slot
+    auto store_odd = [&](auto nb) {
         A[n] = f[0];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const unsigned dst = (unsigned)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
-            // downstream node x + c_i is the upstream node of link opp(i)
             if (PORE && ((wmask >> opp(i)) & 1u))
                 plane(opp(i))[n] = g.chan ? (T)((double)f[i] - chan_term(g, cy(i) < 0 ? 0 : 1, i)) : (T)f[i];
-            else plane(i)[dst] = f[i];
+            else plane(i)[nb(cx(i), cy(i), cz(i))] = f[i];
         }
+    };
+    if (!ODD) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) plane(opp(i))[n] = f[i];
+    } else if (row_in) {
+        store_odd(nb_in);
+    } else {
+        store_odd(nb_any);
     }
 }
 
