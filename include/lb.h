@@ -378,6 +378,48 @@ lb_status lb_msd_trajectory(const double *X, const double *q, int nrec, int nbod
 lb_status lb_pore_msd(const double *X, int nrec, int nx, int ny, int nz, int axis, double R_pore, int nbins,
                       int max_lag, double *out, long long *counts, void *cuda_stream, char *err, size_t err_len);
 
+/* Raspberry shell construction (Sec. 2.1 and the SI section "Details for
+ * ellipsoidal raspberry construction"): beads on an ellipsoid
+ * x^2/a^2 + y^2/b^2 + z^2/c^2 = 1 (body frame, centred at the origin) spread
+ * evenly by an MD-style relaxation. Each bead is pulled to its nearest surface
+ * point r_s by U = k |r - r_s|^2 (Eq. (harmonic_sphere) generalised); r_s =
+ * (x a^2/(t + a^2), y b^2/(t + b^2), z c^2/(t + c^2)) (Eq. (xtoxs)) with t the
+ * root of F(t) = sum (x a/(t + a^2))^2 - 1 (Eq. (bisection), read without the
+ * printed "+1", which contradicts Eq. (xtoxs)) found by bisection on
+ * [-m^2 + m |x_m|, a_max |r|] (m the smallest semi-axis, x_m the coordinate
+ * along it): 64 halvings in FP64, 40 in FP32. Beads of one shell repel
+ * pairwise with WCA (sigma, epsilon, cut at 2^(1/6) sigma). Damped leapfrog,
+ * unit mass, zero initial velocity: v <- (1 - eta dt) v + dt F, r <- r + dt v.
+ * After `steps` steps each bead is optionally replaced by its nearest surface
+ * point. Paper values: eta = 1000, sigma = 1.4, epsilon = 0.1, dt = 0.001,
+ * about 1e7 steps; k is not given (1000 is a reasonable choice). */
+typedef struct {
+    double k_surface;        /* harmonic restraint constant k (> 0)                  */
+    double sigma, epsilon;   /* WCA size and energy between beads of a shell (> 0)   */
+    double dt, eta;          /* time step (> 0) and damping (eta dt in [0, 2])       */
+    long long steps;         /* relaxation steps (>= 0)                              */
+    int precision;           /* 64: FP64 arithmetic; 32: FP32 arithmetic (positions
+                                are returned as doubles either way)                  */
+    int project_final;       /* 1: end with every bead on its nearest surface point  */
+} lb_shell_params;
+
+/* Relax nshells independent shells in one launch (one thread block per
+ * shell). axes: host [nshells][3] semi-axes (a, b, c > 0); counts: host
+ * [nshells] beads per shell (1 to LB_SHELL_MAX_BEADS each); xyz: host
+ * [sum counts][3], shell after shell: the initial positions on entry, the
+ * relaxed positions on return (the caller draws the initial positions, e.g.
+ * seeded random points near the surface). The stream may be NULL. Errors:
+ * LB_ERR_ARG (null pointers, nshells outside [1, 65535], counts, axes or
+ * parameters out of range), LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_UNSTABLE (a
+ * non-finite position: the step is too large for the stiffness); on error
+ * xyz is left unchanged. The message goes to err (err_len bytes, may be
+ * NULL). Allocates and frees its own device memory and synchronises the
+ * stream. Cost per step and shell: O(n^2) pair tests, n = beads of the
+ * shell. */
+#define LB_SHELL_MAX_BEADS 4096
+lb_status lb_relax_shells(int nshells, const double *axes, const int *counts, double *xyz,
+                          const lb_shell_params *params, void *cuda_stream, char *err, size_t err_len);
+
 /* Host-only: the velocity set c[19*3], weights w[19] and opposite-link table
  * opp[19] the library uses. Needs no GPU. Returns 19. */
 int lb_lattice(int *c, double *w, int *opp);

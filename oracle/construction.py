@@ -98,28 +98,48 @@ def wca_energy(r2, sigma, epsilon):
     return 4.0 * epsilon * (s6 * s6 - s6) + epsilon
 
 
+def surface_points(X, axes):
+    """surface_point for every row of X at once (the same bisection, the
+    bracket halved for all beads together)."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+    axes = np.asarray(axes, dtype=np.float64)
+    m = float(np.min(axes))
+    tied = [k for k in range(3) if axes[k] == m]
+    xm = np.max(np.abs(X[:, tied]), axis=1)
+    lo = -m * m + m * xm
+    hi = float(np.max(axes)) * np.linalg.norm(X, axis=1)
+    hi = np.maximum(hi, lo)
+    for _ in range(BISECTION_HALVINGS):
+        mid = 0.5 * (lo + hi)
+        F = np.sum((X * axes / (mid[:, None] + axes * axes)) ** 2, axis=1) - 1.0
+        pos = F > 0.0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+    t = 0.5 * (lo + hi)
+    den = t[:, None] + axes * axes
+    return np.where(den > 0.0, X * axes * axes / np.where(den > 0.0, den, 1.0), 0.0)
+
+
 def forces(X, axes, k, sigma, epsilon):
     """Total force on every bead: harmonic pull to its nearest surface point
     (-2k (r - r_s)) plus the WCA forces of all other beads of the shell."""
-    X = np.asarray(X, dtype=np.float64)
-    n = len(X)
-    F = np.zeros_like(X)
-    for i in range(n):
-        rs, _ = surface_point(X[i], axes)
-        F[i] = -2.0 * k * (X[i] - rs)
-        for j in range(n):
-            if j != i:
-                F[i] += wca_force(X[i] - X[j], sigma, epsilon)
-    return F
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+    F = -2.0 * k * (X - surface_points(X, axes))
+    d = X[:, None, :] - X[None, :, :]                 # d[i, j] = r_i - r_j
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    near = r2 < (WCA_CUT * sigma) ** 2
+    r2n = np.where(near, r2, 1.0)
+    s6 = (sigma * sigma / r2n) ** 3
+    fm = np.where(near, 24.0 * epsilon * (2.0 * s6 * s6 - s6) / r2n, 0.0)
+    return F + (fm[:, :, None] * d).sum(axis=1)
 
 
 def energy(X, axes, k, sigma, epsilon):
     """Harmonic plus pairwise WCA energy of a shell."""
-    X = np.asarray(X, dtype=np.float64)
-    U = 0.0
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+    U = k * float(((X - surface_points(X, axes)) ** 2).sum())
     for i in range(len(X)):
-        rs, _ = surface_point(X[i], axes)
-        U += k * float(np.dot(X[i] - rs, X[i] - rs))
         for j in range(i + 1, len(X)):
             d = X[i] - X[j]
             U += wca_energy(float(np.dot(d, d)), sigma, epsilon)
@@ -137,7 +157,7 @@ def relax_shell(X0, axes, steps, k=1000.0, sigma=1.4, epsilon=0.1, dt=1e-3, eta=
         V = (1.0 - eta * dt) * V + dt * F
         X = X + dt * V
     if project_final:
-        X = np.array([surface_point(x, axes)[0] for x in X])
+        X = surface_points(X, axes)
     return X
 
 

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "liblbrasp.so")
 SOURCES = ["lb_fluid.cu", "lb_fluid_tma.cu", "lb_bodies.cu", "lb_api.cu", "lb_batch.cu", "lb_adjoint.cu", "lb_static.cu",
-           "lb_traj.cu"]
+           "lb_traj.cu", "lb_shell.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,278 @@
+// Raspberry shell construction on the GPU (Ustach & Faller, arXiv:1604.01829,
+// Sec. 2.1 and the SI section "Details for ellipsoidal raspberry
+// construction").
+//
+// Beads of one shell relax on an ellipsoid x^2/a^2 + y^2/b^2 + z^2/c^2 = 1
+// under two forces: a harmonic pull -2k (r - r_s) towards the nearest surface
+// point r_s, and pairwise WCA repulsion between the beads of the shell. The
+// nearest point follows from the normal condition r - r_s = (t/2) grad S(r_s),
+// i.e. r_s = (x a^2/(t + a^2), ...) (Eq. (xtoxs)), with t the root of
+// F(t) = sum (x a/(t + a^2))^2 - 1 (Eq. (bisection) read without its printed
+// "+1", which contradicts Eq. (xtoxs)). F decreases for t > -m^2 (m the
+// smallest semi-axis); the root lies in [-m^2 + m |x_m|, a_max |r|], where the
+// term of the smallest axis alone is 1 at the lower end and F <= 0 at the
+// upper end. The paper stops its bisection at |F| < 1e-6; here the bracket is
+// halved a fixed number of times (64 in FP64, 40 in FP32), which is tighter.
+// Integration: damped leapfrog with unit mass, v <- (1 - eta dt) v + dt F,
+// r <- r + dt v.
+//
+// Design: one thread block per shell, the shell's positions and velocities in
+// shared memory (structure of arrays, 6 n values: 192 KB for 4096 beads in
+// FP64), each thread owning up to 4 beads. A step reads every position once per owned
+// bead group (shared-memory broadcast: all lanes of a warp read the same j),
+// then, after a barrier, each thread moves its beads. Shells are independent,
+// so many of them fill the GPU in one launch.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lb.h"
+
+namespace lbk {
+
+namespace {
+
+constexpr int kShellThreads = 1024;
+constexpr double kWcaCut = 1.122462048309373;      // 2^(1/6)
+
+template <typename R>
+struct ShellArgs {
+    const double *axes;       // [nshells][3]
+    const int *count;         // [nshells]
+    const long long *offset;  // [nshells] first bead of each shell
+    double *xyz;              // [total][3], in and out
+    int max_count;            // largest shell (shared-memory extent)
+    R k2;                     // 2k
+    R sig2, rc2, eps24;       // sigma^2, (2^(1/6) sigma)^2, 24 epsilon
+    R dt, damp;               // dt, 1 - eta dt
+    long long steps;
+    int project_final;
+};
+
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
+
+// Nearest surface point of (x, y, z): bisection for the root of F(t).
+template <typename R>
+__device__ __forceinline__ void surface_point(R x, R y, R z, R a, R b, R c, R &sx, R &sy, R &sz) {
+    constexpr int H = sizeof(R) == 8 ? 64 : 40;
+    const R m = fmin(a, fmin(b, c));
+    R xm = R(0);
+    if (a == m) xm = fmax(xm, fabs(x));
+    if (b == m) xm = fmax(xm, fabs(y));
+    if (c == m) xm = fmax(xm, fabs(z));
+    R lo = -m * m + m * xm;
+    R hi = fmax(a, fmax(b, c)) * sqrt(x * x + y * y + z * z);
+    if (hi < lo) hi = lo;
+    const R a2 = a * a, b2 = b * b, c2 = c * c, xa = x * a, yb = y * b, zc = z * c;
+    for (int it = 0; it < H; ++it) {
+        const R mid = R(0.5) * (lo + hi);
+        const R u = rdiv(xa, mid + a2), v = rdiv(yb, mid + b2), w = rdiv(zc, mid + c2);
+        if (u * u + v * v + w * w - R(1) > R(0)) lo = mid;
+        else hi = mid;
+    }
+    const R t = R(0.5) * (lo + hi);
+    const R da = t + a2, db = t + b2, dc = t + c2;
+    // a denominator vanishes only when the bracket collapsed onto -m^2 (a bead
+    // on the medial set inside, without a unique nearest point): component 0
+    sx = da > R(0) ? rdiv(x * a2, da) : R(0);
+    sy = db > R(0) ? rdiv(y * b2, db) : R(0);
+    sz = dc > R(0) ? rdiv(z * c2, dc) : R(0);
+}
+
+template <typename R, int BPT>
+__global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<R> a) {
+    extern __shared__ unsigned char smem_raw[];
+    R *px = reinterpret_cast<R *>(smem_raw);
+    R *py = px + a.max_count;
+    R *pz = py + a.max_count;
+    R *vx = pz + a.max_count;              // velocities
+    R *vy = vx + a.max_count;
+    R *vz = vy + a.max_count;
+    const int s = blockIdx.x;
+    const int n = a.count[s];
+    double *X = a.xyz + 3 * a.offset[s];
+    const R ax = (R)a.axes[3 * s], ay = (R)a.axes[3 * s + 1], az = (R)a.axes[3 * s + 2];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        px[i] = (R)X[3 * i];
+        py[i] = (R)X[3 * i + 1];
+        pz[i] = (R)X[3 * i + 2];
+        vx[i] = vy[i] = vz[i] = R(0);
+    }
+    __syncthreads();
+
+    for (long long step = 0; step < a.steps; ++step) {
+        R xi[BPT], yi[BPT], zi[BPT], fx[BPT], fy[BPT], fz[BPT];
+        int id[BPT];
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int i = threadIdx.x + b * blockDim.x;
+            id[b] = i < n ? i : -1;
+            xi[b] = yi[b] = zi[b] = fx[b] = fy[b] = fz[b] = R(0);
+            if (i < n) {
+                xi[b] = px[i];
+                yi[b] = py[i];
+                zi[b] = pz[i];
+                R sx, sy, sz;
+                surface_point(xi[b], yi[b], zi[b], ax, ay, az, sx, sy, sz);
+                fx[b] = -a.k2 * (xi[b] - sx);
+                fy[b] = -a.k2 * (yi[b] - sy);
+                fz[b] = -a.k2 * (zi[b] - sz);
+            }
+        }
+        // pairwise WCA, summed over j in index order
+        for (int j = 0; j < n; ++j) {
+            const R xj = px[j], yj = py[j], zj = pz[j];
+#pragma unroll
+            for (int b = 0; b < BPT; ++b) {
+                const R dx = xi[b] - xj, dy = yi[b] - yj, dz = zi[b] - zj;
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < a.rc2 && j != id[b] && id[b] >= 0) {
+                    const R s2 = rdiv(a.sig2, r2);
+                    const R s6 = s2 * s2 * s2;
+                    const R fm = rdiv(a.eps24 * (R(2) * s6 * s6 - s6), r2);
+                    fx[b] += fm * dx;
+                    fy[b] += fm * dy;
+                    fz[b] += fm * dz;
+                }
+            }
+        }
+        __syncthreads();   // every thread has read every position of this step
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int i = id[b];
+            if (i < 0) continue;
+            const R ux = a.damp * vx[i] + a.dt * fx[b];
+            const R uy = a.damp * vy[i] + a.dt * fy[b];
+            const R uz = a.damp * vz[i] + a.dt * fz[b];
+            vx[i] = ux;
+            vy[i] = uy;
+            vz[i] = uz;
+            px[i] = xi[b] + a.dt * ux;
+            py[i] = yi[b] + a.dt * uy;
+            pz[i] = zi[b] + a.dt * uz;
+        }
+        __syncthreads();   // positions of the next step are complete
+    }
+
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        R x = px[i], y = py[i], z = pz[i];
+        if (a.project_final) {
+            R sx, sy, sz;
+            surface_point(x, y, z, ax, ay, az, sx, sy, sz);
+            x = sx;
+            y = sy;
+            z = sz;
+        }
+        X[3 * i] = (double)x;
+        X[3 * i + 1] = (double)y;
+        X[3 * i + 2] = (double)z;
+    }
+}
+
+template <typename R, int BPT>
+cudaError_t launch_shells_t(const ShellArgs<R> &a, int nshells, int threads, cudaStream_t s) {
+    const size_t smem = 6 * sizeof(R) * (size_t)a.max_count;
+    cudaError_t e = cudaFuncSetAttribute(k_relax_shells<R, BPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_relax_shells<R, BPT><<<nshells, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_shells(ShellArgs<R> a, const lb_shell_params &p, int nshells, cudaStream_t s) {
+    a.k2 = (R)(2.0 * p.k_surface);
+    a.sig2 = (R)(p.sigma * p.sigma);
+    a.rc2 = (R)(kWcaCut * kWcaCut * p.sigma * p.sigma);
+    a.eps24 = (R)(24.0 * p.epsilon);
+    a.dt = (R)p.dt;
+    a.damp = (R)(1.0 - p.eta * p.dt);
+    a.steps = p.steps;
+    a.project_final = p.project_final;
+    // beads per thread: 1, 2 or 4; threads a multiple of the warp
+    const int bpt = a.max_count <= kShellThreads ? 1 : (a.max_count <= 2 * kShellThreads ? 2 : 4);
+    int threads = (a.max_count + bpt - 1) / bpt;
+    threads = ((threads + 31) / 32) * 32;
+    if (bpt == 1) return launch_shells_t<R, 1>(a, nshells, threads, s);
+    if (bpt == 2) return launch_shells_t<R, 2>(a, nshells, threads, s);
+    return launch_shells_t<R, 4>(a, nshells, threads, s);
+}
+
+}  // namespace
+
+}  // namespace lbk
+
+extern "C" lb_status lb_relax_shells(int nshells, const double *axes, const int *counts, double *xyz,
+                                     const lb_shell_params *p, void *cuda_stream, char *err, size_t err_len) {
+    auto fail = [&](lb_status st, const std::string &m) {
+        if (err && err_len) {
+            std::strncpy(err, m.c_str(), err_len - 1);
+            err[err_len - 1] = 0;
+        }
+        return st;
+    };
+    if (!axes || !counts || !xyz || !p) return fail(LB_ERR_ARG, "null pointer");
+    if (nshells < 1 || nshells > 65535) return fail(LB_ERR_ARG, "nshells must be in [1, 65535]");
+    if (p->precision != 32 && p->precision != 64) return fail(LB_ERR_ARG, "precision must be 32 or 64");
+    if (!(p->k_surface > 0.0) || !(p->sigma > 0.0) || !(p->epsilon > 0.0) || !(p->dt > 0.0) || !(p->eta >= 0.0) ||
+        !(p->eta * p->dt <= 2.0) || p->steps < 0 || !std::isfinite(p->k_surface) || !std::isfinite(p->sigma) ||
+        !std::isfinite(p->epsilon) || !std::isfinite(p->dt) || !std::isfinite(p->eta))
+        return fail(LB_ERR_ARG, "need k, sigma, epsilon, dt > 0, eta >= 0, eta dt <= 2 and steps >= 0");
+    std::vector<long long> off(nshells);
+    long long total = 0;
+    int max_count = 0;
+    for (int s = 0; s < nshells; ++s) {
+        if (counts[s] < 1 || counts[s] > LB_SHELL_MAX_BEADS)
+            return fail(LB_ERR_ARG, "every shell needs 1 to LB_SHELL_MAX_BEADS (4096) beads");
+        for (int q = 0; q < 3; ++q)
+            if (!(axes[3 * s + q] > 0.0) || !std::isfinite(axes[3 * s + q]))
+                return fail(LB_ERR_ARG, "semi-axes must be positive and finite");
+        off[s] = total;
+        total += counts[s];
+        if (counts[s] > max_count) max_count = counts[s];
+    }
+    for (long long i = 0; i < 3 * total; ++i)
+        if (!std::isfinite(xyz[i])) return fail(LB_ERR_ARG, "initial positions must be finite");
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t nd = (size_t)3 * nshells + (size_t)3 * total;
+    const size_t bytes = nd * sizeof(double) + (size_t)nshells * (sizeof(long long) + sizeof(int));
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(LB_ERR_OOM, "device allocation for the shells failed");
+    }
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    double *daxes = static_cast<double *>(d), *dxyz = daxes + 3 * nshells;
+    long long *doff = reinterpret_cast<long long *>(dxyz + 3 * total);
+    int *dcount = reinterpret_cast<int *>(doff + nshells);
+    std::vector<double> out((size_t)3 * total);
+    e = cudaMemcpyAsync(daxes, axes, 3 * nshells * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dxyz, xyz, 3 * total * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off.data(), nshells * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dcount, counts, nshells * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        if (p->precision == 64) {
+            lbk::ShellArgs<double> a{};
+            a.axes = daxes; a.count = dcount; a.offset = doff; a.xyz = dxyz; a.max_count = max_count;
+            e = lbk::launch_shells<double>(a, *p, nshells, st);
+        } else {
+            lbk::ShellArgs<float> a{};
+            a.axes = daxes; a.count = dcount; a.offset = doff; a.xyz = dxyz; a.max_count = max_count;
+            e = lbk::launch_shells<float>(a, *p, nshells, st);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dxyz, 3 * total * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("lb_relax_shells: ") + cudaGetErrorString(e));
+    for (double v : out)
+        if (!std::isfinite(v)) return fail(LB_ERR_UNSTABLE, "non-finite bead position: reduce dt or k");
+    std::memcpy(xyz, out.data(), out.size() * sizeof(double));
+    return LB_OK;
+}

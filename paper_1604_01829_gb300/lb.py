@@ -96,7 +96,7 @@ _BSIGS = {
 # every symbol include/lb.h declares
 EXPORTS = sorted(list(_SIGS) + list(_BSIGS) + ["lb_last_error", "lb_status_string", "lb_lattice",
                                                 "lb_moments_noalloc", "lb_batch_last_error",
-                                                "lb_msd_trajectory", "lb_pore_msd"])
+                                                "lb_msd_trajectory", "lb_pore_msd", "lb_relax_shells"])
 
 
 def load():
@@ -131,6 +131,9 @@ def load():
             L.lb_pore_msd.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.c_int, _dp, _llp, C.c_void_p, C.c_char_p, C.c_size_t]
             L.lb_pore_msd.restype = C.c_int
+            L.lb_relax_shells.argtypes = [C.c_int, _dp, _ip, _dp, C.POINTER(lb_shell_params), C.c_void_p,
+                                          C.c_char_p, C.c_size_t]
+            L.lb_relax_shells.restype = C.c_int
             _lib = L
     return _lib
 
@@ -220,6 +223,37 @@ def lb_pore_msd(X, shape, axis, R_pore, nbins, max_lag, stream=None):
     if st != LB_OK:
         raise LBError(st, err.value.decode())
     return out, cnt
+
+
+class lb_shell_params(C.Structure):
+    _fields_ = [("k_surface", C.c_double), ("sigma", C.c_double), ("epsilon", C.c_double),
+                ("dt", C.c_double), ("eta", C.c_double), ("steps", C.c_longlong),
+                ("precision", C.c_int), ("project_final", C.c_int)]
+
+
+SHELL_MAX_BEADS = 4096
+
+
+def lb_relax_shells(axes, xyz, steps, k_surface=1000.0, sigma=1.4, epsilon=0.1, dt=1e-3, eta=1000.0,
+                    precision=32, project_final=True, stream=None):
+    """Relax raspberry shells on the GPU (see include/lb.h). axes: [nshells, 3]
+    semi-axes; xyz: a list of [n_s, 3] initial positions, one per shell.
+    Returns the relaxed positions as a list of [n_s, 3] arrays."""
+    axes = np.ascontiguousarray(axes, dtype=np.float64).reshape(-1, 3)
+    shells = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) for x in xyz]
+    if len(shells) != len(axes):
+        raise ValueError("one position array per shell")
+    counts = np.array([len(x) for x in shells], np.int32)
+    flat = np.ascontiguousarray(np.concatenate(shells).reshape(-1))
+    p = lb_shell_params(float(k_surface), float(sigma), float(epsilon), float(dt), float(eta), int(steps),
+                        int(precision), int(bool(project_final)))
+    err = C.create_string_buffer(256)
+    st = load().lb_relax_shells(len(shells), _d(axes), counts.ctypes.data_as(_ip), _d(flat), C.byref(p),
+                                C.c_void_p(stream) if stream else None, err, 256)
+    if st != LB_OK:
+        raise LBError(st, err.value.decode())
+    out = flat.reshape(-1, 3)
+    return np.split(out, np.cumsum(counts)[:-1])
 
 
 def make_params(nx, ny, nz, precision=64, collision=0, tau=1.0, gamma_shear=0.0, gamma_bulk=0.0,

@@ -98,17 +98,8 @@ def ellipsoid_raspberry(a: float, b: float, c: float, density: float = 1.0,
     """Filled two-layer ellipsoidal raspberry with semi-axes (a, b, c) along the
     body x, y, z axes (Sec. 2.1: inner shell (a-0.5, b-0.5, c-0.5))."""
     rng = np.random.default_rng(seed)
-    shells = [(a, b, c)]
-    if inner_offset > 0 and min(a, b, c) - inner_offset > 0.25:
-        shells.append((a - inner_offset, b - inner_offset, c - inner_offset))
-    if fill:
-        k = inner_offset + 1.0
-        while min(a, b, c) - k > 0.25:
-            shells.append((a - k, b - k, c - k))
-            k += 1.0
     pts = []
-    for (sa, sb, sc) in shells:
-        n = max(1, int(round(ellipsoid_area(sa, sb, sc) * density)))
+    for (sa, sb, sc), n in raspberry_shells(a, b, c, density, inner_offset, fill):
         pts.append(_ellipsoid_shell(sa, sb, sc, n, rng))
     if fill:
         # a line of core beads along the longest axis, unit spacing
@@ -119,6 +110,44 @@ def ellipsoid_raspberry(a: float, b: float, c: float, density: float = 1.0,
         core[:, ax] = np.arange(-m, m + 1, dtype=np.float64)
         pts.append(core)
     return np.concatenate(pts, axis=0)
+
+
+def raspberry_shells(a: float, b: float, c: float, density: float = 1.0, inner_offset: float = 0.5,
+                     fill: bool = True) -> list:
+    """(semi-axes, bead count) of every shell of a filled two-layer raspberry
+    (Sec. 2.1): the outer shell, the inner shell inner_offset further in, fill
+    shells every unit further in; round(area x density) beads each."""
+    shells = [(a, b, c)]
+    if inner_offset > 0 and min(a, b, c) - inner_offset > 0.25:
+        shells.append((a - inner_offset, b - inner_offset, c - inner_offset))
+    if fill:
+        k = inner_offset + 1.0
+        while min(a, b, c) - k > 0.25:
+            shells.append((a - k, b - k, c - k))
+            k += 1.0
+    return [((sa, sb, sc), max(1, int(round(ellipsoid_area(sa, sb, sc) * density)))) for (sa, sb, sc) in shells]
+
+
+def random_shell_start(a: float, b: float, c: float, n: int, seed: int, spread: float = 0.0) -> np.ndarray:
+    """Seeded starting positions for a shell relaxation: n uniformly random
+    directions u mapped to (a u_x, b u_y, c u_z) on the ellipsoid (not
+    area-uniform: the relaxation evens them out), each scaled by
+    1 + spread U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    scale = 1.0 + spread * rng.uniform(-1.0, 1.0, size=(n, 1))
+    return u * np.array([a, b, c]) * scale
+
+
+def spread_shell_start(a: float, b: float, c: float, n: int, seed: int, jitter: float = 0.0) -> np.ndarray:
+    """Seeded, roughly evenly spread starting positions for a shell
+    relaxation (area-uniform candidates thinned by farthest-point selection,
+    so no two beads start very close), each scaled radially by
+    1 + jitter U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    P = _ellipsoid_shell(a, b, c, n, rng)
+    return P * (1.0 + jitter * rng.uniform(-1.0, 1.0, size=(n, 1)))
 
 
 def solid_ellipsoid_inertia(mass: float, a: float, b: float, c: float) -> np.ndarray:

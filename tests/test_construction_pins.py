@@ -74,6 +74,22 @@ def test_nearest_point_by_brute_force_and_normal_condition(ax):
         assert abs(C.bisection_function(t, p, ax)) < 1e-6                    # the paper's tolerance
 
 
+def test_vectorised_forms_equal_the_per_bead_forms():
+    ax = np.array([3.0, 2.0, 1.5])
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(30, 3)) * 1.5
+    P = C.surface_points(X, ax)
+    for i in range(len(X)):
+        assert np.array_equal(P[i], C.surface_point(X[i], ax)[0])
+    F = C.forces(X, ax, 1000.0, 1.4, 0.1)
+    for i in range(len(X)):
+        f = -2000.0 * (X[i] - P[i])
+        for j in range(len(X)):
+            if j != i:
+                f = f + C.wca_force(X[i] - X[j], 1.4, 0.1)
+        assert np.allclose(F[i], f, rtol=1e-13, atol=1e-13)
+
+
 def test_printed_bisection_function_is_inconsistent():
     """Reading check: with the '+1' inside the squares, as printed, the exact
     nearest point's t does not solve the equation; without it, it does."""
