@@ -174,6 +174,7 @@ class Body:
     F_ext: np.ndarray = field(default_factory=lambda: np.zeros(3))
     T_ext: np.ndarray = field(default_factory=lambda: np.zeros(3))
     fixed: int = 0          # 0 free, 1 held, 2 translation only
+    axes: tuple | None = None  # semi-axes (a, b, c) of an ellipsoidal raspberry
 
 
 @dataclass
@@ -309,7 +310,7 @@ def ellipsoids_256(n_bodies: int = 64, L: int = 256, seed: int = 1607, kT: float
         beads = ellipsoid_raspberry(a_ax, b_ax, b_ax, seed=int(rng.integers(1 << 30)))
         mass = (4.0 / 3.0) * math.pi * a_ax * b_ax * b_ax
         bodies.append(Body(beads, X, random_unit_quaternion(rng), mass,
-                           solid_ellipsoid_inertia(mass, a_ax, b_ax, b_ax)))
+                           solid_ellipsoid_inertia(mass, a_ax, b_ax, b_ax), axes=(a_ax, b_ax, b_ax)))
     params = dict(collision=1, rho0=1.0, kT=kT, gamma_bead=paper_gamma_to_lattice(gamma), seed=seed, precision=precision,
                   compensate_force=0, **mrt_rates(NU_PAPER))
     return Workload(f"ellipsoids{n_bodies}_{L}^3_mrt_kT", L, L, L, params, bodies, None, 2000)
