@@ -8,17 +8,38 @@
 namespace lbk {
 
 // Pre-collision density and momentum of one node in the compute precision R.
+// A periodic box without walls (the common case) takes the neighbours from
+// per-axis wrapped offsets, so the 19 loads issue back to back; boxes with
+// walls go through load_pre (wall and moving-wall tests per link).
 template <typename R, typename T>
 __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int y, int z, long long n,
                                            bool odd, R rho0, R &rho, R j[3]) {
+    R v[19];
+    if (g.pore_axis < 0 && !g.chan) {
+        const int nx = g.nx, nxy = g.nx * g.ny;
+        const int xo[3] = {(x == 0 ? nx : x) - 1, x, x + 1 == nx ? 0 : x + 1};
+        const int yo[3] = {((y == 0 ? g.ny : y) - 1) * nx, y * nx, (y + 1 == g.ny ? 0 : y + 1) * nx};
+        const int zo[3] = {((z == 0 ? g.nz : z) - 1) * nxy, z * nxy, (z + 1 == g.nz ? 0 : z + 1) * nxy};
+        if (!odd) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) v[i] = (R)A[(long long)i * g.N + n];
+        } else {
+            v[0] = (R)A[n];
+#pragma unroll
+            for (int i = 1; i < 19; ++i)
+                v[i] = (R)A[(long long)opp(i) * g.N + (unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)])];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) v[i] = (R)load_pre(A, g, x, y, z, n, i, odd);
+    }
     R s = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const R v = (R)load_pre(A, g, x, y, z, n, i, odd);
-        s += v;
-        if (cx(i)) jx += cx(i) * v;
-        if (cy(i)) jy += cy(i) * v;
-        if (cz(i)) jz += cz(i) * v;
+        s += v[i];
+        if (cx(i)) jx += cx(i) * v[i];
+        if (cy(i)) jy += cy(i) * v[i];
+        if (cz(i)) jz += cz(i) * v[i];
     }
     rho = sizeof(T) == 4 ? rho0 + s : s;
     j[0] = jx; j[1] = jy; j[2] = jz;
