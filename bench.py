@@ -260,7 +260,9 @@ def run_ours(args, ws, rank, local):
     peak, peak_kind = measured_peak()
     bytes_per_node = 2 * 19 * 4
     achieved = bytes_per_node * N / (main["kernel_ms"] * 1e-3) / 1e9
-    traffic = ncu_traffic(WORKLOAD)
+    default_size = (args.lattice, args.bodies) == (256, 64)
+    # the committed DRAM counters are for the 256^3 / 64-body workload
+    traffic = ncu_traffic(WORKLOAD) if default_size else None
     copy_gbs = copy_ceiling(torch, torch.cuda.Stream())
 
     # end to end through the C ABI with host buffers: per step the host sets
@@ -300,7 +302,7 @@ def run_ours(args, ws, rank, local):
                      "hbm_frac": round(fp64_ach / peak, 4), "bytes_per_node": 2 * 19 * 8}
         # the FP64 step is bound by the FP64 pipe: instruction counts per node
         # from the committed ncu capture of the same kernel
-        ops = ncu_entry(WORKLOAD.replace("_fp32", "_fp64_ops"))
+        ops = ncu_entry(WORKLOAD.replace("_fp32", "_fp64_ops")) if default_size else None
         if ops is not None:
             rate = fp64["nodes"] / (fp64["kernel_ms"] * 1e-3)
             pipe = ops["fp64_thread_inst_per_node"]["fp64_pipe"] * rate
@@ -340,7 +342,8 @@ def run_ours(args, ws, rank, local):
                        else f"ellipsoids{args.bodies}_{args.lattice}^3_mrt_kT_fp32",
                        "lattice": [args.lattice] * 3, "collision": "MRT",
                        "kT": 1e-4, "nu": 0.016, "bodies": main["nbodies"], "beads": main["nbeads"],
-                       "storage": "fp32 deviation f - w rho0", "l2": "state 1.27 GB > L2, no flush",
+                       "storage": "fp32 deviation f - w rho0",
+                       "l2": f"state {N * 76 / 1e9:.2f} GB " + ("> L2, no flush" if N * 76 > 129e6 else "fits in L2"),
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "kernel": "k_collide_stream<float,MRT,noise>",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
