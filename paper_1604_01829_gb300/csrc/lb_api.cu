@@ -167,7 +167,7 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
         a.pd.ks[k - 4] = c * 0.5 * (1.0 + g);
     }
     for (int k = 10; k <= 18; ++k) a.pd.kg[k - 10] = (1.0 / 36.0) / bk[k] * rate(k);
-    for (int k = 4; k <= 18; ++k) a.pd.kn[k - 4] = (1.0 / 36.0) / bk[k] * h->sig[k - 4];
+    for (int k = 4; k <= 18; ++k) a.pd.kn[k - 4] = (1.0 / 36.0) / bk[k] * h->sig[k - 4] * 3.4641016151377544;
     a.pf.rho0 = (float)a.pd.rho0;
     a.pf.omega = (float)a.pd.omega;
     for (int k = 0; k < 6; ++k) {
@@ -176,7 +176,7 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
         a.pf.ks[k] = (float)a.pd.ks[k];
     }
     for (int k = 0; k < 9; ++k) a.pf.kg[k] = (float)a.pd.kg[k];
-    for (int k = 0; k < 15; ++k) a.pf.kn[k] = (float)(a.pd.kn[k] * 3.4641016151377544 * 2.3283064365386963e-10);
+    for (int k = 0; k < 15; ++k) a.pf.kn[k] = (float)(a.pd.kn[k] * 2.3283064365386963e-10);
     a.gforce = h->gforce;
     a.gforce_f = h->gforce_f;
     const bool bodies = !h->hb.empty() && !h->hbody_of.empty();

@@ -458,7 +458,7 @@ void fill_coll(const lb_params &p, BInst &I) {
     for (int k = 4; k <= 18; ++k) {
         const double g = rate(k);
         const double sig = (p.collision == 1 && p.kT > 0.0) ? std::sqrt(3.0 * p.kT * bk[k] * (1.0 - g * g)) : 0.0;
-        I.pd.kn[k - 4] = (1.0 / 36.0) / bk[k] * sig;
+        I.pd.kn[k - 4] = (1.0 / 36.0) / bk[k] * sig * 3.4641016151377544;
     }
     I.pf.rho0 = (float)I.pd.rho0;
     I.pf.omega = (float)I.pd.omega;
@@ -468,7 +468,7 @@ void fill_coll(const lb_params &p, BInst &I) {
         I.pf.ks[k] = (float)I.pd.ks[k];
     }
     for (int k = 0; k < 9; ++k) I.pf.kg[k] = (float)I.pd.kg[k];
-    for (int k = 0; k < 15; ++k) I.pf.kn[k] = (float)(I.pd.kn[k] * 3.4641016151377544 * 2.3283064365386963e-10);
+    for (int k = 0; k < 15; ++k) I.pf.kn[k] = (float)(I.pd.kn[k] * 2.3283064365386963e-10);
 }
 
 lb_status validate(const lb_params &p) {

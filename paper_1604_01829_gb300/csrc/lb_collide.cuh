@@ -105,7 +105,7 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Coll
 
     if (NOISE) {
         // 15 non-conserved modes, variance 3 rho kT b_k (1 - g_k^2); kn_k holds
-        // c_k sqrt(3 kT b_k (1 - g_k^2)) (times sqrt(12) 2^-32 in FP32). The
+        // c_k sqrt(3 kT b_k (1 - g_k^2)) sqrt(12) (times 2^-32 in FP32). The
         // variates are 16-bit: two Philox calls give 16 half-words, mode 4 + j
         // takes half-word j (high half of word j/2 for even j, else the low
         // half), xi = sqrt(12) ((h + 1/2) 2^-16 - 1/2). In FP32 the half-word
@@ -118,11 +118,11 @@ __device__ __forceinline__ void collide(R (&f)[19], R Fx, R Fy, R Fz, const Coll
         if constexpr (sizeof(R) == 4) asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sr) : "f"(rho));
         else sr = sqrt(rho);
         auto hi = [&](R &q, int k, uint32_t v) {
-            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * unit_uniform16_d(v >> 16);
+            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * centred16_d(v >> 16);
             else q = fmaf(sr * a.kn[k], fmaf(__uint_as_float(((v >> 9) & 0x7FFF80u) | 0x3F800040u), 0x1p32f, -0x1.8p32f), q);
         };
         auto lo = [&](R &q, int k, uint32_t v) {
-            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * unit_uniform16_d(v & 0xFFFFu);
+            if constexpr (sizeof(R) == 8) q += (sr * a.kn[k]) * centred16_d(v & 0xFFFFu);
             else q = fmaf(sr * a.kn[k], fmaf(__uint_as_float(((v << 7) & 0x7FFF80u) | 0x3F800040u), 0x1p32f, -0x1.8p32f), q);
         };
         hi(q4, 0, r0.x); lo(q5, 1, r0.x); hi(q6, 2, r0.y); lo(q7, 3, r0.y);

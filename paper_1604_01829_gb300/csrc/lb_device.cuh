@@ -53,9 +53,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __device__ __forceinline__ double unit_uniform_d(uint32_t x) {
     return 3.4641016151377544 * (((double)x + 0.5) * 2.3283064365386963e-10 - 0.5);
 }
-// The same from 16 random bits: sqrt(12) ((h + 1/2) 2^-16 - 1/2).
-__device__ __forceinline__ double unit_uniform16_d(uint32_t h) {
-    return 3.4641016151377544 * (((double)h + 0.5) * 1.52587890625e-05 - 0.5);
+// The centred 16-bit variate (h + 1/2) 2^-16 - 1/2 (times sqrt(12) for unit
+// variance), exact in one FMA: h 2^-16 and 2^-17 - 1/2 are exact in FP64.
+__device__ __forceinline__ double centred16_d(uint32_t h) {
+    return fma((double)h, 0x1p-16, 0x1p-17 - 0.5);
 }
 __device__ __forceinline__ float unit_uniform_f(uint32_t x) {
     // (x - 2^31 + 1/2) 2^-32 with one integer-to-float conversion

@@ -20,8 +20,8 @@ struct CollParams {
     R km[6];                     // c_k g_k: weight of the pre-collision moment
     R ks[6];                     // c_k (1 + g_k)/2: weight of the Guo source moment
     R kg[9];                     // ghost modes 10-18: c_k g_k
-    R kn[15];                    // noise modes 4-18: c_k sqrt(3 kT b_k (1 - g_k^2)) / sqrt(rho)
-                                 //   (FP32: times sqrt(12) 2^-32, applied to the centred integer)
+    R kn[15];                    // noise modes 4-18: c_k sqrt(3 kT b_k (1 - g_k^2)) sqrt(12) / sqrt(rho),
+                                 //   applied to a centred uniform variate in (-1/2, 1/2) (FP32: times 2^-32)
 };
 
 // Everything the fused collide-and-stream kernel reads besides populations.
