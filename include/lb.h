@@ -401,6 +401,13 @@ typedef struct {
     int precision;           /* 64: FP64 arithmetic; 32: FP32 arithmetic (positions
                                 are returned as doubles either way)                  */
     int project_final;       /* 1: end with every bead on its nearest surface point  */
+    int pair_search;         /* 0: automatic (cell list when it fits in shared memory
+                                and a shell has 1024 beads or more, or 256 or more with
+                                at most two shells per SM); 1: all pairs; 2: cell list
+                                (cells at least as wide as the WCA range, rebuilt every
+                                step; a step with a bead outside the box 1.25 a + 1
+                                around the centre tests all pairs). The results agree
+                                to summation order.                                   */
 } lb_shell_params;
 
 /* Relax nshells independent shells in one launch (one thread block per
@@ -414,8 +421,8 @@ typedef struct {
  * non-finite position: the step is too large for the stiffness); on error
  * xyz is left unchanged. The message goes to err (err_len bytes, may be
  * NULL). Allocates and frees its own device memory and synchronises the
- * stream. Cost per step and shell: O(n^2) pair tests, n = beads of the
- * shell. */
+ * stream. Cost per step and shell: O(n) with the cell list, O(n^2) when
+ * testing all pairs, n = beads of the shell. */
 #define LB_SHELL_MAX_BEADS 4096
 lb_status lb_relax_shells(int nshells, const double *axes, const int *counts, double *xyz,
                           const lb_shell_params *params, void *cuda_stream, char *err, size_t err_len);

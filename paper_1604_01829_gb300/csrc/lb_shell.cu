@@ -36,6 +36,8 @@ namespace lbk {
 namespace {
 
 constexpr int kShellThreads = 1024;
+constexpr int kMaxCells = 4096;                     // cells per shell at most
+constexpr int kCellsFrom = 256;                     // automatic pair search: cell list from this many beads
 constexpr double kWcaCut = 1.122462048309373;      // 2^(1/6)
 
 template <typename R>
@@ -50,6 +52,11 @@ struct ShellArgs {
     R dt, damp;               // dt, 1 - eta dt
     long long steps;
     int project_final;
+    // cell list (CELLS kernels): per shell the grid g[3] over the box
+    // [-L, L) per axis (L = box[3 s + q]) with cells of size >= the WCA range
+    const int *cgrid;         // [nshells][3]
+    const double *cbox;       // [nshells][3] half-widths L
+    int max_cells;            // largest grid (shared-memory extent)
 };
 
 __device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
@@ -83,7 +90,45 @@ __device__ __forceinline__ void surface_point(R x, R y, R z, R a, R b, R c, R &s
     sz = dc > R(0) ? rdiv(z * c2, dc) : R(0);
 }
 
-template <typename R, int BPT>
+// Block-wide exclusive scan of cnt[0..C) into start[0..C] (start[C] = total),
+// resetting cnt to 0 (it then serves as the fill cursor). wsum: 32 ints.
+__device__ __forceinline__ void scan_cells(int *cnt, int *start, int C, int *wsum) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (C + T - 1) / T;
+    const int c0 = min(C, tid * per), c1 = min(C, c0 + per);
+    int sum = 0;
+    for (int c = c0; c < c1; ++c) sum += cnt[c];
+    int v = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < ((T + 31) >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int base = v - sum + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int c = c0; c < c1; ++c) {
+        start[c] = base;
+        base += cnt[c];
+        cnt[c] = 0;
+    }
+    if (tid == T - 1) start[C] = base;
+}
+
+// One block per shell. CELLS: pair search through a cell list rebuilt every
+// step (counting sort by cell, beads of a cell in index order, so results do
+// not depend on the order of the atomics); a step in which a bead lies
+// outside the grid's box searches all pairs instead. Without CELLS every
+// step tests all pairs, summed in index order.
+template <typename R, int BPT, bool CELLS>
 __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<R> a) {
     extern __shared__ unsigned char smem_raw[];
     R *px = reinterpret_cast<R *>(smem_raw);
@@ -92,10 +137,24 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
     R *vx = pz + a.max_count;              // velocities
     R *vy = vx + a.max_count;
     R *vz = vy + a.max_count;
+    int *bcell = reinterpret_cast<int *>(vz + a.max_count);   // CELLS: cell of each bead
+    int *sorted = bcell + a.max_count;                        // bead indices by cell
+    int *cnt = sorted + a.max_count;                          // per cell count / cursor
+    int *start = cnt + a.max_cells;                           // per cell first slot (+1)
+    __shared__ int wsum[32];
     const int s = blockIdx.x;
     const int n = a.count[s];
     double *X = a.xyz + 3 * a.offset[s];
     const R ax = (R)a.axes[3 * s], ay = (R)a.axes[3 * s + 1], az = (R)a.axes[3 * s + 2];
+    int gx = 1, gy = 1, gz = 1, C = 1;
+    R Lx = R(0), Ly = R(0), Lz = R(0), ihx = R(0), ihy = R(0), ihz = R(0);
+    if (CELLS) {
+        gx = a.cgrid[3 * s]; gy = a.cgrid[3 * s + 1]; gz = a.cgrid[3 * s + 2];
+        C = gx * gy * gz;
+        Lx = (R)a.cbox[3 * s]; Ly = (R)a.cbox[3 * s + 1]; Lz = (R)a.cbox[3 * s + 2];
+        ihx = (R)gx / (R(2) * Lx); ihy = (R)gy / (R(2) * Ly); ihz = (R)gz / (R(2) * Lz);
+        for (int c = threadIdx.x; c < C; c += blockDim.x) cnt[c] = 0;
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         px[i] = (R)X[3 * i];
         py[i] = (R)X[3 * i + 1];
@@ -107,6 +166,7 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
     for (long long step = 0; step < a.steps; ++step) {
         R xi[BPT], yi[BPT], zi[BPT], fx[BPT], fy[BPT], fz[BPT];
         int id[BPT];
+        bool outside = false;
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
             const int i = threadIdx.x + b * blockDim.x;
@@ -116,6 +176,18 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
                 xi[b] = px[i];
                 yi[b] = py[i];
                 zi[b] = pz[i];
+                if (CELLS) {
+                    const int cx = (int)floor((xi[b] + Lx) * ihx), cy = (int)floor((yi[b] + Ly) * ihy),
+                              cz = (int)floor((zi[b] + Lz) * ihz);
+                    if (cx < 0 || cx >= gx || cy < 0 || cy >= gy || cz < 0 || cz >= gz) {
+                        outside = true;
+                        bcell[i] = -1;
+                    } else {
+                        const int c = cx + gx * (cy + gy * cz);
+                        bcell[i] = c;
+                        atomicAdd(&cnt[c], 1);
+                    }
+                }
                 R sx, sy, sz;
                 surface_point(xi[b], yi[b], zi[b], ax, ay, az, sx, sy, sz);
                 fx[b] = -a.k2 * (xi[b] - sx);
@@ -123,20 +195,81 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
                 fz[b] = -a.k2 * (zi[b] - sz);
             }
         }
-        // pairwise WCA, summed over j in index order
-        for (int j = 0; j < n; ++j) {
-            const R xj = px[j], yj = py[j], zj = pz[j];
+        auto pair = [&](int b, int j) {
+            const R dx = xi[b] - px[j], dy = yi[b] - py[j], dz = zi[b] - pz[j];
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < a.rc2 && j != id[b]) {
+                const R s2 = rdiv(a.sig2, r2);
+                const R s6 = s2 * s2 * s2;
+                const R fm = rdiv(a.eps24 * (R(2) * s6 * s6 - s6), r2);
+                fx[b] += fm * dx;
+                fy[b] += fm * dy;
+                fz[b] += fm * dz;
+            }
+        };
+        bool use_cells = false;
+        if (CELLS) {
+            use_cells = !__syncthreads_or(outside);
+            if (use_cells) {
+                scan_cells(cnt, start, C, wsum);
+                __syncthreads();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) sorted[start[bcell[i]] + atomicAdd(&cnt[bcell[i]], 1)] = i;
+                __syncthreads();
+                // beads of each cell in index order (few per cell: insertion sort)
+                for (int c = threadIdx.x; c < C; c += blockDim.x) {
+                    for (int k = start[c] + 1; k < start[c + 1]; ++k) {
+                        const int v = sorted[k];
+                        int m = k - 1;
+                        while (m >= start[c] && sorted[m] > v) {
+                            sorted[m + 1] = sorted[m];
+                            --m;
+                        }
+                        sorted[m + 1] = v;
+                    }
+                }
+                __syncthreads();
+            } else {
+                for (int c = threadIdx.x; c < C; c += blockDim.x) cnt[c] = 0;
+            }
+        }
+        if (use_cells) {
+            // WCA over the 27 cells around each bead (cells are at least as wide as the range)
 #pragma unroll
             for (int b = 0; b < BPT; ++b) {
-                const R dx = xi[b] - xj, dy = yi[b] - yj, dz = zi[b] - zj;
-                const R r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < a.rc2 && j != id[b] && id[b] >= 0) {
-                    const R s2 = rdiv(a.sig2, r2);
-                    const R s6 = s2 * s2 * s2;
-                    const R fm = rdiv(a.eps24 * (R(2) * s6 * s6 - s6), r2);
-                    fx[b] += fm * dx;
-                    fy[b] += fm * dy;
-                    fz[b] += fm * dz;
+                if (id[b] < 0) continue;
+                const int c = bcell[id[b]];
+                const int cx = c % gx, cy = (c / gx) % gy, cz = c / (gx * gy);
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const int z = cz + dz;
+                    if (z < 0 || z >= gz) continue;
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int y = cy + dy;
+                        if (y < 0 || y >= gy) continue;
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int x = cx + dx;
+                            if (x < 0 || x >= gx) continue;
+                            const int cc = x + gx * (y + gy * z);
+                            for (int k = start[cc]; k < start[cc + 1]; ++k) pair(b, sorted[k]);
+                        }
+                    }
+                }
+            }
+        } else {
+            // pairwise WCA, summed over j in index order (one read of j for all owned beads)
+            for (int j = 0; j < n; ++j) {
+                const R xj = px[j], yj = py[j], zj = pz[j];
+#pragma unroll
+                for (int b = 0; b < BPT; ++b) {
+                    const R dx = xi[b] - xj, dy = yi[b] - yj, dz = zi[b] - zj;
+                    const R r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < a.rc2 && j != id[b] && id[b] >= 0) {
+                        const R s2 = rdiv(a.sig2, r2);
+                        const R s6 = s2 * s2 * s2;
+                        const R fm = rdiv(a.eps24 * (R(2) * s6 * s6 - s6), r2);
+                        fx[b] += fm * dx;
+                        fy[b] += fm * dy;
+                        fz[b] += fm * dz;
+                    }
                 }
             }
         }
@@ -155,6 +288,8 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
             py[i] = yi[b] + a.dt * uy;
             pz[i] = zi[b] + a.dt * uz;
         }
+        if (CELLS && use_cells)
+            for (int c = threadIdx.x; c < C; c += blockDim.x) cnt[c] = 0;
         __syncthreads();   // positions of the next step are complete
     }
 
@@ -173,18 +308,22 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
     }
 }
 
-template <typename R, int BPT>
+size_t shell_smem(size_t rsize, int max_count, int max_cells, bool cells) {
+    return 6 * rsize * (size_t)max_count + (cells ? sizeof(int) * (2 * (size_t)max_count + 2 * (size_t)max_cells + 1) : 0);
+}
+
+template <typename R, int BPT, bool CELLS>
 cudaError_t launch_shells_t(const ShellArgs<R> &a, int nshells, int threads, cudaStream_t s) {
-    const size_t smem = 6 * sizeof(R) * (size_t)a.max_count;
-    cudaError_t e = cudaFuncSetAttribute(k_relax_shells<R, BPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = shell_smem(sizeof(R), a.max_count, a.max_cells, CELLS);
+    cudaError_t e = cudaFuncSetAttribute(k_relax_shells<R, BPT, CELLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_relax_shells<R, BPT><<<nshells, threads, smem, s>>>(a);
+    k_relax_shells<R, BPT, CELLS><<<nshells, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_shells(ShellArgs<R> a, const lb_shell_params &p, int nshells, cudaStream_t s) {
+cudaError_t launch_shells(ShellArgs<R> a, const lb_shell_params &p, int nshells, bool cells, cudaStream_t s) {
     a.k2 = (R)(2.0 * p.k_surface);
     a.sig2 = (R)(p.sigma * p.sigma);
     a.rc2 = (R)(kWcaCut * kWcaCut * p.sigma * p.sigma);
@@ -197,9 +336,14 @@ cudaError_t launch_shells(ShellArgs<R> a, const lb_shell_params &p, int nshells,
     const int bpt = a.max_count <= kShellThreads ? 1 : (a.max_count <= 2 * kShellThreads ? 2 : 4);
     int threads = (a.max_count + bpt - 1) / bpt;
     threads = ((threads + 31) / 32) * 32;
-    if (bpt == 1) return launch_shells_t<R, 1>(a, nshells, threads, s);
-    if (bpt == 2) return launch_shells_t<R, 2>(a, nshells, threads, s);
-    return launch_shells_t<R, 4>(a, nshells, threads, s);
+    if (cells) {
+        if (bpt == 1) return launch_shells_t<R, 1, true>(a, nshells, threads, s);
+        if (bpt == 2) return launch_shells_t<R, 2, true>(a, nshells, threads, s);
+        return launch_shells_t<R, 4, true>(a, nshells, threads, s);
+    }
+    if (bpt == 1) return launch_shells_t<R, 1, false>(a, nshells, threads, s);
+    if (bpt == 2) return launch_shells_t<R, 2, false>(a, nshells, threads, s);
+    return launch_shells_t<R, 4, false>(a, nshells, threads, s);
 }
 
 }  // namespace
@@ -222,6 +366,7 @@ extern "C" lb_status lb_relax_shells(int nshells, const double *axes, const int 
         !(p->eta * p->dt <= 2.0) || p->steps < 0 || !std::isfinite(p->k_surface) || !std::isfinite(p->sigma) ||
         !std::isfinite(p->epsilon) || !std::isfinite(p->dt) || !std::isfinite(p->eta))
         return fail(LB_ERR_ARG, "need k, sigma, epsilon, dt > 0, eta >= 0, eta dt <= 2 and steps >= 0");
+    if (p->pair_search < 0 || p->pair_search > 2) return fail(LB_ERR_ARG, "pair_search must be 0, 1 or 2");
     std::vector<long long> off(nshells);
     long long total = 0;
     int max_count = 0;
@@ -238,33 +383,76 @@ extern "C" lb_status lb_relax_shells(int nshells, const double *axes, const int 
     for (long long i = 0; i < 3 * total; ++i)
         if (!std::isfinite(xyz[i])) return fail(LB_ERR_ARG, "initial positions must be finite");
 
+    // cell grids: per axis the box [-L, L), L = 1.25 a + 1, cut into cells at
+    // least as wide as the WCA range, at most kMaxCells cells per shell
+    const double rc = lbk::kWcaCut * p->sigma;
+    std::vector<int> grid((size_t)3 * nshells);
+    std::vector<double> box((size_t)3 * nshells);
+    int max_cells = 1;
+    for (int s = 0; s < nshells; ++s) {
+        long long g[3];
+        for (int q = 0; q < 3; ++q) {
+            box[3 * s + q] = 1.25 * axes[3 * s + q] + 1.0;
+            g[q] = std::max(1LL, (long long)std::floor(2.0 * box[3 * s + q] / rc));
+            g[q] = std::min(g[q], 4096LL);
+        }
+        while (g[0] * g[1] * g[2] > lbk::kMaxCells) {
+            const int q = g[0] >= g[1] && g[0] >= g[2] ? 0 : (g[1] >= g[2] ? 1 : 2);
+            g[q] = std::max(1LL, (g[q] * 7) / 8);
+        }
+        for (int q = 0; q < 3; ++q) grid[3 * s + q] = (int)g[q];
+        max_cells = std::max(max_cells, (int)(g[0] * g[1] * g[2]));
+    }
+    const size_t rsize = p->precision == 64 ? sizeof(double) : sizeof(float);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+    const bool cells_fit = lbk::shell_smem(rsize, max_count, max_cells, true) <= (size_t)optin;
+    if (p->pair_search == 2 && !cells_fit)
+        return fail(LB_ERR_ARG, "the cell list does not fit in shared memory for this shell size and precision");
+    if (lbk::shell_smem(rsize, max_count, 1, false) > (size_t)optin)
+        return fail(LB_ERR_ARG, "the shell does not fit in shared memory at this precision");
+    // automatic: the cell list pays off when a block per shell is latency-bound
+    // (few shells for the SMs) or the shells are large; many small shells fill
+    // the GPU and are faster testing all pairs (measured on GB300)
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 1;
+    const bool auto_cells = max_count >= 1024 || (max_count >= lbk::kCellsFrom && nshells <= 2 * nsm);
+    const bool cells = p->pair_search == 2 || (p->pair_search == 0 && auto_cells && cells_fit);
+
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const size_t nd = (size_t)3 * nshells + (size_t)3 * total;
-    const size_t bytes = nd * sizeof(double) + (size_t)nshells * (sizeof(long long) + sizeof(int));
+    const size_t nd = (size_t)3 * nshells + (size_t)3 * total + (size_t)3 * nshells;
+    const size_t bytes = nd * sizeof(double) + (size_t)nshells * (sizeof(long long) + sizeof(int) + 3 * sizeof(int));
     void *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, bytes);
+    e = cudaMalloc(&d, bytes);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return fail(LB_ERR_OOM, "device allocation for the shells failed");
     }
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    double *daxes = static_cast<double *>(d), *dxyz = daxes + 3 * nshells;
-    long long *doff = reinterpret_cast<long long *>(dxyz + 3 * total);
+    double *daxes = static_cast<double *>(d), *dxyz = daxes + 3 * nshells, *dbox = dxyz + 3 * total;
+    long long *doff = reinterpret_cast<long long *>(dbox + 3 * nshells);
     int *dcount = reinterpret_cast<int *>(doff + nshells);
+    int *dgrid = dcount + nshells;
     std::vector<double> out((size_t)3 * total);
     e = cudaMemcpyAsync(daxes, axes, 3 * nshells * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dxyz, xyz, 3 * total * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off.data(), nshells * sizeof(long long), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dcount, counts, nshells * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbox, box.data(), 3 * nshells * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dgrid, grid.data(), 3 * nshells * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         if (p->precision == 64) {
             lbk::ShellArgs<double> a{};
             a.axes = daxes; a.count = dcount; a.offset = doff; a.xyz = dxyz; a.max_count = max_count;
-            e = lbk::launch_shells<double>(a, *p, nshells, st);
+            a.cgrid = dgrid; a.cbox = dbox; a.max_cells = cells ? max_cells : 1;
+            e = lbk::launch_shells<double>(a, *p, nshells, cells, st);
         } else {
             lbk::ShellArgs<float> a{};
             a.axes = daxes; a.count = dcount; a.offset = doff; a.xyz = dxyz; a.max_count = max_count;
-            e = lbk::launch_shells<float>(a, *p, nshells, st);
+            a.cgrid = dgrid; a.cbox = dbox; a.max_cells = cells ? max_cells : 1;
+            e = lbk::launch_shells<float>(a, *p, nshells, cells, st);
         }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dxyz, 3 * total * sizeof(double), cudaMemcpyDeviceToHost, st);

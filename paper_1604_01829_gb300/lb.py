@@ -228,14 +228,14 @@ def lb_pore_msd(X, shape, axis, R_pore, nbins, max_lag, stream=None):
 class lb_shell_params(C.Structure):
     _fields_ = [("k_surface", C.c_double), ("sigma", C.c_double), ("epsilon", C.c_double),
                 ("dt", C.c_double), ("eta", C.c_double), ("steps", C.c_longlong),
-                ("precision", C.c_int), ("project_final", C.c_int)]
+                ("precision", C.c_int), ("project_final", C.c_int), ("pair_search", C.c_int)]
 
 
 SHELL_MAX_BEADS = 4096
 
 
 def lb_relax_shells(axes, xyz, steps, k_surface=1000.0, sigma=1.4, epsilon=0.1, dt=1e-3, eta=1000.0,
-                    precision=32, project_final=True, stream=None):
+                    precision=32, project_final=True, pair_search=0, stream=None):
     """Relax raspberry shells on the GPU (see include/lb.h). axes: [nshells, 3]
     semi-axes; xyz: a list of [n_s, 3] initial positions, one per shell.
     Returns the relaxed positions as a list of [n_s, 3] arrays."""
@@ -246,7 +246,7 @@ def lb_relax_shells(axes, xyz, steps, k_surface=1000.0, sigma=1.4, epsilon=0.1, 
     counts = np.array([len(x) for x in shells], np.int32)
     flat = np.ascontiguousarray(np.concatenate(shells).reshape(-1))
     p = lb_shell_params(float(k_surface), float(sigma), float(epsilon), float(dt), float(eta), int(steps),
-                        int(precision), int(bool(project_final)))
+                        int(precision), int(bool(project_final)), int(pair_search))
     err = C.create_string_buffer(256)
     st = load().lb_relax_shells(len(shells), _d(axes), counts.ctypes.data_as(_ip), _d(flat), C.byref(p),
                                 C.c_void_p(stream) if stream else None, err, 256)

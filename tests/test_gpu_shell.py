@@ -3,7 +3,8 @@ against the construction oracle (oracle/construction.py): element-wise
 parity of the nearest surface points and of whole relaxations in FP64 and
 FP32, sampled one-step parity at the largest shell sizes, the optimal
 2/4/6-point arrangements, many shells in one launch equal to each shell
-alone, and argument errors.
+alone, the cell-list pair search against the all-pairs one and its fallback
+for beads outside its box, and argument errors.
 
 Tolerances: FP64 differs from the oracle by contraction (FMA) and division
 rounding only, O(1e-15) per operation, and the damped scheme does not amplify
@@ -51,12 +52,13 @@ def test_nearest_surface_points_match_oracle(precision, tol):
 
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-4)])
 @pytest.mark.parametrize("project", [False, True])
-def test_relaxation_matches_oracle(precision, tol, project):
+@pytest.mark.parametrize("search", [1, 2])
+def test_relaxation_matches_oracle(precision, tol, project, search):
     from paper_1604_01829_gb300 import lb
     starts = _spread_starts(density=0.5)
     steps = 150
     out = lb.lb_relax_shells(SHAPES, starts, steps=steps, dt=0.01, eta=100.0, precision=precision,
-                             project_final=project)
+                             project_final=project, pair_search=search)
     for ax, X0, X in zip(SHAPES, starts, out):
         ref = C.relax_shell(X0, ax, steps, dt=0.01, eta=100.0, project_final=project)
         err = np.abs(X - ref).max()
@@ -69,8 +71,9 @@ def test_paper_time_step_matches_oracle():
     0.8 beads per unit area, FP64 and FP32."""
     from paper_1604_01829_gb300 import lb
     starts = _spread_starts()
-    for precision, tol in ((64, 1e-9), (32, 1e-4)):
-        out = lb.lb_relax_shells(SHAPES, starts, steps=200, precision=precision, project_final=False)
+    for precision, tol, search in ((64, 1e-9, 1), (64, 1e-9, 2), (32, 1e-4, 2)):
+        out = lb.lb_relax_shells(SHAPES, starts, steps=200, precision=precision, project_final=False,
+                                 pair_search=search)
         for ax, X0, X in zip(SHAPES, starts, out):
             ref = C.relax_shell(X0, ax, 200, project_final=False)
             assert np.abs(X - ref).max() <= tol, (precision, ax, np.abs(X - ref).max())
@@ -78,7 +81,8 @@ def test_paper_time_step_matches_oracle():
 
 
 @pytest.mark.parametrize("n", [1000, 1500, 3000, 4096])
-def test_one_step_at_full_shell_sizes_on_sampled_beads(n):
+@pytest.mark.parametrize("search", [1, 2])
+def test_one_step_at_full_shell_sizes_on_sampled_beads(n, search):
     """From rest, one step moves bead i by dt^2 F_i; the oracle computes F_i
     of sampled beads one by one (all n - 1 partners) at every beads-per-thread
     layout (1, 2 and 4 beads per thread)."""
@@ -87,7 +91,9 @@ def test_one_step_at_full_shell_sizes_on_sampled_beads(n):
     ax = (1.3 * a, a, 0.8 * a)
     X0 = W.spread_shell_start(*ax, n, seed=n, jitter=0.02)
     dt = 0.001
-    (X,) = lb.lb_relax_shells([ax], [X0], steps=1, dt=dt, eta=1000.0, precision=64, project_final=False)
+    p64 = 32 if (search == 2 and n == 4096) else 64          # an FP64 cell list of 4096 beads does not fit
+    (X,) = lb.lb_relax_shells([ax], [X0], steps=1, dt=dt, eta=1000.0, precision=p64, project_final=False,
+                              pair_search=search)
     rng = np.random.default_rng(3)
     for i in rng.choice(n, 12, replace=False):
         rs, _ = C.surface_point(X0[i], ax)
@@ -97,8 +103,9 @@ def test_one_step_at_full_shell_sizes_on_sampled_beads(n):
         for j in np.nonzero(r2 < (C.WCA_CUT * 1.4) ** 2)[0]:
             if j != i:
                 F = F + C.wca_force(d[j], 1.4, 0.1)
-        assert np.allclose(X[i], X0[i] + dt * dt * F, rtol=0, atol=1e-10), i
-    (X32,) = lb.lb_relax_shells([ax], [X0], steps=1, dt=dt, eta=1000.0, precision=32, project_final=False)
+        assert np.allclose(X[i], X0[i] + dt * dt * F, rtol=0, atol=1e-10 if p64 == 64 else 1e-5), i
+    (X32,) = lb.lb_relax_shells([ax], [X0], steps=1, dt=dt, eta=1000.0, precision=32, project_final=False,
+                                pair_search=search)
     assert np.abs(X32 - X).max() < 1e-4
 
 
@@ -126,10 +133,23 @@ def test_many_shells_in_one_launch_equal_each_alone():
         n = int(rng.integers(5, 300))
         axes.append(ax)
         starts.append(W.spread_shell_start(*ax, n, seed=100 + s, jitter=0.05))
-    together = lb.lb_relax_shells(axes, starts, steps=60, precision=32)
-    for s in (0, 7, 23, 39):
-        (alone,) = lb.lb_relax_shells([axes[s]], [starts[s]], steps=60, precision=32)
-        assert np.array_equal(alone, together[s])
+    for search in (1, 2):
+        together = lb.lb_relax_shells(axes, starts, steps=60, precision=32, pair_search=search)
+        for s in (0, 7, 23, 39):
+            (alone,) = lb.lb_relax_shells([axes[s]], [starts[s]], steps=60, precision=32, pair_search=search)
+            assert np.array_equal(alone, together[s])
+
+
+def test_cell_list_falls_back_when_beads_leave_its_box():
+    """Beads started far outside the surface lie outside the cell grid's box
+    (1.25 a + 1): those steps test all pairs; the result matches the oracle."""
+    from paper_1604_01829_gb300 import lb, workloads as W
+    ax = (4.0, 3.0, 2.5)
+    X0 = W.spread_shell_start(*ax, 60, seed=3, jitter=0.02)
+    X0[:5] *= 1.9                                              # beyond 1.25 a + 1 on every axis
+    out = lb.lb_relax_shells([ax], [X0], steps=120, precision=64, project_final=False, pair_search=2)
+    ref = C.relax_shell(X0, ax, 120, project_final=False)
+    assert np.abs(out[0] - ref).max() <= 1e-9
 
 
 def test_long_relaxation_spreads_beads_evenly():
@@ -163,4 +183,10 @@ def test_argument_errors():
     assert e.value.status == lb.LB_ERR_ARG
     with pytest.raises(lb.LBError) as e:
         lb.lb_relax_shells([(1, 1, 1)], [X0], steps=1, precision=16)
+    assert e.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_relax_shells([(1, 1, 1)], [X0], steps=1, pair_search=3)
+    assert e.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError) as e:                     # FP64 cell list of 4096 beads: no room
+        lb.lb_relax_shells([(20, 20, 20)], [np.ones((4096, 3))], steps=1, precision=64, pair_search=2)
     assert e.value.status == lb.LB_ERR_ARG
