@@ -317,6 +317,7 @@ def run_ours(args, ws, rank, local):
 
     batched = None if args.skip_batched else measure_batched(args, torch, lb, barrier_max, ws)
     pore = None if args.skip_pore else measure_pore(torch, lb)
+    sphere32 = None if args.skip_pore else measure_sphere32(torch, lb)
     adjoint = None if args.skip_adjoint else measure_adjoint(args, torch, lb)
     construction = None if args.skip_construction else measure_construction(args, torch, lb)
 
@@ -359,6 +360,7 @@ def run_ours(args, ws, rank, local):
             "fp64": fp64_line,
             "batched": batched,
             "pore": pore,
+            "sphere32": sphere32,
             "adjoint": adjoint,
             "construction": construction,
             "clocks": main["clocks"],
@@ -467,22 +469,28 @@ def measure_pore(torch, lb, steps=2000):
     of 1.2e6 records (20 radial bins, 25 lags)."""
     import numpy as np
     from paper_1604_01829_gb300 import workloads as W
-    w = W.pore_48(offset_frac=0.4)
     stream = torch.cuda.Stream()
-    L = lb.from_workload(w, stream=stream.cuda_stream)
-    L.lb_set_pore_beads(5.0, 6.25, 0.5, w.params["kT"])
-    L.lb_record_bodies(200, 64)
-    L.lb_step(10)
-    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    L.lb_step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    rec = len(L.lb_get_trajectory(0)[0])
-    L.close()
+    timed = {}
+    for precision in (32, 64):
+        w = W.pore_48(offset_frac=0.4, precision=precision)
+        L = lb.from_workload(w, stream=stream.cuda_stream)
+        L.lb_set_pore_beads(5.0, 6.25, 0.5, w.params["kT"])
+        L.lb_record_bodies(200, 64)
+        L.lb_step(10)
+        torch.cuda.synchronize()
+        n_steps = steps if precision == 32 else steps // 10
+        e0.record(stream)
+        L.lb_step(n_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        timed[precision] = (e0.elapsed_time(e1), n_steps)
+        if precision == 32:
+            rec = len(L.lb_get_trajectory(0)[0])
+        L.close()
+    ms, _ = timed[32]
+    ms64, steps64 = timed[64]
     rng = np.random.default_rng(1611)
     n = 1_200_000
     X = np.empty((n, 3))
@@ -500,7 +508,36 @@ def measure_pore(torch, lb, steps=2000):
             "nodes": w.nodes, "steps": steps, "ms_per_step": round(ms / steps, 4),
             "value": round(w.nodes * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "l2": "state 34 MB fits in L2: MLUPS only", "records": rec,
+            "fp64": {"steps": steps64, "ms_per_step": round(ms64 / steps64, 4),
+                     "value": round(w.nodes * steps64 / (ms64 * 1e-3) / 1e6, 1), "unit": "MLUPS"},
             "pore_msd": {"records": n, "bins": 20, "lags": 25, "ms": round(sec * 1e3, 2)}}
+
+
+def measure_sphere32(torch, lb, steps=200):
+    """The small validation case: 32^3 periodic FP64 BGK tau = 1, one filled
+    sphere R = 3 (224 beads) pulled by a constant force, the drive compensated
+    on the fluid; 200 steps; L2-resident (MLUPS only). Also the conservation
+    check the case is for: total mass and momentum (fluid + body) after the
+    run."""
+    from paper_1604_01829_gb300 import workloads as W
+    w = W.sphere_32()
+    stream = torch.cuda.Stream()
+    L = lb.from_workload(w, stream=stream.cuda_stream)
+    L.lb_step(10)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.lb_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m, p = L.lb_conservation()
+    L.close()
+    return {"workload": w.name + ", sphere R = 3 (224 beads), F_ext 1e-4 compensated on the fluid",
+            "nodes": w.nodes, "steps": steps, "ms_per_step": round(ms / steps, 4),
+            "value": round(w.nodes * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "l2": "state 10 MB fits in L2: MLUPS only", "mass_rel_error": abs(m / w.nodes - 1.0)}
 
 
 def measure_msd(torch, lb, nbodies=256, nrec=4000, max_lag=400, seed=1610):

@@ -202,6 +202,16 @@ lb_status lb_info(lb_handle h, lb_info_t *info);
  * (0 = auto) the persistent grid. Results do not depend on the choice. */
 lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_per_sm);
 
+/* Limit, in SM clock cycles, of each bounded device wait (the TMA-staged
+ * kernel's wait for a stage's copies; 0 = the default of about 2 s). A wait
+ * that runs out stops its thread block (after its copies in flight have
+ * landed) and sets the handle's device error word; the next synchronising
+ * call (lb_forces, lb_forces_all, lb_conservation) returns LB_ERR_TIMEOUT once
+ * and clears it. The lattice state is then partly stepped and should be
+ * restored (lb_set_populations). No effect on the plain kernel, which does not
+ * wait. Errors: LB_ERR_ARG for cycles < 0. */
+lb_status lb_set_wait_limit(lb_handle h, long long cycles);
+
 /* Kernel timing: when on, CUDA events bracket every launch of the fused
  * collide-and-stream kernel on the handle's stream. lb_kernel_time returns
  * (synchronising) the summed device time in ms and the number of timed

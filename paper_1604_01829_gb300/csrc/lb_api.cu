@@ -132,12 +132,16 @@ lb_status push_bodies(lb_ctx *h) {
     return LB_OK;
 }
 
-// LB_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out (synchronises)
+// LB_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out since the
+// last check (synchronises; the error word is reset, so it is reported once)
 lb_status check_device_error(lb_ctx *h) {
     int e = 0;
     LB_CUDA(h, cudaMemcpyAsync(&e, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (e) return fail(h, LB_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy did not complete)");
+    if (e) {
+        LB_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+        return fail(h, LB_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy did not complete in time)");
+    }
     return LB_OK;
 }
 
@@ -230,7 +234,7 @@ lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
     }
     const bool tma = h->cs_variant == 2 && lbk::tma_collide_supported(h->g, h->fp32);
     cudaError_t e = tma ? lbk::launch_collide_stream_tma(a, h->p.collision, noise, odd, h->tma_stages, h->tma_ctas,
-                                                         h->stream)
+                                                         h->wait_limit, h->stream)
                         : lbk::launch_collide_stream(a, h->fp32, h->p.collision, noise, odd, h->block, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "collide_stream launch");
     if (h->timing) {
@@ -882,6 +886,13 @@ lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_p
     h->cs_variant = variant;
     h->tma_stages = stages;
     h->tma_ctas = ctas_per_sm;
+    return LB_OK;
+}
+
+lb_status lb_set_wait_limit(lb_handle h, long long cycles) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (cycles < 0) return fail(h, LB_ERR_ARG, "cycles must be >= 0 (0: the default of ~2 s)");
+    h->wait_limit = cycles;
     return LB_OK;
 }
 

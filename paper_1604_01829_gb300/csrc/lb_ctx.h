@@ -29,6 +29,7 @@ struct lb_ctx {
     lbk::WallBeads wall{};                  // pore-wall beads (lb_set_pore_beads)
     int cs_variant = 0;                     // collide kernel: 0 auto (plain), 1 plain, 2 TMA-staged
     int tma_stages = 0, tma_ctas = 0;       // 0 = library default
+    long long wait_limit = 0;               // bounded device waits, SM clock cycles (0: ~2 s)
     long long step = 0;                     // host mirror
     long long nfluid = 0;
     double sig[15] = {};

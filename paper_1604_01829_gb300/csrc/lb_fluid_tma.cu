@@ -19,9 +19,9 @@
 // update stays race-free although the reads happen rows ahead.
 //
 // Bounded waits: one thread per CTA waits on each stage's mbarrier with a
-// clock limit; on expiry it records an error code for the host, the CTA
-// stops, and before leaving it waits (again bounded) for its own copies
-// still in flight.
+// clock limit (lb_set_wait_limit, default ~2 s); on expiry it records an
+// error code for the host, the CTA stops, and before leaving it waits (bounded
+// by ~2 s whatever the limit) for its own copies still in flight.
 #include "lb_collide.cuh"
 
 namespace lbk {
@@ -60,11 +60,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// wait with a limit of ~2 s of SM clock; false on expiry
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// wait with a limit in SM clock cycles; false on expiry
+constexpr long long kDrainLimit = 4000000000LL;     // ~2 s: copies in flight after an abort
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 4000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -74,7 +75,8 @@ constexpr int kThreads = 256;
 #endif
 
 template <int COLL, bool NOISE, bool ODD>
-__global__ void __launch_bounds__(kThreads, LB_TMA_MINB) k_collide_stream_tma(const FluidArgs a, int stages) {
+__global__ void __launch_bounds__(kThreads, LB_TMA_MINB)
+    k_collide_stream_tma(const FluidArgs a, int stages, long long wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int abort_flag;
     const Geom &g = a.g;
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, LB_TMA_MINB) k_collide_stream_tma(co
     int done = 0;
     for (int k = 0; k < mine; ++k) {
         const int s = k % stages;
-        if (threadIdx.x == 0 && !mbar_wait_bounded(&bars[s], (uint32_t)((k / stages) & 1))) {
+        if (threadIdx.x == 0 && !mbar_wait_bounded(&bars[s], (uint32_t)((k / stages) & 1), wait_limit)) {
             abort_flag = 1;
             if (a.err) atomicExch(a.err, 1);
         }
@@ -183,16 +185,17 @@ __global__ void __launch_bounds__(kThreads, LB_TMA_MINB) k_collide_stream_tma(co
     if (threadIdx.x == 0 && abort_flag) {
         const int issued = mine < done + stages ? mine : done + stages;
         for (int k = done; k < issued; ++k)
-            mbar_wait_bounded(&bars[k % stages], (uint32_t)((k / stages) & 1));
+            mbar_wait_bounded(&bars[k % stages], (uint32_t)((k / stages) & 1), kDrainLimit);
     }
 }
 
 template <int COLL, bool NOISE>
-cudaError_t launch_tma_t(const FluidArgs &a, bool odd, int stages, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_tma_t(const FluidArgs &a, bool odd, int stages, int grid, size_t smem, long long wait_limit,
+                         cudaStream_t s) {
     auto kern = odd ? k_collide_stream_tma<COLL, NOISE, true> : k_collide_stream_tma<COLL, NOISE, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, smem, s>>>(a, stages);
+    kern<<<grid, kThreads, smem, s>>>(a, stages, wait_limit);
     return cudaGetLastError();
 }
 
@@ -203,7 +206,7 @@ bool tma_collide_supported(const Geom &g, bool fp32) {
 }
 
 cudaError_t launch_collide_stream_tma(const FluidArgs &a, int collision, bool noise, bool odd, int stages_hint,
-                                      int ctas_per_sm_hint, cudaStream_t s) {
+                                      int ctas_per_sm_hint, long long wait_limit, cudaStream_t s) {
     if (!tma_collide_supported(a.g, true)) return cudaErrorNotSupported;
     const size_t row_stage = 19ull * a.g.nx * 4ull;
     int stages = stages_hint > 0 ? stages_hint : (int)(100000 / row_stage);
@@ -218,9 +221,10 @@ cudaError_t launch_collide_stream_tma(const FluidArgs &a, int collision, bool no
     const int rows = a.g.ny * a.g.nz;
     int grid = sms * (per_sm > 0 ? per_sm : 1);
     if (grid > rows) grid = rows;
-    if (collision == 0) return launch_tma_t<0, false>(a, odd, stages, grid, smem, s);
-    if (noise) return launch_tma_t<1, true>(a, odd, stages, grid, smem, s);
-    return launch_tma_t<1, false>(a, odd, stages, grid, smem, s);
+    if (wait_limit <= 0) wait_limit = kDrainLimit;
+    if (collision == 0) return launch_tma_t<0, false>(a, odd, stages, grid, smem, wait_limit, s);
+    if (noise) return launch_tma_t<1, true>(a, odd, stages, grid, smem, wait_limit, s);
+    return launch_tma_t<1, false>(a, odd, stages, grid, smem, wait_limit, s);
 }
 
 }  // namespace lbk

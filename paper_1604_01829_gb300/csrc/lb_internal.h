@@ -118,8 +118,10 @@ bool tma_collide_supported(const Geom &g, bool fp32);
 long long pore_section_size(const Geom &g);
 // wall masks of a pore geometry into out[pore_section_size(g)]
 cudaError_t launch_build_masks(const Geom &g, uint32_t *out, cudaStream_t s);
+// wait_limit: SM clock cycles a stage's wait may take before the launch gives up
+// (error word set); <= 0 selects ~2 s
 cudaError_t launch_collide_stream_tma(const FluidArgs &a, int collision, bool noise, bool odd, int stages_hint,
-                                      int ctas_per_sm_hint, cudaStream_t s);
+                                      int ctas_per_sm_hint, long long wait_limit, cudaStream_t s);
 cudaError_t launch_gather(const void *f, bool fp32, const Geom &g, bool odd, double rho0, double *out,
                           cudaStream_t s);
 cudaError_t launch_scatter(void *f, bool fp32, const Geom &g, bool odd, double rho0, const double *in,

@@ -67,6 +67,7 @@ _SIGS = {
     "lb_info": [C.c_void_p, C.POINTER(lb_info_t)],
     "lb_set_timing": [C.c_void_p, C.c_int],
     "lb_set_kernel_variant": [C.c_void_p, C.c_int, C.c_int, C.c_int],
+    "lb_set_wait_limit": [C.c_void_p, C.c_longlong],
     "lb_adjoint_drag": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
     "lb_record_bodies": [C.c_void_p, C.c_int, C.c_int],
@@ -383,6 +384,9 @@ class LB:
 
     def lb_set_kernel_variant(self, variant=0, stages=0, ctas_per_sm=0):
         _check(self.h, load().lb_set_kernel_variant(self.h, int(variant), int(stages), int(ctas_per_sm)))
+
+    def lb_set_wait_limit(self, cycles=0):
+        _check(self.h, load().lb_set_wait_limit(self.h, int(cycles)))
 
     def lb_set_timing(self, on=True):
         _check(self.h, load().lb_set_timing(self.h, int(bool(on))))

@@ -182,6 +182,34 @@ def test_fp32_kernel_variants(variant, case, steps):
     assert P.pop_error() <= TOL[32]
 
 
+def test_bounded_wait_runs_out_and_is_reported():
+    """Failure detection without a fault: the TMA-staged kernel's stage waits
+    get a limit (16 SM cycles) far below the copy latency, so they run out; the
+    blocks stop once their copies in flight have landed and the next
+    synchronising call returns LB_ERR_TIMEOUT, once. The context stays usable:
+    with the default limit and the state restored, further steps match the
+    oracle."""
+    from paper_1604_01829_gb300 import lb
+    P = Pair(64, 24, 20, precision=32, **dict(MRT, kT=1e-4, seed=5))
+    P.set_populations(perturbed_populations(P.N, seed=3))
+    P.gpu.lb_set_kernel_variant(2)
+    P.gpu.lb_set_wait_limit(16)
+    P.step(1)
+    with pytest.raises(lb.LBError) as e:
+        P.gpu.lb_conservation()
+    assert e.value.status == lb.LB_ERR_TIMEOUT
+    P.gpu.lb_conservation()                                   # reported once
+    with pytest.raises(lb.LBError):
+        P.gpu.lb_set_wait_limit(-1)
+    P.gpu.lb_set_wait_limit(0)
+    P.gpu.lb_set_populations(P.orc.populations())             # the oracle's state after the same step
+    P.step(4)
+    assert P.pop_error() <= TOL[32]
+    m, _ = P.gpu.lb_conservation()
+    m_orc = float(P.orc.populations().sum())
+    assert abs(m / m_orc - 1.0) < 1e-6
+
+
 @pytest.mark.parametrize("stages,ctas", [(2, 1), (3, 2), (6, 1)])
 def test_tma_ring_depths_with_coupling(stages, ctas):
     """TMA-staged kernel with bead forces in flagged tiles, several ring
