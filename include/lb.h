@@ -202,6 +202,26 @@ lb_status lb_info(lb_handle h, lb_info_t *info);
  * (0 = auto) the persistent grid. Results do not depend on the choice. */
 lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_per_sm);
 
+/* Checkpoint and resume. A checkpoint holds the whole state a later step
+ * depends on: the populations in the storage precision (bit for bit), the
+ * step counter (which is also the Philox counter of the noise), every body's
+ * state, the per-bead forces, and the spread-force buffers with their tile
+ * flags and lists (the previous step's force enters the next interpolation).
+ * Loading it into a handle created with the same parameters (lattice,
+ * precision, collision, seed, pore or walls) and the same bodies and beads
+ * resumes the run exactly: the same steps then give the same results, up to
+ * the summation order of the bead-force atomics. The trajectory recorder is
+ * not part of a checkpoint. lb_checkpoint_size: bytes needed (uploads the
+ * bodies on the first call); lb_checkpoint_save: into a caller-owned host
+ * buffer of at least that size (synchronises); lb_checkpoint_load: from such
+ * a buffer. Errors: LB_ERR_ARG (null or short buffer, not a checkpoint),
+ * LB_ERR_STATE (taken from a lattice with other parameters or bodies),
+ * LB_ERR_CUDA. The layout is this library's own and may change between
+ * versions. */
+lb_status lb_checkpoint_size(lb_handle h, size_t *bytes);
+lb_status lb_checkpoint_save(lb_handle h, void *host, size_t bytes);
+lb_status lb_checkpoint_load(lb_handle h, const void *host, size_t bytes);
+
 /* Limit, in SM clock cycles, of each bounded device wait (the TMA-staged
  * kernel's wait for a stage's copies; 0 = the default of about 2 s). A wait
  * that runs out stops its thread block (after its copies in flight have

@@ -889,6 +889,118 @@ lb_status lb_set_kernel_variant(lb_handle h, int variant, int stages, int ctas_p
     return LB_OK;
 }
 
+// ------------------------------------------------------------- checkpoints
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    int nx, ny, nz, precision, collision, nbodies, nbeads, pore_axis, chan, list_cap;
+    double pore_R;
+    unsigned long long seed;
+    long long step, ntiles;
+    unsigned long long body_bytes, total;
+};
+
+// the sections of a checkpoint: device pointer and bytes, in file order
+std::vector<std::pair<void *, size_t>> ckpt_sections(lb_ctx *h) {
+    std::vector<std::pair<void *, size_t>> v;
+    const size_t es = h->fp32 ? 4 : 8;
+    v.push_back({h->f, 19 * es * (size_t)h->g.N});
+    const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
+    if (nb > 0) {
+        v.push_back({h->db, sizeof(Body) * nb});
+        v.push_back({h->dFbead, sizeof(double) * 3 * (size_t)std::max(nbeads, 1)});
+        const size_t ntiles = (size_t)h->ntx * h->nty * h->ntz;
+        for (int k = 0; k < 2; ++k) {
+            v.push_back({h->Fbuf[k], 3 * es * (size_t)h->g.N});
+            v.push_back({h->tiles[k], sizeof(int) * ntiles});
+            v.push_back({h->tlist[k], sizeof(int) * (size_t)h->list_cap});
+            v.push_back({h->tcount[k], sizeof(int)});
+        }
+    }
+    return v;
+}
+
+CkptHeader ckpt_header(lb_ctx *h) {
+    CkptHeader c{};
+    std::memcpy(c.magic, "LBCKPT1", 8);
+    c.nx = h->g.nx; c.ny = h->g.ny; c.nz = h->g.nz;
+    c.precision = h->fp32 ? 32 : 64;
+    c.collision = h->p.collision;
+    c.nbodies = (int)h->hb.size();
+    c.nbeads = (int)h->hbody_of.size();
+    c.pore_axis = h->g.pore_axis;
+    c.chan = h->g.chan;
+    c.list_cap = h->list_cap;
+    c.pore_R = h->pore_R;
+    c.seed = h->p.seed;
+    c.step = h->step;
+    c.ntiles = (long long)h->ntx * h->nty * h->ntz;
+    c.body_bytes = sizeof(Body);
+    size_t total = sizeof(CkptHeader);
+    for (auto &s : ckpt_sections(h)) total += s.second;
+    c.total = total;
+    return c;
+}
+
+}  // namespace
+
+lb_status lb_checkpoint_size(lb_handle h, size_t *bytes) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!bytes) return fail(h, LB_ERR_ARG, "null argument");
+    lb_status s = upload_bodies(h);
+    if (s != LB_OK) return s;
+    *bytes = (size_t)ckpt_header(h).total;
+    return LB_OK;
+}
+
+lb_status lb_checkpoint_save(lb_handle h, void *host, size_t bytes) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!host) return fail(h, LB_ERR_ARG, "null buffer");
+    lb_status s = upload_bodies(h);
+    if (s != LB_OK) return s;
+    const CkptHeader c = ckpt_header(h);
+    if (bytes < c.total) return fail(h, LB_ERR_ARG, "buffer smaller than lb_checkpoint_size");
+    char *p = static_cast<char *>(host);
+    std::memcpy(p, &c, sizeof(c));
+    p += sizeof(c);
+    for (auto &sec : ckpt_sections(h)) {
+        LB_CUDA(h, cudaMemcpyAsync(p, sec.first, sec.second, cudaMemcpyDeviceToHost, h->stream));
+        p += sec.second;
+    }
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return check_device_error(h);
+}
+
+lb_status lb_checkpoint_load(lb_handle h, const void *host, size_t bytes) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    if (!host || bytes < sizeof(CkptHeader)) return fail(h, LB_ERR_ARG, "buffer too small for a checkpoint");
+    CkptHeader c;
+    std::memcpy(&c, host, sizeof(c));
+    if (std::memcmp(c.magic, "LBCKPT1", 8) != 0) return fail(h, LB_ERR_ARG, "not a checkpoint of this library");
+    lb_status s = upload_bodies(h);
+    if (s != LB_OK) return s;
+    const CkptHeader mine = ckpt_header(h);
+    if (c.nx != mine.nx || c.ny != mine.ny || c.nz != mine.nz || c.precision != mine.precision ||
+        c.collision != mine.collision || c.nbodies != mine.nbodies || c.nbeads != mine.nbeads ||
+        c.pore_axis != mine.pore_axis || c.chan != mine.chan || c.list_cap != mine.list_cap ||
+        c.pore_R != mine.pore_R || c.seed != mine.seed || c.ntiles != mine.ntiles ||
+        c.body_bytes != mine.body_bytes || c.total != mine.total)
+        return fail(h, LB_ERR_STATE, "the checkpoint was taken from a lattice with other parameters or bodies");
+    if (bytes < c.total) return fail(h, LB_ERR_ARG, "buffer shorter than the checkpoint");
+    drop_graph(h);
+    const char *p = static_cast<const char *>(host) + sizeof(c);
+    for (auto &sec : ckpt_sections(h)) {
+        LB_CUDA(h, cudaMemcpyAsync(sec.first, p, sec.second, cudaMemcpyHostToDevice, h->stream));
+        p += sec.second;
+    }
+    const unsigned long long st = (unsigned long long)c.step;
+    LB_CUDA(h, cudaMemcpyAsync(h->step_dev, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->step = c.step;
+    return LB_OK;
+}
+
 lb_status lb_set_wait_limit(lb_handle h, long long cycles) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
     if (cycles < 0) return fail(h, LB_ERR_ARG, "cycles must be >= 0 (0: the default of ~2 s)");

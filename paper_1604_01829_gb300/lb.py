@@ -68,6 +68,9 @@ _SIGS = {
     "lb_set_timing": [C.c_void_p, C.c_int],
     "lb_set_kernel_variant": [C.c_void_p, C.c_int, C.c_int, C.c_int],
     "lb_set_wait_limit": [C.c_void_p, C.c_longlong],
+    "lb_checkpoint_size": [C.c_void_p, C.POINTER(C.c_size_t)],
+    "lb_checkpoint_save": [C.c_void_p, C.c_void_p, C.c_size_t],
+    "lb_checkpoint_load": [C.c_void_p, C.c_void_p, C.c_size_t],
     "lb_adjoint_drag": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
     "lb_record_bodies": [C.c_void_p, C.c_int, C.c_int],
@@ -384,6 +387,18 @@ class LB:
 
     def lb_set_kernel_variant(self, variant=0, stages=0, ctas_per_sm=0):
         _check(self.h, load().lb_set_kernel_variant(self.h, int(variant), int(stages), int(ctas_per_sm)))
+
+    def lb_checkpoint_save(self):
+        """The handle's full state as bytes (see lb_checkpoint_* in include/lb.h)."""
+        n = C.c_size_t()
+        _check(self.h, load().lb_checkpoint_size(self.h, C.byref(n)))
+        buf = (C.c_char * n.value)()
+        _check(self.h, load().lb_checkpoint_save(self.h, buf, n.value))
+        return bytes(buf)
+
+    def lb_checkpoint_load(self, data):
+        buf = C.create_string_buffer(bytes(data), len(data))
+        _check(self.h, load().lb_checkpoint_load(self.h, buf, len(data)))
 
     def lb_set_wait_limit(self, cycles=0):
         _check(self.h, load().lb_set_wait_limit(self.h, int(cycles)))

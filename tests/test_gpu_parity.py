@@ -182,6 +182,52 @@ def test_fp32_kernel_variants(variant, case, steps):
     assert P.pop_error() <= TOL[32]
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_checkpoint_resume(precision):
+    """A checkpoint taken at an odd step count and loaded into a fresh handle
+    with the same parameters and bodies resumes the run: without bodies bit
+    for bit (the noise is counter-based), with a body up to the order of the
+    bead-force atomics. A checkpoint of another lattice is refused."""
+    from paper_1604_01829_gb300 import lb
+    params = dict(MRT, kT=1e-4, seed=21, gamma_bead=Wl.paper_gamma_to_lattice(50.0), precision=precision)
+    f0 = perturbed_populations(40 * 20 * 18, seed=5)
+    q = np.array([0.9, 0.2, -0.3, 0.1]) / np.linalg.norm([0.9, 0.2, -0.3, 0.1])
+    ell = Wl.ellipsoid_raspberry(4.0, 2.0, 2.0, seed=2)
+    m = 4.0 / 3.0 * math.pi * 16.0
+
+    def make(with_body):
+        g = lb.LB(40, 20, 18, **params)
+        if with_body:
+            g.lb_add_raspberry(ell, [20.3, 9.7, 8.8], q, m, tuple(Wl.solid_ellipsoid_inertia(m, 4.0, 2.0, 2.0)),
+                               (1e-3, 0, 0))
+        return g
+
+    for with_body in (False, True):
+        a = make(with_body)
+        a.lb_set_populations(f0)
+        a.lb_step(7)
+        ck = a.lb_checkpoint_save()
+        a.lb_step(6)
+        b = make(with_body)
+        b.lb_checkpoint_load(ck)
+        b.lb_step(6)
+        fa, fb = a.lb_get_populations(), b.lb_get_populations()
+        assert a.lb_info()["step"] == b.lb_info()["step"] == 13
+        if not with_body:
+            assert np.array_equal(fa, fb)
+        else:
+            d = (np.abs(fa - fb).max(axis=1) / W19).max()
+            assert d <= (1e-13 if precision == 64 else 1e-6), d
+            xa, xb = a.lb_get_body(0)["X"], b.lb_get_body(0)["X"]
+            assert np.abs(xa - xb).max() <= (1e-12 if precision == 64 else 1e-7)
+        other = lb.LB(40, 20, 16, **params)
+        with pytest.raises(lb.LBError) as e:
+            other.lb_checkpoint_load(ck)
+        assert e.value.status == lb.LB_ERR_STATE
+        for g in (a, b, other):
+            g.close()
+
+
 def test_bounded_wait_runs_out_and_is_reported():
     """Failure detection without a fault: the TMA-staged kernel's stage waits
     get a limit (16 SM cycles) far below the copy latency, so they run out; the
