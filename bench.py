@@ -270,10 +270,9 @@ def run_ours(args, ws, rank, local):
     # and torque back (D2H)
     L, w = main["L"], main["w"]
     nb = len(w.bodies)
-    Fext = np.zeros(3 * nb)
-    Text = np.zeros(3 * nb)
-    Fout = np.zeros(3 * nb)
-    Tout = np.zeros(3 * nb)
+    # page-locked host buffers (torch pins them; numpy views share the memory)
+    pinned = [torch.zeros(3 * nb, dtype=torch.float64).pin_memory() for _ in range(4)]
+    Fext, Text, Fout, Tout = (t.numpy() for t in pinned)
     e2e_steps = 0 if args.no_e2e else max(10, min(K, 200))
     torch.cuda.synchronize()
     t0 = time.perf_counter()

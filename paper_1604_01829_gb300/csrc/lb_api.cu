@@ -132,12 +132,14 @@ lb_status push_bodies(lb_ctx *h) {
     return LB_OK;
 }
 
-// LB_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out since the
-// last check (synchronises; the error word is reset, so it is reported once)
+// Synchronises the stream (completing the copies the caller queued before)
+// and returns LB_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out
+// since the last check (the error word is reset, so it is reported once).
+// The error word travels in the same synchronisation as the caller's copies.
 lb_status check_device_error(lb_ctx *h) {
-    int e = 0;
-    LB_CUDA(h, cudaMemcpyAsync(&e, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int e = *h->err_host;
     if (e) {
         LB_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
         return fail(h, LB_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy did not complete in time)");
@@ -341,7 +343,8 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
         if (e != cudaSuccess) { lb_status s = cuda_fail(nullptr, e, "cudaStreamCreate"); delete h; return s; }
         h->own_stream = true;
     }
-    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    e = cudaMallocHost((void **)&h->err_host, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -395,6 +398,7 @@ lb_status lb_destroy(lb_handle h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->err_host) cudaFreeHost(h->err_host);
     delete h;
     return LB_OK;
 }
@@ -732,7 +736,6 @@ lb_status lb_forces(lb_handle h, int id, double F[3], double T[3], double *per_b
     if (per_bead && b1 > b0)
         LB_CUDA(h, cudaMemcpyAsync(per_bead, h->dFbead + 3 * (size_t)b0, sizeof(double) * 3 * (b1 - b0),
                                    cudaMemcpyDeviceToHost, h->stream));
-    LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return check_device_error(h);
 }
 
@@ -749,7 +752,6 @@ lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T) {
                                         nbodies, cudaMemcpyDeviceToHost, h->stream));
     if (T) LB_CUDA(h, cudaMemcpy2DAsync(T, 3 * sizeof(double), &h->db[0].T_tot[0], sizeof(Body), 3 * sizeof(double),
                                         nbodies, cudaMemcpyDeviceToHost, h->stream));
-    LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return check_device_error(h);
 }
 
@@ -850,7 +852,6 @@ lb_status lb_conservation(lb_handle h, double *mass, double mom[3]) {
     cudaError_t e = lbk::launch_moments(h->f, h->fp32, h->g, (h->step & 1) != 0, h->partials, h->red_blocks,
                                         h->out4, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(o, h->out4, sizeof(o), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lb_conservation");
     lb_status de = check_device_error(h);
     if (de != LB_OK) return de;
@@ -968,7 +969,6 @@ lb_status lb_checkpoint_save(lb_handle h, void *host, size_t bytes) {
         LB_CUDA(h, cudaMemcpyAsync(p, sec.first, sec.second, cudaMemcpyDeviceToHost, h->stream));
         p += sec.second;
     }
-    LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return check_device_error(h);
 }
 

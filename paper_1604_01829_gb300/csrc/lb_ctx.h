@@ -23,6 +23,7 @@ struct lb_ctx {
     float *gforce_f = nullptr;              // device (3), FP32 copy
     unsigned long long *step_dev = nullptr; // device step counter
     int *err_dev = nullptr;                 // device error word of bounded waits
+    int *err_host = nullptr;                // pinned host copy of it (read in the caller's synchronisation)
     uint32_t *dmask = nullptr;              // pore wall masks across the axis (launch_build_masks)
     double pore_R = 0.0;                    // pore radius (lb_set_pore)
     double *dwchan = nullptr;               // channel walls: Geom::wchan
