@@ -208,6 +208,11 @@ void drop_graph(lb_ctx *h) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
     }
+    for (auto &g : h->gexec1)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
 }
 
 lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
@@ -677,20 +682,23 @@ lb_status eager_steps(lb_ctx *h, int n) {
     return s;
 }
 
-// an even and an odd step as one CUDA graph, replayed from even step counts
-lb_status ensure_graph(lb_ctx *h) {
-    if (h->gexec) return LB_OK;
+// An even and an odd step as one CUDA graph, replayed from even step counts
+// (n = 2); one step from the current parity as its own graph (n = 1), so a
+// caller stepping one step at a time submits one launch per step.
+lb_status ensure_graph(lb_ctx *h, int n = 2) {
+    cudaGraphExec_t &slot = n == 2 ? h->gexec : h->gexec1[h->step & 1];
+    if (slot) return LB_OK;
     cudaGraph_t graph = nullptr;
     LB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    lb_status s = launch_steps(h, 2);
-    if (s == LB_OK) s = finish_group(h, 2);
+    lb_status s = launch_steps(h, n);
+    if (s == LB_OK) s = finish_group(h, n);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (s != LB_OK) {
         if (graph) cudaGraphDestroy(graph);
         return s;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
-    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    e = cudaGraphInstantiate(&slot, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
     return LB_OK;
@@ -704,8 +712,17 @@ lb_status lb_step(lb_handle h, int nsteps) {
     if (nsteps == 0) return LB_OK;
     lb_status s = upload_bodies(h);
     if (s != LB_OK) return s;
-    // short calls, timed kernels and the TMA variant launch step by step
-    if (nsteps < 4 || h->timing || h->cs_variant == 2) return eager_steps(h, nsteps);
+    // timed kernels and the TMA variant launch step by step; short calls
+    // replay single-step graphs
+    if (h->timing || h->cs_variant == 2) return eager_steps(h, nsteps);
+    if (nsteps < 4) {
+        for (int k = 0; k < nsteps; ++k) {
+            if ((s = ensure_graph(h, 1)) != LB_OK) return s;
+            LB_CUDA(h, cudaGraphLaunch(h->gexec1[h->step & 1], h->stream));
+            h->step += 1;
+        }
+        return LB_OK;
+    }
     if (h->step & 1) {
         if ((s = eager_steps(h, 1)) != LB_OK) return s;
         --nsteps;
