@@ -228,6 +228,36 @@ def test_checkpoint_resume(precision):
             g.close()
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_run_to_run_nondeterminism_is_bounded(precision):
+    """The same coupled run twice: bead forces are summed onto nodes and bodies
+    by atomics in arbitrary order, so results may differ in the last bits;
+    over 20 steps the populations stay within 1e-14 w_i (FP64) / 1e-6 w_i
+    (FP32) of each other. The fluid alone (no atomics, counter-based noise)
+    repeats bit for bit."""
+    from paper_1604_01829_gb300 import lb
+    params = dict(MRT, kT=1e-4, seed=31, gamma_bead=Wl.paper_gamma_to_lattice(50.0), precision=precision)
+    f0 = perturbed_populations(48 * 20 * 18, seed=8)
+    ell = Wl.ellipsoid_raspberry(4.0, 2.0, 2.0, seed=3)
+    m = 4.0 / 3.0 * math.pi * 16.0
+    q = np.array([0.8, 0.1, 0.5, -0.2]) / np.linalg.norm([0.8, 0.1, 0.5, -0.2])
+
+    def run(with_body):
+        g = lb.LB(48, 20, 18, **params)
+        g.lb_set_populations(f0)
+        if with_body:
+            g.lb_add_raspberry(ell, [22.6, 9.3, 8.1], q, m, tuple(Wl.solid_ellipsoid_inertia(m, 4.0, 2.0, 2.0)),
+                               (1e-3, 5e-4, 0))
+        g.lb_step(20)
+        f = g.lb_get_populations()
+        g.close()
+        return f
+
+    assert np.array_equal(run(False), run(False))
+    d = (np.abs(run(True) - run(True)).max(axis=1) / W19).max()
+    assert d <= (1e-14 if precision == 64 else 1e-6), d
+
+
 def test_bounded_wait_runs_out_and_is_reported():
     """Failure detection without a fault: the TMA-staged kernel's stage waits
     get a limit (16 SM cycles) far below the copy latency, so they run out; the

@@ -16,7 +16,10 @@ ABI against closed forms of Stokes flow:
   same unbounded drag as a pulled raspberry in a periodic box extrapolated
   by Hasimoto's law.
 
-All runs: BGK tau = 1 (nu = 1/6), FP64, deterministic fluid (kT = 0)."""
+* the fluctuating fluid: node velocity variance kT/rho0 per component and the
+  stationary variance 3 rho0 kT b_k of every non-conserved mode.
+
+The drag runs: BGK tau = 1 (nu = 1/6), FP64, deterministic fluid (kT = 0)."""
 import math
 
 import numpy as np
@@ -193,3 +196,34 @@ def test_stokes_flow_set_up_gives_the_unbounded_drag():
     mass = 4.0 / 3.0 * math.pi * 8.0
     xi0_pulled = _unbounded([_pulled_drag(L, beads, mass, 0) for L in Ls], Ls)
     assert abs(xi0_stokes / xi0_pulled - 1) < 0.01, (xs, xi0_stokes, xi0_pulled)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_fluctuating_fluid_thermalises_on_the_cuda_path(precision):
+    """Fluctuating MRT (Sec. 1.1, stochastic mode; 16-bit Philox variates) on
+    the CUDA path: after a warm-up the node velocity variance per component is
+    kT/rho0, and every non-conserved mode k has the stationary variance
+    3 rho0 kT b_k (b_k the mode norm). The mode basis and norms are the
+    oracle's (Gram-Schmidt of the DSL polynomials)."""
+    from oracle import oracle as O
+    from paper_1604_01829_gb300 import lb
+    kT, L = 1e-4, 24
+    rates = dict(collision=1, gamma_shear=-0.5, gamma_bulk=-0.3, gamma_odd=0.0, gamma_even=0.0)
+    h = lb.LB(L, L, L, precision=precision, kT=kT, seed=4242, **rates)
+    M, _, b = O.mrt_tables()
+    c = np.array(O.lattice()[0], dtype=np.float64)
+    h.lb_step(400)
+    u2, mv = [], []
+    for _ in range(40):
+        h.lb_step(7)
+        f = h.lb_get_populations()
+        rho = f.sum(axis=0)
+        u = (c.T @ f) / rho
+        u2.append(((u - u.mean(axis=1, keepdims=True)) ** 2).mean(axis=1))
+        m = M @ f
+        mv.append((m[4:] ** 2).mean(axis=1))
+    h.close()
+    u2 = np.mean(u2, axis=0)
+    assert np.all(np.abs(u2 / kT - 1.0) < 0.03), u2 / kT
+    ratio = np.mean(mv, axis=0) / (3.0 * kT * b[4:])
+    assert np.all(np.abs(ratio - 1.0) < 0.03), ratio
