@@ -140,6 +140,10 @@ lb_status check_device_error(lb_ctx *h) {
     LB_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
     const int e = *h->err_host;
+    if (e & 2) {
+        LB_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+        return fail(h, LB_ERR_STATE, "an index check of the checked build failed (an index outside its array)");
+    }
     if (e) {
         LB_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
         return fail(h, LB_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy did not complete in time)");
@@ -623,6 +627,10 @@ lb_status launch_step_coupling(lb_ctx *h, int k) {
     c.instance = h->p.instance;
     c.step_base = h->step_dev;
     c.step_off = (uint32_t)k;
+    c.err = h->err_dev;
+    c.ntiles = (long long)h->ntx * h->nty * h->ntz;
+    c.list_cap = h->list_cap;
+    c.nbodies = (int)h->hb.size();
     cudaError_t e = lbk::launch_couple(c, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "couple launch");
     e = lbk::launch_wall_beads(h->wall, h->db, h->ds, h->dbody_of, nbeads, h->stream);

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     // lanes of inactive groups borrow bead 0's instance (they do no work)
     const int kk = active ? k : 0;
     const BInst &I = b.inst[b.bodies[b.bead_body[kk]].inst];
-    CoupleArgs a;
+    CoupleArgs a{};
     a.g = I.g;
     a.f = static_cast<const T *>(b.pool) + I.off;
     a.fp32 = b.fp32;
@@ -247,6 +247,11 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.bodies = b.bodies;
     a.F_bead = b.F_bead;
     a.nbeads = b.nbeads;
+    // the batched handle has no device error word: index checks of checked
+    // builds cover the single-lattice kernels; no bound here
+    a.ntiles = 1LL << 62;
+    a.list_cap = 0x7fffffff;
+    a.nbodies = 0x7fffffff;
     a.key0 = I.key0;
     a.key1 = I.key1;
     a.instance = I.instance;

@@ -13,7 +13,7 @@ namespace lbk {
 // walls go through load_pre (wall and moving-wall tests per link).
 template <typename R, typename T>
 __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int y, int z, long long n,
-                                           bool odd, R rho0, R &rho, R j[3]) {
+                                           bool odd, R rho0, R &rho, R j[3], int *err = nullptr) {
     R v[19];
     if (g.pore_axis < 0 && !g.chan) {
         const int nx = g.nx, nxy = g.nx * g.ny;
@@ -22,12 +22,12 @@ __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int
         const int zo[3] = {((z == 0 ? g.nz : z) - 1) * nxy, z * nxy, (z + 1 == g.nz ? 0 : z + 1) * nxy};
         if (!odd) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) v[i] = (R)A[(long long)i * g.N + n];
+            for (int i = 0; i < 19; ++i) v[i] = (R)A[(long long)i * g.N + chk(n, g.N, err)];
         } else {
-            v[0] = (R)A[n];
+            v[0] = (R)A[chk(n, g.N, err)];
 #pragma unroll
             for (int i = 1; i < 19; ++i)
-                v[i] = (R)A[(long long)opp(i) * g.N + (unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)])];
+                v[i] = (R)A[(long long)opp(i) * g.N + chk((unsigned)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]), g.N, err)];
         }
     } else {
 #pragma unroll
@@ -117,7 +117,7 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
                                                 bool active) {
     const Geom &g = a.g;
     const float *A = static_cast<const float *>(a.f);
-    const int body = active ? a.bead_body[k] : -1;
+    const int body = active ? chk(a.bead_body[chk(k, a.nbeads, a.err)], a.nbodies, a.err) : -1;
     const Body *Bp = active ? &a.bodies[body] : nullptr;
 
     float rel[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
@@ -152,14 +152,14 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
             wt *= o[q] ? fr : 1.f - fr;
         }
     }
-    const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
+    const long long n = chk(nidx(g, xyz[0], xyz[1], xyz[2]), g.N, a.err);
     const bool fluid = active && ywall < 0 && !is_wall(g, xyz[0], xyz[1], xyz[2]);
     float ub[3] = {0.f, 0.f, 0.f};
     if (active && ywall >= 0)            // a node beyond a moving wall carries the wall's velocity
         for (int q = 0; q < 3; ++q) ub[q] = wt * (float)g.wchan[38 + 3 * ywall + q];
     if (fluid) {                         // wall nodes carry u = 0
         float rho, j[3];
-        node_rho_j<float>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (float)a.rho0, rho, j);
+        node_rho_j<float>(A, g, xyz[0], xyz[1], xyz[2], chk(n, g.N, a.err), a.odd, (float)a.rho0, rho, j, a.err);
         const float ir = 1.f / rho;
         const float *Fp = static_cast<const float *>(a.Fprev);
         ub[0] = wt * ((j[0] + 0.5f * (a.gforce_f[0] + Fp[n])) * ir);
@@ -190,8 +190,9 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
         atomicAdd(&Fc[n], -wt * Fb[0]);
         atomicAdd(&Fc[g.N + n], -wt * Fb[1]);
         atomicAdd(&Fc[2 * g.N + n], -wt * Fb[2]);
-        const int tile = (int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty);
-        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0) a.tlist[atomicAdd(a.tcount, 1)] = a.tile_base + tile;
+        const int tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
+        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0)
+            a.tlist[chk(atomicAdd(a.tcount, 1), a.list_cap, a.err)] = a.tile_base + tile;
     }
 
     // force and torque: FP32 sums over the (up to 4) beads of the warp's first
@@ -234,7 +235,7 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
     using R = T;
     const Geom &g = a.g;
     const T *A = static_cast<const T *>(a.f);
-    const int body = active ? a.bead_body[k] : -1;
+    const int body = active ? chk(a.bead_body[chk(k, a.nbeads, a.err)], a.nbodies, a.err) : -1;
 
     double rel[3] = {0, 0, 0}, r[3] = {0, 0, 0}, v[3] = {0, 0, 0};
     if (active && c == 0) {
@@ -268,14 +269,14 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
         xyz[q] = o[q] ? (b0 + 1 == n3[q] ? 0 : b0 + 1) : b0;
         wt *= o[q] ? fr : R(1) - fr;
     }
-    const long long n = nidx(g, xyz[0], xyz[1], xyz[2]);
+    const long long n = chk(nidx(g, xyz[0], xyz[1], xyz[2]), g.N, a.err);
     const bool fluid = active && ywall < 0 && !is_wall(g, xyz[0], xyz[1], xyz[2]);
     R ub[3] = {R(0), R(0), R(0)};
     if (active && ywall >= 0)            // a node beyond a moving wall carries the wall's velocity
         for (int q = 0; q < 3; ++q) ub[q] = wt * (R)g.wchan[38 + 3 * ywall + q];
     if (fluid) {                         // wall nodes carry u = 0
         R rho, j[3];
-        node_rho_j<R>(A, g, xyz[0], xyz[1], xyz[2], n, a.odd, (R)a.rho0, rho, j);
+        node_rho_j<R>(A, g, xyz[0], xyz[1], xyz[2], chk(n, g.N, a.err), a.odd, (R)a.rho0, rho, j, a.err);
         const R ir = R(1) / rho;
         const T *Fp = static_cast<const T *>(a.Fprev);
         R gx, gy, gz;
@@ -313,9 +314,10 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
         atomicAdd(&Fc[n], -wt * (T)Fb[0]);
         atomicAdd(&Fc[g.N + n], -wt * (T)Fb[1]);
         atomicAdd(&Fc[2 * g.N + n], -wt * (T)Fb[2]);
-        const int tile = (int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty);
+        const int tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
         // first flag of a tile also records it for clearing two steps later
-        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0) a.tlist[atomicAdd(a.tcount, 1)] = a.tile_base + tile;
+        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0)
+            a.tlist[chk(atomicAdd(a.tcount, 1), a.list_cap, a.err)] = a.tile_base + tile;
     }
 
     // force and torque on the body: sum the (up to 4) beads of this warp

@@ -77,6 +77,21 @@ struct Geom {
 
 __device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Index check of checked builds (-DLB_CHECKS, a stand-in for a memory
+// sanitizer): an index outside [0, n) is replaced by 0, an in-bounds access,
+// and bit 2 of the device error word is set (the host reports LB_ERR_STATE).
+// Other builds return the index unchanged.
+template <typename I>
+__device__ __forceinline__ I chk(I i, long long n, int *err) {
+#ifdef LB_CHECKS
+    if ((long long)i < 0 || (long long)i >= n) {
+        if (err) atomicOr(err, 2);
+        return I(0);
+    }
+#endif
+    return i;
+}
+
 __device__ __forceinline__ long long nidx(const Geom &g, int x, int y, int z) {
     return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
 }

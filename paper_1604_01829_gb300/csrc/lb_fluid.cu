@@ -138,12 +138,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOIS
             if (PORE && ((wmask >> i) & 1u))
                 f[i] = g.chan ? (R)((double)plane(i)[n] + chan_term(g, cy(i) > 0 ? 0 : 1, i)) : (R)plane(i)[n];
             else
-                f[i] = plane(opp(i))[nb(-cx(i), -cy(i), -cz(i))];
+                f[i] = plane(opp(i))[chk(nb(-cx(i), -cy(i), -cz(i)), N, a.err)];
         }
     };
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = plane(i)[n];
+        for (int i = 0; i < 19; ++i) f[i] = plane(i)[chk(n, N, a.err)];
     } else if (row_in) {
         load_odd(nb_in);
     } else {
@@ -177,12 +177,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOIS
         for (int i = 1; i < 19; ++i) {
             if (PORE && ((wmask >> opp(i)) & 1u))
                 plane(opp(i))[n] = g.chan ? (T)((double)f[i] - chan_term(g, cy(i) < 0 ? 0 : 1, i)) : (T)f[i];
-            else plane(i)[nb(cx(i), cy(i), cz(i))] = f[i];
+            else plane(i)[chk(nb(cx(i), cy(i), cz(i)), N, a.err)] = f[i];
         }
     };
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) plane(opp(i))[n] = f[i];
+        for (int i = 0; i < 19; ++i) plane(opp(i))[chk(n, N, a.err)] = f[i];
     } else if (row_in) {
         store_odd(nb_in);
     } else {

@@ -106,6 +106,10 @@ struct CoupleArgs {
     uint32_t key0, key1, instance;
     const unsigned long long *step_base;
     uint32_t step_off;
+    // extents for the index checks of checked builds (LB_CHECKS); err may be null
+    int *err;
+    long long ntiles;
+    int list_cap, nbodies;
 };
 
 // launchers (return the launch error)

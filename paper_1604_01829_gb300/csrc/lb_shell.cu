@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lb.h"
+#include "lb_device.cuh"
 
 namespace lbk {
 
@@ -57,6 +58,7 @@ struct ShellArgs {
     const int *cgrid;         // [nshells][3]
     const double *cbox;       // [nshells][3] half-widths L
     int max_cells;            // largest grid (shared-memory extent)
+    int *err;                 // index checks of checked builds (LB_CHECKS): bit 2 on failure
 };
 
 __device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
                         outside = true;
                         bcell[i] = -1;
                     } else {
-                        const int c = cx + gx * (cy + gy * cz);
+                        const int c = chk(cx + gx * (cy + gy * cz), C, a.err);
                         bcell[i] = c;
                         atomicAdd(&cnt[c], 1);
                     }
@@ -213,7 +215,8 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
             if (use_cells) {
                 scan_cells(cnt, start, C, wsum);
                 __syncthreads();
-                for (int i = threadIdx.x; i < n; i += blockDim.x) sorted[start[bcell[i]] + atomicAdd(&cnt[bcell[i]], 1)] = i;
+                for (int i = threadIdx.x; i < n; i += blockDim.x)
+                    sorted[chk(start[bcell[i]] + atomicAdd(&cnt[bcell[i]], 1), n, a.err)] = i;
                 __syncthreads();
                 // beads of each cell in index order (few per cell: insertion sort)
                 for (int c = threadIdx.x; c < C; c += blockDim.x) {
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(kShellThreads) k_relax_shells(const ShellArgs<
                             const int x = cx + dx;
                             if (x < 0 || x >= gx) continue;
                             const int cc = x + gx * (y + gy * z);
-                            for (int k = start[cc]; k < start[cc + 1]; ++k) pair(b, sorted[k]);
+                            for (int k = start[cc]; k < start[cc + 1]; ++k) pair(b, chk(sorted[k], n, a.err));
                         }
                     }
                 }
@@ -423,7 +426,8 @@ extern "C" lb_status lb_relax_shells(int nshells, const double *axes, const int 
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const size_t nd = (size_t)3 * nshells + (size_t)3 * total + (size_t)3 * nshells;
-    const size_t bytes = nd * sizeof(double) + (size_t)nshells * (sizeof(long long) + sizeof(int) + 3 * sizeof(int));
+    const size_t bytes = nd * sizeof(double) + (size_t)nshells * (sizeof(long long) + sizeof(int) + 3 * sizeof(int)) +
+                         sizeof(int);
     void *d = nullptr;
     e = cudaMalloc(&d, bytes);
     if (e == cudaErrorMemoryAllocation) {
@@ -435,6 +439,7 @@ extern "C" lb_status lb_relax_shells(int nshells, const double *axes, const int 
     long long *doff = reinterpret_cast<long long *>(dbox + 3 * nshells);
     int *dcount = reinterpret_cast<int *>(doff + nshells);
     int *dgrid = dcount + nshells;
+    int *derr = dgrid + 3 * nshells;             // index checks of checked builds
     std::vector<double> out((size_t)3 * total);
     e = cudaMemcpyAsync(daxes, axes, 3 * nshells * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dxyz, xyz, 3 * total * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -442,23 +447,27 @@ extern "C" lb_status lb_relax_shells(int nshells, const double *axes, const int 
     if (e == cudaSuccess) e = cudaMemcpyAsync(dcount, counts, nshells * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dbox, box.data(), 3 * nshells * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dgrid, grid.data(), 3 * nshells * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     if (e == cudaSuccess) {
         if (p->precision == 64) {
             lbk::ShellArgs<double> a{};
             a.axes = daxes; a.count = dcount; a.offset = doff; a.xyz = dxyz; a.max_count = max_count;
-            a.cgrid = dgrid; a.cbox = dbox; a.max_cells = cells ? max_cells : 1;
+            a.cgrid = dgrid; a.cbox = dbox; a.max_cells = cells ? max_cells : 1; a.err = derr;
             e = lbk::launch_shells<double>(a, *p, nshells, cells, st);
         } else {
             lbk::ShellArgs<float> a{};
             a.axes = daxes; a.count = dcount; a.offset = doff; a.xyz = dxyz; a.max_count = max_count;
-            a.cgrid = dgrid; a.cbox = dbox; a.max_cells = cells ? max_cells : 1;
+            a.cgrid = dgrid; a.cbox = dbox; a.max_cells = cells ? max_cells : 1; a.err = derr;
             e = lbk::launch_shells<float>(a, *p, nshells, cells, st);
         }
     }
+    int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dxyz, 3 * total * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d);
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("lb_relax_shells: ") + cudaGetErrorString(e));
+    if (herr) return fail(LB_ERR_STATE, "an index check of the checked build failed (an index outside its array)");
     for (double v : out)
         if (!std::isfinite(v)) return fail(LB_ERR_UNSTABLE, "non-finite bead position: reduce dt or k");
     std::memcpy(xyz, out.data(), out.size() * sizeof(double));

@@ -15,7 +15,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "liblbrasp.so")
+# LB_CHECKED=1 selects the index-checked build (build.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbrasp_checked.so" if os.environ.get("LB_CHECKED") == "1"
+                        else "liblbrasp.so")
 
 LB_OK, LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_UNSTABLE, LB_ERR_TIMEOUT, LB_ERR_STATE = range(7)
 
