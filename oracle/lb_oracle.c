@@ -208,6 +208,11 @@ typedef struct {
        tangential velocities uw_lo and uw_hi; the box is not periodic in y */
     int ywalls;
     double uw_lo[3], uw_hi[3];
+    /* MD substeps per LB step (Sec. 2.3: the MD time step is half the LB
+       step, so the paper's value is 2; 0 or 1 = one). Each substep moves the
+       bodies by dt = 1/n and couples the beads to the fluid of this LB step;
+       the fluid receives each substep's bead forces with weight dt. */
+    int md_substeps;
 } orc_params;
 
 typedef struct {
@@ -366,22 +371,22 @@ static void cross(const double a[3], const double b[3], double o[3])
  * pair of half kicks around each step boundary is the trapezoidal rule and
  * the rotation integrator is second order and time-symmetric, the property
  * of the velocity-Verlet rotation schemes cited in Sec. 2.3. */
-static void euler_half_kick(double w[3], const double I[3], const double T[3])
+static void euler_half_kick(double w[3], const double I[3], const double T[3], double dt)
 {
     double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]}, wxIw[3];
     cross(w, Iw, wxIw);
-    for (int a = 0; a < 3; ++a) w[a] += 0.5 * (T[a] - wxIw[a]) / I[a];
+    for (int a = 0; a < 3; ++a) w[a] += 0.5 * dt * (T[a] - wxIw[a]) / I[a];
 }
 
 #define IMPLICIT_KICK_ITERS 6
 
-static void euler_half_kick_implicit(double w[3], const double I[3], const double T[3])
+static void euler_half_kick_implicit(double w[3], const double I[3], const double T[3], double dt)
 {
     double w0[3] = {w[0], w[1], w[2]};
     for (int it = 0; it < IMPLICIT_KICK_ITERS; ++it) {
         double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]}, wxIw[3];
         cross(w, Iw, wxIw);
-        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * (T[a] - wxIw[a]) / I[a];
+        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * dt * (T[a] - wxIw[a]) / I[a];
     }
 }
 
@@ -620,57 +625,46 @@ void orc_node_velocity(const orc_params *p, const double *f, const double *F, do
  *  6. bodies: second half kick with this step's force and torque.
  * Returns 0, or -1 on bad input.
  */
-int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *Fnode,
-             orc_bodies *b, int64_t step)
+/* First half kick with the previous (sub)step's force and torque, then the
+ * drift over dt: V += dt F/(2M), X += dt V, explicit Euler half kick of the
+ * body-frame omega, q <- q (x) exp(omega dt / 2). */
+static void bodies_kick_drift(orc_bodies *b, double dt)
 {
-    init_tables();
-    if (p->collision == 0 && p->kT > 0.0) return -1;
-    const int nx = p->nx, ny = p->ny, nz = p->nz;
-    const size_t N = (size_t)nx * ny * nz;
-    const uint32_t step32 = (uint32_t)step;
-    const int nbodies = b ? b->nbodies : 0;
-
-    size_t nfluid = 0;
-    for (size_t n = 0; n < N; ++n) nfluid += (mask && mask[n]) ? 0 : 1;
-
-    /* uniform force density on the fluid */
-    double g[3];
-    for (int a = 0; a < 3; ++a) g[a] = p->body_force[a];
-    if (p->compensate_force && nfluid > 0)
-        for (int bi = 0; bi < nbodies; ++bi)
-            if (b->fixed[bi] != 1)
-                for (int a = 0; a < 3; ++a) g[a] -= b->F_ext[3 * bi + a] / (double)nfluid;
-
-    double *Fnew = (double *)calloc(3 * N, sizeof(double));
-    double *fpost = (double *)malloc(sizeof(double) * NQ * N);
-    if (!Fnew || !fpost) { free(Fnew); free(fpost); return -1; }
-
-    /* 1. first half kick and drift */
-    for (int bi = 0; bi < nbodies; ++bi) {
+    for (int bi = 0; bi < b->nbodies; ++bi) {
         if (b->fixed[bi] == 1) continue;
         double M = b->mass[bi];
         double *X = &b->X[3 * bi], *V = &b->V[3 * bi], *q = &b->q[4 * bi], *w = &b->w[3 * bi];
         for (int a = 0; a < 3; ++a) {
-            V[a] += 0.5 * b->F_last[3 * bi + a] / M;
-            X[a] += V[a];
+            V[a] += 0.5 * dt * b->F_last[3 * bi + a] / M;
+            X[a] += dt * V[a];
         }
         if (b->fixed[bi] == 2) {           /* orientation held */
             for (int a = 0; a < 3; ++a) w[a] = 0.0;
             continue;
         }
-        euler_half_kick(w, &b->inertia[3 * bi], &b->T_last[3 * bi]);
+        euler_half_kick(w, &b->inertia[3 * bi], &b->T_last[3 * bi], dt);
         double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
         if (wn > 0.0) {
-            double h = 0.5 * wn;
+            double h = 0.5 * wn * dt;
             double dq[4] = {cos(h), sin(h) * w[0] / wn, sin(h) * w[1] / wn, sin(h) * w[2] / wn};
             quat_mul(q, dq, q);
         }
         double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         for (int a = 0; a < 4; ++a) q[a] /= qn;
     }
+}
 
-    /* 2.-3. virtual sites and coupling */
-    for (int bi = 0; bi < nbodies; ++bi) {
+/* Virtual sites and friction coupling of one (sub)step: every bead's drag
+ * against the fluid velocity interpolated from the populations f of this
+ * LB step (with the previous step's node force Fnode), bead noise of
+ * variance 2 kT gamma / dt (Philox call 4 + substep), -w dt F_b added to
+ * Fnew, and the bodies' totals F_tot, T_tot. */
+static void couple_bodies(const orc_params *p, const double *f, const unsigned char *mask, const double *Fnode,
+                          const double g[3], double *Fnew, orc_bodies *b, uint32_t step32, int substep, double dt)
+{
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    for (int bi = 0; bi < b->nbodies; ++bi) {
         double R[3][3];
         rotation(&b->q[4 * bi], R);
         const double *X = &b->X[3 * bi], *V = &b->V[3 * bi], *wb = &b->w[3 * bi];
@@ -730,16 +724,16 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
             double fs[3] = {0, 0, 0};
             if (p->kT > 0.0 && p->gamma_bead > 0.0) {
                 uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
-                uint32_t ctr[4] = {(uint32_t)k, step32, p->instance, 4u};
+                uint32_t ctr[4] = {(uint32_t)k, step32, p->instance, 4u + (uint32_t)substep};
                 uint32_t rr[4];
                 philox4x32_10(ctr, key, rr);
-                double amp = sqrt(2.0 * p->kT * p->gamma_bead);
+                double amp = sqrt(2.0 * p->kT * p->gamma_bead / dt);
                 for (int a = 0; a < 3; ++a) fs[a] = amp * unit_uniform(rr[a]);
             }
             for (int a = 0; a < 3; ++a) Fb[a] = -p->gamma_bead * (v[a] - ub[a]) + fs[a];
             for (int cidx = 0; cidx < 8; ++cidx) {
                 if (!fluid[cidx]) continue; /* momentum into a wall node is taken by the wall */
-                for (int a = 0; a < 3; ++a) Fnew[(size_t)a * N + node[cidx]] -= wgt[cidx] * Fb[a];
+                for (int a = 0; a < 3; ++a) Fnew[(size_t)a * N + node[cidx]] -= dt * wgt[cidx] * Fb[a];
             }
             double tq[3];
             cross(rel, Fb, tq);
@@ -762,6 +756,64 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
             b->T_tot[3 * bi + a] = Tt[a] + b->T_ext[3 * bi + a];
         }
     }
+}
+
+/* Second half kick over dt with this (sub)step's totals, which become the
+ * next first half kick's force and (body-frame) torque. */
+static void bodies_kick2(orc_bodies *b, double dt)
+{
+    for (int bi = 0; bi < b->nbodies; ++bi) {
+        double R[3][3];
+        rotation(&b->q[4 * bi], R);
+        double Tb[3];
+        const double *Tl = &b->T_tot[3 * bi];
+        for (int a = 0; a < 3; ++a) Tb[a] = R[0][a] * Tl[0] + R[1][a] * Tl[1] + R[2][a] * Tl[2];
+        for (int a = 0; a < 3; ++a) {
+            b->F_last[3 * bi + a] = b->F_tot[3 * bi + a];
+            b->T_last[3 * bi + a] = Tb[a];
+        }
+        if (b->fixed[bi] == 1) continue;
+        for (int a = 0; a < 3; ++a) b->V[3 * bi + a] += 0.5 * dt * b->F_tot[3 * bi + a] / b->mass[bi];
+        if (b->fixed[bi] == 2) continue;
+        euler_half_kick_implicit(&b->w[3 * bi], &b->inertia[3 * bi], Tb, dt);
+    }
+}
+
+int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *Fnode,
+             orc_bodies *b, int64_t step)
+{
+    init_tables();
+    if (p->collision == 0 && p->kT > 0.0) return -1;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const uint32_t step32 = (uint32_t)step;
+    const int nbodies = b ? b->nbodies : 0;
+    const int nsub = p->md_substeps > 1 ? p->md_substeps : 1;
+    const double dt = 1.0 / nsub;
+
+    size_t nfluid = 0;
+    for (size_t n = 0; n < N; ++n) nfluid += (mask && mask[n]) ? 0 : 1;
+
+    /* uniform force density on the fluid */
+    double g[3];
+    for (int a = 0; a < 3; ++a) g[a] = p->body_force[a];
+    if (p->compensate_force && nfluid > 0)
+        for (int bi = 0; bi < nbodies; ++bi)
+            if (b->fixed[bi] != 1)
+                for (int a = 0; a < 3; ++a) g[a] -= b->F_ext[3 * bi + a] / (double)nfluid;
+
+    double *Fnew = (double *)calloc(3 * N, sizeof(double));
+    double *fpost = (double *)malloc(sizeof(double) * NQ * N);
+    if (!Fnew || !fpost) { free(Fnew); free(fpost); return -1; }
+
+    /* 1.-3. the MD substeps: first half kick and drift, virtual sites and
+       coupling, and (between substeps) the second half kick */
+    if (nbodies > 0)
+        for (int sub = 0; sub < nsub; ++sub) {
+            bodies_kick_drift(b, dt);
+            couple_bodies(p, f, mask, Fnode, g, Fnew, b, step32, sub, dt);
+            if (sub + 1 < nsub) bodies_kick2(b, dt);
+        }
 
     /* 4. collision */
     for (int z = 0; z < nz; ++z)
@@ -804,22 +856,8 @@ int orc_step(const orc_params *p, double *f, const unsigned char *mask, double *
                 }
             }
 
-    /* 6. second half kick */
-    for (int bi = 0; bi < nbodies; ++bi) {
-        double R[3][3];
-        rotation(&b->q[4 * bi], R);
-        double Tb[3];
-        const double *Tl = &b->T_tot[3 * bi];
-        for (int a = 0; a < 3; ++a) Tb[a] = R[0][a] * Tl[0] + R[1][a] * Tl[1] + R[2][a] * Tl[2];
-        for (int a = 0; a < 3; ++a) {
-            b->F_last[3 * bi + a] = b->F_tot[3 * bi + a];
-            b->T_last[3 * bi + a] = Tb[a];
-        }
-        if (b->fixed[bi] == 1) continue;
-        for (int a = 0; a < 3; ++a) b->V[3 * bi + a] += 0.5 * b->F_tot[3 * bi + a] / b->mass[bi];
-        if (b->fixed[bi] == 2) continue;
-        euler_half_kick_implicit(&b->w[3 * bi], &b->inertia[3 * bi], Tb);
-    }
+    /* 6. second half kick of the last substep */
+    if (nbodies > 0) bodies_kick2(b, dt);
 
     memcpy(Fnode, Fnew, sizeof(double) * 3 * N);
     free(Fnew);
@@ -914,7 +952,7 @@ int orc_adjoint_drag(const orc_params *p, double *f, const unsigned char *mask, 
 {
     init_tables();
     if (p->kT > 0.0 || nsteps < 1 || window < 1 || window > nsteps || !b || jb < 0 || jb >= b->nbodies ||
-        axis < 0 || axis > 2 || p->ywalls || p->wall_beads)
+        axis < 0 || axis > 2 || p->ywalls || p->wall_beads || p->md_substeps > 1)
         return -2;      /* the reverse pass covers pores and periodic boxes, without walls or wall beads */
     if (b->nbodies > 64) return -2;
     for (int bi = 0; bi < b->nbodies; ++bi)

@@ -49,7 +49,8 @@ class Params(C.Structure):
                 ("wall_beads", C.c_int), ("wall_axis", C.c_int),
                 ("wall_R", C.c_double), ("wall_spacing", C.c_double), ("wall_rp", C.c_double),
                 ("wall_rr", C.c_double), ("wall_eps", C.c_double),
-                ("ywalls", C.c_int), ("uw_lo", C.c_double * 3), ("uw_hi", C.c_double * 3)]
+                ("ywalls", C.c_int), ("uw_lo", C.c_double * 3), ("uw_hi", C.c_double * 3),
+                ("md_substeps", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -169,10 +170,12 @@ def pore_mask(nx, ny, nz, R, axis=2):
 
 def make_params(nx, ny, nz, collision=0, tau=1.0, gamma_shear=0.0, gamma_bulk=0.0,
                 gamma_odd=0.0, gamma_even=0.0, rho0=1.0, kT=0.0, gamma_bead=0.0,
-                seed=0, instance=0, body_force=(0.0, 0.0, 0.0), compensate_force=0):
-    return Params(nx, ny, nz, collision, tau, gamma_shear, gamma_bulk, gamma_odd, gamma_even,
-                  rho0, kT, gamma_bead, seed, instance, (C.c_double * 3)(*body_force),
-                  compensate_force)
+                seed=0, instance=0, body_force=(0.0, 0.0, 0.0), compensate_force=0, md_substeps=1):
+    p = Params(nx, ny, nz, collision, tau, gamma_shear, gamma_bulk, gamma_odd, gamma_even,
+               rho0, kT, gamma_bead, seed, instance, (C.c_double * 3)(*body_force),
+               compensate_force)
+    p.md_substeps = int(md_substeps)
+    return p
 
 
 def collide_node(p: Params, f, F, node_id=0, step=0):

@@ -9,7 +9,7 @@ from oracle import oracle as O
 W19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 
 ORACLE_KEYS = ("collision", "tau", "gamma_shear", "gamma_bulk", "gamma_odd", "gamma_even", "rho0",
-               "kT", "gamma_bead", "seed", "instance", "body_force", "compensate_force")
+               "kT", "gamma_bead", "seed", "instance", "body_force", "compensate_force", "md_substeps")
 
 
 def oracle_kw(params):

@@ -473,6 +473,50 @@ def test_total_momentum_invariant_with_free_colloid_and_compensation():
     assert B["V"][2] > 0  # the colloid moves along the applied force
 
 
+@pytest.mark.parametrize("nsub", [2, 3])
+def test_md_substeps_conserve_momentum(nsub):
+    """MD substeps (Sec. 2.3: two MD steps per LB step in the paper): the
+    bodies move nsub times per LB step with dt = 1/nsub and the fluid receives
+    each substep's bead forces times dt, so sum(j) + M V + dt F_last / 2 is
+    invariant with the compensating drive, and mass is conserved."""
+    from paper_1604_01829_gb300 import workloads as W
+    n = 14
+    sph = W.sphere_raspberry(2.0)
+    L = O.OracleLB(n, n, n, collision=0, tau=1.0, gamma_bead=W.paper_gamma_to_lattice(20.0),
+                   compensate_force=1, md_substeps=nsub)
+    L.add_raspberry(sph, [7.3, 6.9, 7.1], [0.9, 0.3, 0.1, -0.2], mass=33.5, inertia=(53.6,) * 3,
+                    F_ext=(0, 0, 1e-3), T_ext=(2e-4, 0, 0))
+    m0, _ = L.conservation()
+    for _ in range(4):
+        L.step(20)
+        m, p = L.conservation()
+        B = L.body(0)
+        Ptot = p + 33.5 * B["V"] + 0.5 / nsub * B["F_last"]
+        assert abs(m - m0) < 1e-10
+        assert np.abs(Ptot).max() < 1e-12
+    assert B["V"][2] > 0
+
+
+def test_md_substeps_give_the_same_steady_drag():
+    """The MD time step does not change the steady drag of a pulled colloid:
+    terminal velocities with one and with two MD substeps per LB step agree
+    within 1 % (survey reading C-19)."""
+    from paper_1604_01829_gb300 import workloads as W
+    n = 12
+    sph = W.sphere_raspberry(2.0)
+    V = {}
+    for nsub in (1, 2):
+        L = O.OracleLB(n, n, n, collision=0, tau=1.0, gamma_bead=W.paper_gamma_to_lattice(50.0),
+                       compensate_force=1, md_substeps=nsub)
+        L.add_raspberry(sph, [6.2, 5.9, 6.1], mass=33.5, inertia=(53.6,) * 3, F_ext=(1e-4, 0, 0), fixed=2)
+        L.step(1500)
+        v1 = L.body(0)["V"][0]
+        L.step(100)
+        V[nsub] = L.body(0)["V"][0]
+        assert abs(V[nsub] / v1 - 1) < 2e-3        # steady
+    assert abs(V[2] / V[1] - 1) < 0.01, V
+
+
 def test_spinning_colloid_is_slowed_by_the_fluid():
     """Torque sign: a colloid spinning in quiescent fluid receives a torque
     opposing its angular velocity, and the fluid picks up angular momentum."""
