@@ -75,7 +75,12 @@ typedef struct {
     double body_force[3];    /* uniform force density on every fluid node            */
     int compensate_force;    /* 1: add -sum(F_ext of free bodies)/N_fluid to the
                                 fluid so the total momentum stays constant           */
-    int md_substeps;         /* MD steps per LB step; only 1 is supported            */
+    int md_substeps;         /* MD substeps per LB step, 1-4 (0 = 1; the paper's MD step
+                                is half the LB step: 2). Each substep moves the bodies by
+                                dt = 1/n and couples the beads to this LB step's fluid
+                                (bead noise of variance 2 kT gamma / dt); the fluid
+                                receives every substep's bead forces times dt. Not with
+                                the adjoint or the batched handle.                     */
 } lb_params;
 
 /* Creates a lattice with every population at rest, f_i = w_i rho0.

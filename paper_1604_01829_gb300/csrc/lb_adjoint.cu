@@ -483,6 +483,7 @@ extern "C" lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int bo
     if (nsteps < 1 || window < 1 || window > nsteps || axis < 0 || axis > 2 || !J || !dJ_dgamma)
         return lbk::ctx_fail(h, LB_ERR_ARG, "need nsteps >= window >= 1, axis 0-2, J and dJ_dgamma");
     if (h->p.kT > 0.0) return lbk::ctx_fail(h, LB_ERR_ARG, "the adjoint needs a deterministic fluid (kT = 0)");
+    if (h->p.md_substeps > 1) return lbk::ctx_fail(h, LB_ERR_STATE, "the adjoint covers one MD step per LB step");
     if (h->g.chan || h->wall.on)
         return lbk::ctx_fail(h, LB_ERR_STATE, "the adjoint covers periodic boxes and pores, not moving or bead walls");
     const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();

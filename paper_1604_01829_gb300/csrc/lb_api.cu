@@ -308,7 +308,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
     if (p->kT > 0.0 && p->collision == 0)
         return fail(nullptr, LB_ERR_ARG, "thermal noise needs MRT collision (BGK has no separate non-conserved modes)");
     if (!(p->gamma_bead >= 0.0) || !std::isfinite(p->gamma_bead)) return fail(nullptr, LB_ERR_ARG, "gamma_bead must be >= 0");
-    if (p->md_substeps != 1 && p->md_substeps != 0) return fail(nullptr, LB_ERR_ARG, "md_substeps must be 1");
+    if (p->md_substeps < 0 || p->md_substeps > 4) return fail(nullptr, LB_ERR_ARG, "md_substeps must be 0-4 (0 = 1)");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p->body_force[a])) return fail(nullptr, LB_ERR_ARG, "body_force must be finite");
 
@@ -322,7 +322,7 @@ lb_status lb_create(const lb_params *p, void *cuda_stream, lb_handle *out) {
     lb_ctx *h = new (std::nothrow) lb_ctx();
     if (!h) return fail(nullptr, LB_ERR_OOM, "host allocation failed");
     h->p = *p;
-    h->p.md_substeps = 1;
+    h->p.md_substeps = p->md_substeps > 1 ? p->md_substeps : 1;
     h->fp32 = p->precision == 32;
     h->g.nx = p->nx; h->g.ny = p->ny; h->g.nz = p->nz;
     h->g.N = (long long)p->nx * p->ny * p->nz;
@@ -581,18 +581,20 @@ lb_status launch_step_prologue(lb_ctx *h, int k, bool finish_prev, cudaStream_t 
     const int nb = (int)h->hb.size();
     const bool coupled = nb > 0 && !h->hbody_of.empty();
     const int cur = (int)((h->step + k) & 1);
-    const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
+    const int nsub = h->p.md_substeps;
+    // with MD substeps the record is taken after the last substep's drift
+    const lbk::Recorder rec{nsub == 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
     cudaError_t e = lbk::launch_step_pre(h->db, nb, finish_prev, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
                                          coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
-                                         h->list_cap, h->g, h->ntx, h->nty, rec, st);
+                                         h->list_cap, h->g, h->ntx, h->nty, rec, st, 1.0 / nsub);
     if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
     // the list of this buffer restarts empty for this step's coupling
     if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), st));
     return LB_OK;
 }
 
-// The coupling of step h->step + k on the main stream.
-lb_status launch_step_coupling(lb_ctx *h, int k) {
+// The coupling of MD substep `sub` of step h->step + k on the main stream.
+lb_status launch_step_coupling(lb_ctx *h, int k, int sub) {
     const int nbeads = (int)h->hbody_of.size();
     const long long t = h->step + k;
     const bool odd = (t & 1) != 0;
@@ -604,7 +606,12 @@ lb_status launch_step_coupling(lb_ctx *h, int k) {
     c.odd = odd;
     c.rho0 = h->p.rho0;
     c.gamma = h->p.gamma_bead;
-    c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead) : 0.0;
+    const double dt = 1.0 / h->p.md_substeps;
+    // bead noise of variance 2 kT gamma / dt per substep (Philox call 4 + sub)
+    c.noise_amp = h->p.kT > 0.0 ? std::sqrt(2.0 * h->p.kT * h->p.gamma_bead / dt) : 0.0;
+    c.dt = dt;
+    c.dt_f = (float)dt;
+    c.call = 4u + (uint32_t)sub;
     c.gforce = h->gforce;
     c.gforce_f = h->gforce_f;
     c.Fprev = h->Fbuf[prev];
@@ -659,7 +666,17 @@ lb_status launch_steps(lb_ctx *h, int n) {
             LB_CUDA(h, cudaEventRecord(h->ev_join, h->side));
             LB_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
             if (!h->hbody_of.empty()) {
-                if ((s = launch_step_coupling(h, k)) != LB_OK) return s;
+                // MD substeps: bodies move by dt = 1/n between the couplings of one LB step
+                const int nsub = h->p.md_substeps;
+                for (int sub = 0; sub < nsub; ++sub) {
+                    if (sub > 0) {
+                        const lbk::Recorder rec{sub == nsub - 1 ? h->rec : nullptr, h->rec_every, h->rec_cap,
+                                                h->step_dev, (uint32_t)k};
+                        cudaError_t e = lbk::launch_substep(h->db, (int)h->hb.size(), 1.0 / nsub, rec, h->stream);
+                        if (e != cudaSuccess) return cuda_fail(h, e, "substep launch");
+                    }
+                    if ((s = launch_step_coupling(h, k, sub)) != LB_OK) return s;
+                }
             }
             if (k + 1 < n) {                  // the next prologue may start now
                 LB_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -674,7 +691,7 @@ lb_status launch_steps(lb_ctx *h, int n) {
 // end of a group of n steps: the last step's second half kick, counter advance
 lb_status finish_group(lb_ctx *h, int n) {
     if (!h->hb.empty()) {
-        cudaError_t e = lbk::launch_kick2(h->db, (int)h->hb.size(), h->stream);
+        cudaError_t e = lbk::launch_kick2(h->db, (int)h->hb.size(), h->stream, 1.0 / h->p.md_substeps);
         if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
     }
     cudaError_t e = lbk::launch_advance(h->step_dev, (unsigned)n, h->stream);

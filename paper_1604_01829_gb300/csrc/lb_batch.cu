@@ -252,6 +252,9 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.ntiles = 1LL << 62;
     a.list_cap = 0x7fffffff;
     a.nbodies = 0x7fffffff;
+    a.dt = 1.0;
+    a.dt_f = 1.0f;
+    a.call = 4u;
     a.key0 = I.key0;
     a.key1 = I.key1;
     a.instance = I.instance;

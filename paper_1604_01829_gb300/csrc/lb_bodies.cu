@@ -19,14 +19,14 @@ namespace {
 // flagged 4x4x4 tiles of this step's spread-force buffer.
 template <typename T>
 __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
-                           const int *tcount, Geom g, int ntx, int nty, Recorder rec) {
+                           const int *tcount, Geom g, int ntx, int nty, Recorder rec, double dt) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     // one body per block, so the FP64 work of the bodies spreads over SMs;
     // a private copy means one read and one write of the record
     if (threadIdx.x == 0 && blockIdx.x < nb) {
         Body B = bodies[blockIdx.x];
-        if (finish_prev) kick2(B);
-        kick_drift(B);
+        if (finish_prev) kick2(B, dt);
+        kick_drift(B, dt);
         bodies[blockIdx.x] = B;
         record_body(rec, B, blockIdx.x, nb);
     }
@@ -48,12 +48,26 @@ __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *til
     }
 }
 
-__global__ void k_kick2(Body *bodies, int nb) {
+__global__ void k_kick2(Body *bodies, int nb, double dt) {
     const int b = blockIdx.x;          // one body per block, as in k_step_pre
     if (threadIdx.x == 0 && b < nb) {
         Body B = bodies[b];
-        kick2(B);
+        kick2(B, dt);
         bodies[b] = B;
+    }
+}
+
+// Between two MD substeps of one LB step: the finished substep's second half
+// kick, the next substep's first half kick and drift (and the trajectory
+// record after the last substep's drift).
+__global__ void k_substep(Body *bodies, int nb, double dt, Recorder rec) {
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0 && b < nb) {
+        Body B = bodies[b];
+        kick2(B, dt);
+        kick_drift(B, dt);
+        bodies[b] = B;
+        record_body(rec, B, b, nb);
     }
 }
 
@@ -73,14 +87,14 @@ __global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
 
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
                             const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
-                            cudaStream_t s) {
+                            cudaStream_t s, double dt) {
     // enough threads for the bodies and for a full list (grid-stride beyond)
     long long n = 64LL * list_cap;
     if (n > 152LL * 2048) n = 152LL * 2048;
     unsigned grid = (unsigned)((n + 255) / 256);
     if (grid < (unsigned)nbodies) grid = (unsigned)nbodies;
-    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec);
-    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec);
+    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt);
+    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt);
     return cudaGetLastError();
 }
 
@@ -99,9 +113,15 @@ cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s) {
+cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s, double dt) {
     if (nbodies <= 0) return cudaSuccess;
-    k_kick2<<<nbodies, 32, 0, s>>>(b, nbodies);
+    k_kick2<<<nbodies, 32, 0, s>>>(b, nbodies, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_substep(Body *b, int nbodies, double dt, const Recorder &rec, cudaStream_t s) {
+    if (nbodies <= 0) return cudaSuccess;
+    k_substep<<<nbodies, 32, 0, s>>>(b, nbodies, dt, rec);
     return cudaGetLastError();
 }
 

@@ -175,7 +175,7 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
         float fs[3] = {0.f, 0.f, 0.f};
         if (a.noise_amp_f > 0.f) {
             const uint32_t step = (uint32_t)(*a.step_base) + a.step_off;
-            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k_rng, step, a.instance, 4u), make_uint2(a.key0, a.key1));
+            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k_rng, step, a.instance, a.call), make_uint2(a.key0, a.key1));
             fs[0] = a.noise_amp_f * unit_uniform_f(rr.x);
             fs[1] = a.noise_amp_f * unit_uniform_f(rr.y);
             fs[2] = a.noise_amp_f * unit_uniform_f(rr.z);
@@ -187,9 +187,10 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
 
     if (fluid) {
         float *Fc = static_cast<float *>(a.Fcur);
-        atomicAdd(&Fc[n], -wt * Fb[0]);
-        atomicAdd(&Fc[g.N + n], -wt * Fb[1]);
-        atomicAdd(&Fc[2 * g.N + n], -wt * Fb[2]);
+        const float wdt = wt * a.dt_f;
+        atomicAdd(&Fc[n], -wdt * Fb[0]);
+        atomicAdd(&Fc[g.N + n], -wdt * Fb[1]);
+        atomicAdd(&Fc[2 * g.N + n], -wdt * Fb[2]);
         const int tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
         if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0)
             a.tlist[chk(atomicAdd(a.tcount, 1), a.list_cap, a.err)] = a.tile_base + tile;
@@ -298,7 +299,7 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
         double fs[3] = {0.0, 0.0, 0.0};
         if (a.noise_amp > 0.0) {
             const uint32_t step = (uint32_t)(*a.step_base) + a.step_off;
-            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k_rng, step, a.instance, 4u), make_uint2(a.key0, a.key1));
+            const uint4 rr = philox4x32_10(make_uint4((uint32_t)k_rng, step, a.instance, a.call), make_uint2(a.key0, a.key1));
             fs[0] = a.noise_amp * unit_uniform_d(rr.x);
             fs[1] = a.noise_amp * unit_uniform_d(rr.y);
             fs[2] = a.noise_amp * unit_uniform_d(rr.z);
@@ -311,9 +312,9 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
     // spread -w F_b onto this lane's node; a wall node takes nothing
     if (fluid) {
         T *Fc = static_cast<T *>(a.Fcur);
-        atomicAdd(&Fc[n], -wt * (T)Fb[0]);
-        atomicAdd(&Fc[g.N + n], -wt * (T)Fb[1]);
-        atomicAdd(&Fc[2 * g.N + n], -wt * (T)Fb[2]);
+        atomicAdd(&Fc[n], -wt * (T)(a.dt * Fb[0]));
+        atomicAdd(&Fc[g.N + n], -wt * (T)(a.dt * Fb[1]));
+        atomicAdd(&Fc[2 * g.N + n], -wt * (T)(a.dt * Fb[2]));
         const int tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
         // first flag of a tile also records it for clearing two steps later
         if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0)

@@ -110,6 +110,11 @@ struct CoupleArgs {
     int *err;
     long long ntiles;
     int list_cap, nbodies;
+    // MD substeps: the fluid receives -w dt F_b of this substep (dt = 1 without
+    // substeps); Philox call word of the bead noise, 4 + substep
+    double dt;
+    float dt_f;
+    uint32_t call;
 };
 
 // launchers (return the launch error)
@@ -147,9 +152,10 @@ struct Recorder {
     uint32_t step_off;
 };
 
+// dt: the MD (sub)step, 1 without substeps
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
                             const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
-                            cudaStream_t s);
+                            cudaStream_t s, double dt = 1.0);
 
 // The valid records of body `id` in a recorder ring, oldest first (host
 // arrays; lb_traj.cu).
@@ -160,7 +166,9 @@ cudaError_t copy_records(const double *ring, int every, int cap, long long k0, l
 cudaError_t launch_msd(const double *X, const double *q, int nrec, int nbodies, int max_lag, const double *p_ref,
                        double *work, double *out, cudaStream_t s);
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
-cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s);
+cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s, double dt = 1.0);
+// between MD substeps: second half kick, next first half kick and drift (dt each)
+cudaError_t launch_substep(Body *b, int nbodies, double dt, const Recorder &rec, cudaStream_t s);
 // force and torque of the pore-wall beads on every bead (after the coupling)
 cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, const int *bead_body, int nbeads,
                               cudaStream_t st);

@@ -21,32 +21,34 @@ __device__ __forceinline__ void quat_to_R(const double q[4], double R[9]) {
     R[6] = 2.0 * (x * z - y * w); R[7] = 2.0 * (y * z + x * w); R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
-// Euler's equations I dw/dt = T - w x (I w) over half a step, explicit in w
+// Euler's equations I dw/dt = T - w x (I w) over half a step of length dt,
+// explicit in w
 __device__ __forceinline__ void euler_half_explicit(double w[3], const double I[3], const double invI[3],
-                                                    const double T[3]) {
+                                                    const double T[3], double dt) {
     const double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]};
     double c[3];
     cross3(w, Iw, c);
-    for (int a = 0; a < 3; ++a) w[a] += 0.5 * (T[a] - c[a]) * invI[a];
+    for (int a = 0; a < 3; ++a) w[a] += 0.5 * dt * (T[a] - c[a]) * invI[a];
 }
 
 // ... and implicit in w (fixed point), so that the two half kicks around a
 // step boundary form the trapezoidal rule: a second-order, time-symmetric
 // rotation update like the velocity-Verlet rotation schemes of Sec. 2.3.
 __device__ __forceinline__ void euler_half_implicit(double w[3], const double I[3], const double invI[3],
-                                                    const double T[3]) {
+                                                    const double T[3], double dt) {
     const double w0[3] = {w[0], w[1], w[2]};
     for (int it = 0; it < 6; ++it) {
         const double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]};
         double c[3];
         cross3(w, Iw, c);
-        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * (T[a] - c[a]) * invI[a];
+        for (int a = 0; a < 3; ++a) w[a] = w0[a] + 0.5 * dt * (T[a] - c[a]) * invI[a];
     }
 }
 
-// Totals of a finished step, then its second half kick: V += F/(2M),
-// implicit Euler half kick of the body-frame omega.
-__device__ __forceinline__ void kick2(Body &B) {
+// Totals of a finished (sub)step, then its second half kick over dt:
+// V += dt F/(2M), implicit Euler half kick of the body-frame omega. dt = 1
+// without MD substeps (dt = 1/n with n substeps per LB step).
+__device__ __forceinline__ void kick2(Body &B, double dt = 1.0) {
     double Tb[3];
     for (int a = 0; a < 3; ++a) {
         B.F_tot[a] = B.acc[a] + B.F_ext[a];
@@ -58,31 +60,32 @@ __device__ __forceinline__ void kick2(Body &B) {
         B.T_last[a] = Tb[a];
     }
     if (B.fixed == 1) return;
-    for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * B.F_tot[a] * B.inv_mass;
+    for (int a = 0; a < 3; ++a) B.V[a] += 0.5 * dt * B.F_tot[a] * B.inv_mass;
     if (B.fixed == 2) return;          // orientation held
-    euler_half_implicit(B.w, B.I, B.inv_I, Tb);
+    euler_half_implicit(B.w, B.I, B.inv_I, Tb, dt);
 }
 
-// First half kick with last step's force and torque, then drift: X += V,
-// q <- q (x) exp(omega/2) with the half-step body-frame omega.
-__device__ __forceinline__ void kick_drift(Body &B) {
+// First half kick over dt with the last (sub)step's force and torque, then
+// drift: X += dt V, q <- q (x) exp(omega dt / 2) with the half-step
+// body-frame omega.
+__device__ __forceinline__ void kick_drift(Body &B, double dt = 1.0) {
     if (B.fixed == 2) {                // translation only, orientation held
         for (int a = 0; a < 3; ++a) {
-            B.V[a] += 0.5 * B.F_last[a] * B.inv_mass;
-            B.X[a] += B.V[a];
+            B.V[a] += 0.5 * dt * B.F_last[a] * B.inv_mass;
+            B.X[a] += dt * B.V[a];
             B.w[a] = 0.0;
         }
     } else if (!B.fixed) {
         for (int a = 0; a < 3; ++a) {
-            B.V[a] += 0.5 * B.F_last[a] * B.inv_mass;
-            B.X[a] += B.V[a];
+            B.V[a] += 0.5 * dt * B.F_last[a] * B.inv_mass;
+            B.X[a] += dt * B.V[a];
         }
-        euler_half_explicit(B.w, B.I, B.inv_I, B.T_last);
+        euler_half_explicit(B.w, B.I, B.inv_I, B.T_last, dt);
         const double wn = sqrt(B.w[0] * B.w[0] + B.w[1] * B.w[1] + B.w[2] * B.w[2]);
         double *q = B.q;
         if (wn > 0.0) {
             double sh, ch;
-            sincos(0.5 * wn, &sh, &ch);
+            sincos(0.5 * wn * dt, &sh, &ch);
             const double sw = sh / wn;
             const double d[4] = {ch, sw * B.w[0], sw * B.w[1], sw * B.w[2]};
             const double r[4] = {q[0] * d[0] - q[1] * d[1] - q[2] * d[2] - q[3] * d[3],

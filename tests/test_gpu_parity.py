@@ -90,6 +90,33 @@ def test_free_raspberry_periodic(precision):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nsub", [2, 3])
+def test_md_substeps_match_oracle(precision, nsub):
+    """MD substeps per LB step (the paper's MD step is half the LB step):
+    bodies move and couple nsub times per LB step with dt = 1/nsub, bead noise
+    per substep; a free ellipsoid and a fixed sphere in a thermal pore, odd and
+    even step counts, eager steps and graph replay, with the recorder."""
+    params = dict(MRT, kT=1e-4, seed=88, gamma_bead=Wl.paper_gamma_to_lattice(50.0), md_substeps=nsub)
+    P = Pair(26, 26, 20, precision=precision, pore=(11.0, 2), **params)
+    P.add_body(Wl.sphere_raspberry(2.5), [13 + 6.9, 13.4, 6.0], fixed=True, V=(0, 0, 1e-3))
+    ell = Wl.ellipsoid_raspberry(4.0, 2.0, 2.0, seed=3)
+    m = 4.0 / 3.0 * math.pi * 16.0
+    P.add_body(ell, [11.5, 12.2, 14.7], [0.8, 0.1, 0.5, -0.2], mass=m,
+               inertia=tuple(Wl.solid_ellipsoid_inertia(m, 4.0, 2.0, 2.0)), F_ext=(0, 0, 2e-3), T_ext=(1e-3, 0, 0))
+    P.gpu.lb_record_bodies(2, 20)
+    tb = 1e-11 if precision == 64 else 5e-5
+    for n in (3, 2, 5):
+        P.step(n)
+        assert P.pop_error() <= TOL[precision]
+        for b in range(2):
+            e = P.body_errors(b)
+            assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb and e["X"] <= tb, (n, b, e)
+    steps, X, q = P.gpu.lb_get_trajectory(1)
+    assert list(steps) == [2, 4, 6, 8, 10]
+    assert np.array_equal(X[-1], P.gpu.lb_get_body(1)["X"])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 def test_raspberry_in_pore_with_noise(precision):
     """Thermal MRT fluid, bead noise, a fixed sphere near the pore wall (some
     corners are wall nodes) and a free ellipsoid."""
