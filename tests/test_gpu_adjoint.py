@@ -95,3 +95,34 @@ def test_autograd_function_chains_the_adjoint():
     assert abs(J.item() - Jo) <= 1e-9 * abs(Jo)
     assert abs(gamma.grad.item() - (-2e-3 / Jo ** 2) * dgo) <= 1e-8 * abs((2e-3 / Jo ** 2) * dgo)
     assert np.abs(beads.grad.numpy() - (-2e-3 / Jo ** 2) * dso).max() <= 1e-8 * np.abs((2e-3 / Jo ** 2) * dso).max()
+
+
+@pytest.mark.parametrize("param,p_true,p0", [("gamma", 0.15, 0.08), ("scale", 1.1, 1.0)])
+def test_calibration_recovers_the_parameter_of_a_target_drag(param, p_true, p0):
+    """Calibration with the adjoint: the drag of the pulled raspberry for a
+    known bead friction (or size) is the target; Newton iterations with the
+    adjoint's derivative from another starting value recover that friction
+    (or size)."""
+    from paper_1604_01829_gb300 import adjoint, lb
+    sph = Wl.sphere_raspberry(2.0)
+    F = 2e-3
+
+    def make(gamma, beads):
+        L = lb.LB(12, 12, 12, precision=64, gamma_bead=gamma, compensate_force=1, **MRT)
+        L.lb_add_raspberry(beads, [6.3, 5.9, 6.1], mass=40.0, inertia=(60, 60, 60), F_ext=(0, 0, F), fixed=2)
+        return L
+
+    g_fix = 0.12
+    if param == "gamma":
+        L = make(p_true, sph)
+    else:
+        L = make(g_fix, p_true * np.asarray(sph))
+    J, _, _ = L.lb_adjoint_drag(40, 10)
+    L.close()
+    target = F / J
+    p, xi, hist = adjoint.calibrate(target, F, make, sph, p0 if param == "gamma" else g_fix, 40, 10, param=param)
+    if param == "scale":
+        assert abs(hist[0][0] - 1.0) < 1e-15
+    assert abs(p / p_true - 1) < 1e-6, hist
+    assert abs(xi / target - 1) < 1e-6
+    assert len(hist) <= 8
