@@ -17,7 +17,11 @@ ABI against closed forms of Stokes flow:
   by Hasimoto's law.
 
 * the fluctuating fluid: node velocity variance kT/rho0 per component and the
-  stationary variance 3 rho0 kT b_k of every non-conserved mode.
+  stationary variance 3 rho0 kT b_k of every non-conserved mode;
+* resistance against the designed radius (Sec. 3.2): linear, through a
+  renormalised radius offset from R by a constant, for translation and
+  rotation; and against the bead friction (Sec. 3.1): rising to a plateau,
+  the bead friction in series with the hydrodynamic resistance.
 
 The drag runs: BGK tau = 1 (nu = 1/6), FP64, deterministic fluid (kT = 0)."""
 import math
@@ -227,3 +231,84 @@ def test_fluctuating_fluid_thermalises_on_the_cuda_path(precision):
     assert np.all(np.abs(u2 / kT - 1.0) < 0.03), u2 / kT
     ratio = np.mean(mv, axis=0) / (3.0 * kT * b[4:])
     assert np.all(np.abs(ratio - 1.0) < 0.03), ratio
+
+
+def _spin_drag(L, beads, omega=1e-4):
+    """Rotational drag of a raspberry held in place and spinning at omega
+    about z in a periodic L^3 box: xi_r = -T_z / omega at steady state."""
+    from paper_1604_01829_gb300 import lb
+    h = lb.LB(L, L, L, precision=64, collision=0, tau=1.0, gamma_bead=0.3)
+    h.lb_add_raspberry(beads, [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], fixed=1)
+    h.lb_set_body_state(0, w=(0.0, 0.0, omega))
+    h.lb_step(int(1.2 * L * L))
+    T = []
+    for _ in range(5):
+        h.lb_step(max(1, int(0.02 * L * L)))
+        T.append(h.lb_forces(0)[1][2])
+    h.close()
+    return -float(np.mean(T)) / omega
+
+
+def test_resistance_grows_with_radius_through_a_renormalised_radius():
+    """Sec. 3.2 (Fig. radius): the translational resistance of filled
+    raspberries is linear in the designed radius R, and the rotational one in
+    R^3, through a hydrodynamic radius offset from R by a constant (the LB
+    renormalisation of the bead radius). On the CUDA path, R = 2, 3, 4 at
+    gamma = 0.3 (lattice units, BGK tau = 1): xi_t extrapolated to infinite
+    dilution (Hasimoto, two box sizes) lies on a line within 1 % with a slope
+    within 5 % of 6 pi eta; the translational radius xi_t / (6 pi eta) and the
+    rotational radius (xi_r / (8 pi eta))^(1/3) differ from R by offsets that
+    vary by less than 0.05 between radii and are below half a grid spacing."""
+    Rs = np.array([2.0, 3.0, 4.0])
+    xi_t, xi_r = [], []
+    for R in Rs:
+        beads = Wl.sphere_raspberry(R)
+        mass = 4.0 / 3.0 * math.pi * R ** 3
+        Ls = [int(4 * R + 12), int(6 * R + 16)]
+        xi_t.append(_unbounded([_pulled_drag(L, beads, mass, 2) for L in Ls], Ls))
+        xi_r.append(_spin_drag(int(6 * R + 10), beads))
+    xi_t, xi_r = np.array(xi_t), np.array(xi_r)
+    a, b = np.polyfit(Rs, xi_t, 1)
+    res = np.abs(np.polyval([a, b], Rs) / xi_t - 1).max()
+    dt = xi_t / (6 * math.pi * ETA) - Rs
+    dr = (xi_r / (8 * math.pi * ETA)) ** (1.0 / 3.0) - Rs
+    info = dict(xi_t=xi_t, xi_r=xi_r, slope_ratio=a / (6 * math.pi * ETA), offset_t=dt, offset_r=dr)
+    assert res < 0.01, info
+    assert abs(a / (6 * math.pi * ETA) - 1) < 0.05, info
+    for d in (dt, dr):
+        assert np.ptp(d) < 0.05 and np.abs(d).max() < 0.5, info
+
+
+def test_resistance_rises_with_bead_friction_towards_a_plateau():
+    """Sec. 3.1 (Fig. friction_trans, the Stokes-flow half): the colloid's
+    translational resistance rises with the bead friction towards a plateau.
+    R = 2.5 in a 24^3 box, gamma = 0.025 ... 0.4 (lattice units; the explicit
+    coupling of this bead density becomes unstable near 0.8). The bead
+    friction acts in series with the hydrodynamic resistance (as in the
+    effective friction of a point particle in LB, 1/xi_eff = 1/xi_bead +
+    1/(g a eta)), so 1/xi is linear in 1/gamma (within 2 %), with a positive
+    intercept: the plateau xi_inf, which the largest gamma approaches within
+    20 %."""
+    beads = Wl.sphere_raspberry(2.5)
+    mass = 4.0 / 3.0 * math.pi * 2.5 ** 3
+    from paper_1604_01829_gb300 import lb
+    gam = np.array([0.025, 0.05, 0.1, 0.2, 0.4])
+    xi = []
+    for g in gam:
+        h = lb.LB(24, 24, 24, precision=64, collision=0, tau=1.0, gamma_bead=float(g), compensate_force=1)
+        h.lb_add_raspberry(beads, [12.13, 11.79, 12.07], mass=mass, inertia=(mass,) * 3, F_ext=(0, 0, 1e-3), fixed=2)
+        h.lb_step(900)
+        rel = []
+        for _ in range(5):
+            h.lb_step(20)
+            m, p = h.lb_conservation()
+            rel.append(h.lb_get_body(0)["V"][2] - p[2] / m)
+        h.close()
+        xi.append(1e-3 / float(np.mean(rel)))
+    xi = np.array(xi)
+    assert np.all(np.diff(xi) > 0), xi
+    B, A = np.polyfit(1.0 / gam, 1.0 / xi, 1)
+    fit = A + B / gam
+    assert np.abs(fit * xi - 1).max() < 0.02, (xi, A, B)
+    assert A > 0 and B > 0, (A, B)
+    assert xi[-1] > 0.8 / A, (xi, 1.0 / A)
