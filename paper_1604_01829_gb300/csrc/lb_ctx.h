@@ -66,6 +66,7 @@ struct lb_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> ev;   // pairs
     cudaGraphExec_t gexec = nullptr;   // an even and an odd step (lb_step)
+    cudaGraphExec_t gexec8 = nullptr;  // eight steps from an even count (long lb_step calls)
     cudaGraphExec_t gexec1[2] = {nullptr, nullptr};   // one step from an even / odd count
     size_t ev_used = 0;
     double timed_ms = 0.0;
