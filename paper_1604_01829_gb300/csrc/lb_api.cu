@@ -507,6 +507,9 @@ lb_status lb_add_raspberry(lb_handle h, const double *beads, int nbeads, const d
     if (!(qn > 0.0) || !std::isfinite(qn)) return fail(h, LB_ERR_ARG, "quaternion must be non-zero");
     for (int k = 0; k < 3 * nbeads; ++k)
         if (!std::isfinite(beads[k])) return fail(h, LB_ERR_ARG, "non-finite bead offset");
+    if (!lbk::all_finite(X, 3) || !lbk::all_finite(&mass, 1) || !lbk::all_finite(inertia, 3) ||
+        !lbk::all_finite(F_ext, 3) || !lbk::all_finite(T_ext, 3))
+        return fail(h, LB_ERR_ARG, "non-finite position, mass, inertia or external force");
     Body b{};
     for (int a = 0; a < 3; ++a) {
         b.X[a] = X[a];
@@ -533,6 +536,8 @@ lb_status lb_set_body_state(lb_handle h, int id, const double X[3], const double
                             const double w[3]) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
     if (id < 0 || id >= (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body id");
+    if (!lbk::all_finite(X, 3) || !lbk::all_finite(V, 3) || !lbk::all_finite(q, 4) || !lbk::all_finite(w, 3))
+        return fail(h, LB_ERR_ARG, "non-finite body state");
     lb_status s = pull_bodies(h);
     if (s != LB_OK) return s;
     Body &b = h->hb[id];
@@ -553,6 +558,8 @@ lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, 
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
     if (nbodies < 0 || nbodies > (int)h->hb.size() || (nbodies > 0 && !F_ext))
         return fail(h, LB_ERR_ARG, "bad external force arguments");
+    if (!lbk::all_finite(F_ext, 3 * nbodies) || !lbk::all_finite(T_ext, 3 * nbodies))
+        return fail(h, LB_ERR_ARG, "non-finite external force or torque");
     for (int b = 0; b < nbodies; ++b)
         for (int a = 0; a < 3; ++a) {
             h->hb[b].F_ext[a] = F_ext[3 * b + a];

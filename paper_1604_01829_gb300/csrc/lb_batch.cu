@@ -489,6 +489,9 @@ lb_status validate(const lb_params &p) {
             if (!(v > -1.0 && v < 1.0)) return LB_ERR_ARG;
     }
     if (!(p.rho0 > 0.0) || !(p.kT >= 0.0) || !(p.gamma_bead >= 0.0)) return LB_ERR_ARG;
+    if (!std::isfinite(p.rho0) || !std::isfinite(p.kT) || !std::isfinite(p.gamma_bead)) return LB_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p.body_force[a])) return LB_ERR_ARG;
     if (p.kT > 0.0 && p.collision == 0) return LB_ERR_ARG;
     if (p.md_substeps != 0 && p.md_substeps != 1) return LB_ERR_ARG;
     return LB_OK;
@@ -995,7 +998,10 @@ lb_status lb_batch_add_raspberry(lb_batch_handle h, int k, const double *beads, 
         !(inertia[0] > 0 && inertia[1] > 0 && inertia[2] > 0))
         return bfail(h, LB_ERR_ARG, "bad raspberry arguments");
     const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    if (!(qn > 0.0)) return bfail(h, LB_ERR_ARG, "quaternion must be non-zero");
+    if (!(qn > 0.0) || !std::isfinite(qn)) return bfail(h, LB_ERR_ARG, "quaternion must be non-zero");
+    if (!lbk::all_finite(beads, 3 * nbeads) || !lbk::all_finite(X, 3) || !lbk::all_finite(&mass, 1) ||
+        !lbk::all_finite(inertia, 3) || !lbk::all_finite(F_ext, 3) || !lbk::all_finite(T_ext, 3))
+        return bfail(h, LB_ERR_ARG, "non-finite bead offset, position, mass, inertia or external force");
     Body b{};
     for (int a = 0; a < 3; ++a) {
         b.X[a] = X[a];

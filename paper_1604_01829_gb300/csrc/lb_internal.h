@@ -2,6 +2,7 @@
 // kernels (lb_fluid.cu, lb_bodies.cu). Not part of the public ABI.
 #pragma once
 
+#include <cmath>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -172,5 +173,13 @@ cudaError_t launch_substep(Body *b, int nbodies, double dt, const Recorder &rec,
 // force and torque of the pore-wall beads on every bead (after the coupling)
 cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, const int *bead_body, int nbeads,
                               cudaStream_t st);
+
+// host-side argument check: all n values finite (a null pointer passes)
+inline bool all_finite(const double *v, int n) {
+    if (!v) return true;
+    for (int k = 0; k < n; ++k)
+        if (!std::isfinite(v[k])) return false;
+    return true;
+}
 
 }  // namespace lbk
