@@ -311,6 +311,20 @@ lb_status lb_batch_info(lb_batch_handle h, long long *total_nodes, long long *st
  * while on), as lb_set_timing / lb_kernel_time. */
 lb_status lb_batch_set_timing(lb_batch_handle h, int on);
 lb_status lb_batch_kernel_time(lb_batch_handle h, double *total_ms, long long *launches);
+/* Checkpoint and resume of a whole batch, as lb_checkpoint_* for one lattice:
+ * every instance's populations, the bodies, the last per-bead forces, both
+ * spread-force pools with their tile flags and lists, and the step count, in
+ * a caller-owned host buffer of lb_batch_checkpoint_size bytes (save
+ * synchronises). A batch built with the same instances (sizes, pores, seeds,
+ * instance numbers, in the same order) and the same bodies and beads loads it
+ * and resumes the run: the same steps give the same results up to the
+ * summation order of the bead-force atomics. Not saved: the trajectory
+ * recorder and the schedule (neither changes results). Errors: LB_ERR_ARG
+ * (null or short buffer, not a batch checkpoint), LB_ERR_STATE (taken from a
+ * batch with other instances or bodies), LB_ERR_CUDA. */
+lb_status lb_batch_checkpoint_size(lb_batch_handle h, size_t *bytes);
+lb_status lb_batch_checkpoint_save(lb_batch_handle h, void *host, size_t bytes);
+lb_status lb_batch_checkpoint_load(lb_batch_handle h, const void *host, size_t bytes);
 const char *lb_batch_last_error(lb_batch_handle h);
 
 /* Allocation-free mass and momentum reduction. The paper has no counterpart:

@@ -1284,6 +1284,133 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     return s;
 }
 
+namespace {
+
+struct BatchCkptHeader {
+    char magic[8];
+    int n, precision, collision, nbodies, nbeads, list_cap;
+    long long Ntot, Ftot, Ttot, step;
+    unsigned long long geometry;      // FNV-1a of every instance's sizes, pore, seed and instance number
+    unsigned long long body_bytes, total;
+};
+
+unsigned long long batch_geometry_hash(const lb_batch_ctx *h) {
+    unsigned long long x = 1469598103934665603ULL;
+    auto mix = [&](const void *v, size_t nbytes) {
+        const unsigned char *c = static_cast<const unsigned char *>(v);
+        for (size_t k = 0; k < nbytes; ++k) x = (x ^ c[k]) * 1099511628211ULL;
+    };
+    for (int k = 0; k < h->n; ++k) {
+        const BInst &I = h->hinst[k];
+        const long long v[6] = {I.g.nx, I.g.ny, I.g.nz, I.g.pore_axis, (long long)I.g.pore_t,
+                                (long long)h->p[k].seed};
+        mix(v, sizeof(v));
+        mix(&h->p[k].instance, sizeof(h->p[k].instance));
+        mix(&I.pore_R, sizeof(I.pore_R));
+    }
+    return x;
+}
+
+// the sections of a batch checkpoint: device pointer and bytes, in file order
+std::vector<std::pair<void *, size_t>> batch_ckpt_sections(lb_batch_ctx *h) {
+    std::vector<std::pair<void *, size_t>> v;
+    const size_t es = h->fp32 ? 4 : 8;
+    v.push_back({h->pool, 19 * es * (size_t)h->Ntot});
+    const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
+    if (nb > 0) {
+        v.push_back({h->db, sizeof(Body) * nb});
+        if (nbeads > 0) v.push_back({h->dFbead, sizeof(double) * 3 * (size_t)nbeads});
+        for (int k = 0; k < 2; ++k) {
+            v.push_back({h->Fbuf[k], 3 * es * (size_t)h->Ftot});
+            v.push_back({h->tiles[k], sizeof(int) * (size_t)h->Ttot});
+            if (h->list_cap > 0) v.push_back({h->tlist[k], sizeof(int) * (size_t)h->list_cap});
+            v.push_back({h->tcount[k], sizeof(int)});
+        }
+    }
+    return v;
+}
+
+BatchCkptHeader batch_ckpt_header(lb_batch_ctx *h) {
+    BatchCkptHeader c{};
+    std::memcpy(c.magic, "LBBCKP1", 8);
+    c.n = h->n;
+    c.precision = h->fp32 ? 32 : 64;
+    c.collision = h->collision;
+    c.nbodies = (int)h->hb.size();
+    c.nbeads = (int)h->hbody_of.size();
+    c.list_cap = h->list_cap;
+    c.Ntot = h->Ntot;
+    c.Ftot = h->Ftot;
+    c.Ttot = h->Ttot;
+    c.step = h->step;
+    c.geometry = batch_geometry_hash(h);
+    c.body_bytes = sizeof(Body);
+    size_t total = sizeof(BatchCkptHeader);
+    for (auto &sec : batch_ckpt_sections(h)) total += sec.second;
+    c.total = total;
+    return c;
+}
+
+}  // namespace
+
+lb_status lb_batch_checkpoint_size(lb_batch_handle h, size_t *bytes) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (!bytes) return bfail(h, LB_ERR_ARG, "null argument");
+    lb_status s = upload(h);
+    if (s != LB_OK) return s;
+    *bytes = (size_t)batch_ckpt_header(h).total;
+    return LB_OK;
+}
+
+lb_status lb_batch_checkpoint_save(lb_batch_handle h, void *host, size_t bytes) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (!host) return bfail(h, LB_ERR_ARG, "null buffer");
+    lb_status s = upload(h);
+    if (s != LB_OK) return s;
+    const BatchCkptHeader c = batch_ckpt_header(h);
+    if (bytes < c.total) return bfail(h, LB_ERR_ARG, "buffer smaller than lb_batch_checkpoint_size");
+    char *p = static_cast<char *>(host);
+    std::memcpy(p, &c, sizeof(c));
+    p += sizeof(c);
+    for (auto &sec : batch_ckpt_sections(h)) {
+        BCUDA(h, cudaMemcpyAsync(p, sec.first, sec.second, cudaMemcpyDeviceToHost, h->stream));
+        p += sec.second;
+    }
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_batch_checkpoint_load(lb_batch_handle h, const void *host, size_t bytes) {
+    if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
+    if (!host || bytes < sizeof(BatchCkptHeader)) return bfail(h, LB_ERR_ARG, "buffer too small for a checkpoint");
+    BatchCkptHeader c;
+    std::memcpy(&c, host, sizeof(c));
+    if (std::memcmp(c.magic, "LBBCKP1", 8) != 0) return bfail(h, LB_ERR_ARG, "not a batch checkpoint of this library");
+    lb_status s = upload(h);
+    if (s != LB_OK) return s;
+    const BatchCkptHeader mine = batch_ckpt_header(h);
+    if (c.n != mine.n || c.precision != mine.precision || c.collision != mine.collision ||
+        c.nbodies != mine.nbodies || c.nbeads != mine.nbeads || c.list_cap != mine.list_cap ||
+        c.Ntot != mine.Ntot || c.Ftot != mine.Ftot || c.Ttot != mine.Ttot || c.geometry != mine.geometry ||
+        c.body_bytes != mine.body_bytes || c.total != mine.total)
+        return bfail(h, LB_ERR_STATE, "the checkpoint was taken from a batch with other instances or bodies");
+    if (bytes < c.total) return bfail(h, LB_ERR_ARG, "buffer shorter than the checkpoint");
+    if (h->gexec) {                        // the captured steps start from the saved parity again
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    const char *p = static_cast<const char *>(host) + sizeof(c);
+    for (auto &sec : batch_ckpt_sections(h)) {
+        BCUDA(h, cudaMemcpyAsync(sec.first, p, sec.second, cudaMemcpyHostToDevice, h->stream));
+        p += sec.second;
+    }
+    const unsigned long long st = (unsigned long long)c.step;
+    BCUDA(h, cudaMemcpyAsync(h->step_dev, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    h->step = c.step;
+    return LB_OK;
+}
+
 lb_status lb_batch_info(lb_batch_handle h, long long *total_nodes, long long *step, int schedule[3]) {
     if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
     if (total_nodes) *total_nodes = h->Ntot;

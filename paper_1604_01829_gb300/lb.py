@@ -95,6 +95,9 @@ _BSIGS = {
     "lb_batch_info": [C.c_void_p, _llp, _llp, _ip],
     "lb_batch_set_timing": [C.c_void_p, C.c_int],
     "lb_batch_kernel_time": [C.c_void_p, _dp, _llp],
+    "lb_batch_checkpoint_size": [C.c_void_p, C.POINTER(C.c_size_t)],
+    "lb_batch_checkpoint_save": [C.c_void_p, C.c_void_p, C.c_size_t],
+    "lb_batch_checkpoint_load": [C.c_void_p, C.c_void_p, C.c_size_t],
     "lb_batch_record_bodies": [C.c_void_p, C.c_int, C.c_int],
     "lb_batch_get_trajectory": [C.c_void_p, C.c_int, C.c_int, C.c_int, _llp, _dp, _dp, _ip],
 }
@@ -536,6 +539,18 @@ class LBBatch:
 
     def lb_batch_set_timing(self, on=True):
         _bcheck(self.h, load().lb_batch_set_timing(self.h, int(bool(on))))
+
+    def lb_batch_checkpoint_save(self):
+        """The whole batch's state as bytes (see lb_batch_checkpoint_* in include/lb.h)."""
+        n = C.c_size_t()
+        _bcheck(self.h, load().lb_batch_checkpoint_size(self.h, C.byref(n)))
+        buf = (C.c_char * n.value)()
+        _bcheck(self.h, load().lb_batch_checkpoint_save(self.h, buf, n.value))
+        return bytes(buf)
+
+    def lb_batch_checkpoint_load(self, data):
+        buf = C.create_string_buffer(bytes(data), len(data))
+        _bcheck(self.h, load().lb_batch_checkpoint_load(self.h, buf, len(data)))
 
     def lb_batch_kernel_time(self):
         ms, n = C.c_double(), C.c_longlong()

@@ -1,7 +1,8 @@
 """Batched lattices (lb_batch_*): every instance of a batch of uneven
 periodic and pore lattices, with and without raspberries, against the FP64
 oracle run on that instance alone; schedule and autotuner leave results
-unchanged. Tolerances as in test_gpu_parity.py."""
+unchanged; a batch checkpoint resumes every instance. Tolerances as in
+test_gpu_parity.py."""
 import numpy as np
 import pytest
 
@@ -174,3 +175,37 @@ def test_pore_wall_beads_in_a_batch():
             assert np.abs(T - To).max() <= 1e-11 * np.abs(To).max(), (k, T, To)
             Xg = B.lb_batch_get_body(k, 0)["X"]
             assert np.abs(Xg - orcs[k].body(0)["X"]).max() <= 1e-11
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_checkpoint_resume(precision):
+    """A checkpoint of the whole batch taken at an odd step count and loaded
+    into a fresh batch built the same way resumes every instance (up to the
+    order of the bead-force atomics); a batch with other instances refuses it."""
+    from paper_1604_01829_gb300 import lb
+    cases = _cases(noise=True)
+    A, _ = _build(cases, precision)
+    A.lb_batch_step(5)
+    ck = A.lb_batch_checkpoint_save()
+    A.lb_batch_step(6)
+    B, _ = _build(cases, precision)
+    B.lb_batch_step(2)                     # some other state first: the load replaces all of it
+    B.lb_batch_checkpoint_load(ck)
+    B.lb_batch_step(6)
+    assert A.lb_batch_info()["step"] == B.lb_batch_info()["step"] == 11
+    for k in range(len(cases)):
+        fa, fb = A.lb_batch_get_populations(k), B.lb_batch_get_populations(k)
+        d = float((np.abs(fa - fb).max(axis=1) / W19).max())
+        assert d <= (1e-13 if precision == 64 else 1e-6), (k, d)
+        for j in range(len(cases[k][2])):
+            Fa, _ = A.lb_batch_forces(k, j)
+            Fb, _ = B.lb_batch_forces(k, j)
+            assert np.abs(Fa - Fb).max() <= (1e-12 if precision == 64 else 1e-6) * max(np.abs(Fa).max(), 1e-30)
+    other_cases = [(dict(c[0], nx=c[0]["nx"] + (k == 3)), c[1], c[2]) for k, c in enumerate(cases)]
+    C2, _ = _build(other_cases, precision)
+    with pytest.raises(lb.LBError) as e:
+        C2.lb_batch_checkpoint_load(ck)
+    assert e.value.status == lb.LB_ERR_STATE
+    with pytest.raises(lb.LBError) as e:
+        C2.lb_batch_checkpoint_load(ck[:50])
+    assert e.value.status == lb.LB_ERR_ARG
