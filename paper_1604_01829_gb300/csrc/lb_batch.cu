@@ -73,6 +73,10 @@ struct BatchArgs {
     const uint32_t *fluid;       // fluid positions across the axis of the pore instances (BInst::loff)
     const unsigned long long *step_base;
     uint32_t step_off;
+    // index checks of checked builds (-DLB_CHECKS): the error word and the
+    // extents of the shared tables (other builds compile the checks out)
+    int *err;
+    long long nmask, nfluid, ttot;
 };
 
 namespace {
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
             t = blockIdx.x * a.chunk + it;
         }
         if (t >= a.ntiles) break;
-        const int k = __ldg(a.tile_inst + t);
+        const int k = chk(__ldg(a.tile_inst + t), a.n, a.err);
         const BInst &I = a.inst[k];
         const Geom g = I.g;
         const uint32_t N = (uint32_t)g.N;
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
             const uint32_t q = I.wfast ? __umulhi(w, I.mw) : w / d;
             const uint32_t rm = w - q * d;
             const uint32_t j = g.pore_axis == 0 ? q : rm, ax = g.pore_axis == 0 ? rm : q;
-            n = __ldg(a.fluid + I.loff + j) + ax * I.astride;
+            n = __ldg(a.fluid + chk(I.loff + j, a.nfluid, a.err)) + ax * I.astride;
         }
         uint32_t r, z;
         if (I.fastdiv) {
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
             const uint32_t cs = g.pore_axis == 2 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)y
                               : (g.pore_axis == 1 ? (uint32_t)x + (uint32_t)g.nx * z
                                                   : (uint32_t)y + (uint32_t)g.ny * z);
-            const uint32_t m = __ldg(a.masks + I.moff + cs);
+            const uint32_t m = __ldg(a.masks + chk(I.moff + cs, a.nmask, a.err));
             if (m >> 31) continue;
             if (ODD) wall_up = m;
         }
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         const int yo[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.nx, y * g.nx, (y == g.ny - 1 ? 0 : y + 1) * g.nx};
         const int zo[3] = {((int)z == 0 ? g.nz - 1 : (int)z - 1) * nxy, (int)z * nxy,
                            ((int)z == g.nz - 1 ? 0 : (int)z + 1) * nxy};
-        auto at = [&](int i, uint32_t node) -> T & { return P[base + (uint32_t)i * N + node]; };
+        auto at = [&](int i, uint32_t node) -> T & { return P[base + (uint32_t)i * N + chk(node, N, a.err)]; };
         R f[19];
         if (!ODD) {
 #pragma unroll
@@ -149,9 +153,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         R Fx, Fy, Fz;
         if constexpr (DEV) { Fx = I.gf[0]; Fy = I.gf[1]; Fz = I.gf[2]; }
         else { Fx = I.gd[0]; Fy = I.gd[1]; Fz = I.gd[2]; }
-        if (a.tiles && a.tiles[I.toff + tile_of(x, y, (int)z, I.ntx, I.nty)]) {
+        if (a.tiles && a.tiles[chk(I.toff + tile_of(x, y, (int)z, I.ntx, I.nty), a.ttot, a.err)]) {
             const T *Fn = static_cast<const T *>(a.F) + I.foff;
-            Fx += Fn[n];
+            Fx += Fn[chk(n, N, a.err)];
             Fy += Fn[(size_t)N + n];
             Fz += Fn[2 * (size_t)N + n];
         }
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         // offsets live across the collision (register pressure)
         const uint32_t base2 = *(const volatile uint32_t *)&a.inst[k].off;
         const uint32_t N2 = *(const volatile uint32_t *)&a.inst[k].g.N;
-        auto at2 = [&](int i, uint32_t node) -> T & { return P[base2 + (uint32_t)i * N2 + node]; };
+        auto at2 = [&](int i, uint32_t node) -> T & { return P[base2 + (uint32_t)i * N2 + chk(node, N2, a.err)]; };
         if (!ODD) {
 #pragma unroll
             for (int i = 0; i < 19; ++i) at2(opp(i), n) = f[i];
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
                 if (axis2 == 2) cs = (uint32_t)(xo[1] + yo[1]);
                 else if (axis2 == 1) cs = (uint32_t)(xo[1] + zo[1] / *(const volatile int *)&a.inst[k].g.ny);
                 else cs = (uint32_t)((yo[1] + zo[1]) / *(const volatile int *)&a.inst[k].g.nx);
-                wall_dn = __ldg(a.masks + moff2 + cs);
+                wall_dn = __ldg(a.masks + chk(moff2 + cs, a.nmask, a.err));
             }
             at2(0, n) = f[0];
 #pragma unroll
@@ -211,6 +215,8 @@ struct BatchCouple {
     int nbeads;
     const unsigned long long *step_base;
     uint32_t step_off;
+    int *err;                     // index checks of checked builds, as BatchArgs
+    int list_cap, nbodies;
 };
 
 template <typename T>
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     const bool active = k < b.nbeads;
     // lanes of inactive groups borrow bead 0's instance (they do no work)
     const int kk = active ? k : 0;
-    const BInst &I = b.inst[b.bodies[b.bead_body[kk]].inst];
+    const BInst &I = b.inst[b.bodies[chk(b.bead_body[kk], b.nbodies, b.err)].inst];
     CoupleArgs a{};
     a.g = I.g;
     a.f = static_cast<const T *>(b.pool) + I.off;
@@ -247,11 +253,10 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.bodies = b.bodies;
     a.F_bead = b.F_bead;
     a.nbeads = b.nbeads;
-    // the batched handle has no device error word: index checks of checked
-    // builds cover the single-lattice kernels; no bound here
-    a.ntiles = 1LL << 62;
-    a.list_cap = 0x7fffffff;
-    a.nbodies = 0x7fffffff;
+    a.err = b.err;
+    a.ntiles = (long long)I.ntx * I.nty * I.ntz;
+    a.list_cap = b.list_cap;
+    a.nbodies = b.nbodies;
     a.dt = 1.0;
     a.dt_f = 1.0f;
     a.call = 4u;
@@ -264,10 +269,11 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
 }
 
 // pore-wall beads of each bead's instance (one thread per bead)
-__global__ void k_batch_wall(const BInst *inst, Body *bodies, const double *s, const int *bead_body, int nbeads) {
+__global__ void k_batch_wall(const BInst *inst, Body *bodies, const double *s, const int *bead_body, int nbeads,
+                             int nbodies, int *err) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nbeads) return;
-    const BInst &I = inst[bodies[bead_body[k]].inst];
+    const BInst &I = inst[bodies[chk(bead_body[k], nbodies, err)].inst];
     if (!I.wall.on) return;
     const WallBeads w = I.wall;
     wall_bead_body(w, bodies, s, bead_body, k);
@@ -278,7 +284,7 @@ __global__ void k_batch_wall(const BInst *inst, Body *bodies, const double *s, c
 template <typename T>
 __global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
                             const int *tcount, const BInst *inst, const long long *flag_start, int n,
-                            Recorder rec) {
+                            Recorder rec, int list_cap, long long ttot, int *err) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (threadIdx.x == 0 && blockIdx.x < nb) {     // one body per block
         Body B = bodies[blockIdx.x];
@@ -291,7 +297,7 @@ __global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *ti
     // one thread per (listed tile, node of the tile)
     const long long total = 64LL * (*tcount);
     for (long long i = t; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long gt = tlist[i >> 6];
+        const long long gt = chk((long long)tlist[chk(i >> 6, list_cap, err)], ttot, err);
         int lo = 0, hi = n;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -417,6 +423,11 @@ struct lb_batch_ctx {
     long long timed_n = 0;
     size_t dev_bytes = 0;
     std::string err;
+    // device error word of the index checks (checked builds) and its pinned
+    // host copy; extents of the wall-mask and fluid-position tables
+    int *derr = nullptr;
+    int *herr = nullptr;
+    long long nmask = 0, nfluidpos = 0;
 };
 
 namespace {
@@ -566,6 +577,7 @@ lb_status upload(lb_batch_ctx *h) {
         mtot += I.g.pore_axis == 2 ? (long long)I.g.nx * I.g.ny
               : (I.g.pore_axis == 1 ? (long long)I.g.nx * I.g.nz : (long long)I.g.ny * I.g.nz);
     }
+    h->nmask = mtot;
     if (mtot > 0) {
         lb_status s = balloc(h, &h->dmask, sizeof(uint32_t) * (size_t)mtot);
         if (s != LB_OK) return s;
@@ -602,6 +614,7 @@ lb_status upload(lb_batch_ctx *h) {
         // exact while w * d < 2^32 for every work item w
         I.wfast = (d > 1 && (double)I.nwork * d < 4294967296.0) ? 1 : 0;
     }
+    h->nfluidpos = (long long)fl.size();
     if (!fl.empty()) {
         lb_status s = balloc(h, &h->dfluid, sizeof(uint32_t) * fl.size());
         if (s != LB_OK) return s;
@@ -667,12 +680,12 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
             lbk::k_batch_pre<float><<<pg, 256, 0, h->stream>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (float *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
-                rec);
+                rec, h->list_cap, h->Ttot, h->derr);
         else
             lbk::k_batch_pre<double><<<pg, 256, 0, h->stream>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (double *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
-                rec);
+                rec, h->list_cap, h->Ttot, h->derr);
         BCUDA(h, cudaGetLastError());
         if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
     }
@@ -696,12 +709,16 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
         c.nbeads = nbeads;
         c.step_base = h->step_dev;
         c.step_off = (uint32_t)k;
+        c.err = h->derr;
+        c.list_cap = h->list_cap;
+        c.nbodies = nb;
         const unsigned grid = (unsigned)((8LL * nbeads + 127) / 128);
         if (h->fp32) lbk::k_batch_couple<float><<<grid, 128, 0, h->stream>>>(c);
         else lbk::k_batch_couple<double><<<grid, 128, 0, h->stream>>>(c);
         BCUDA(h, cudaGetLastError());
         if (h->any_wall) {
-            lbk::k_batch_wall<<<(nbeads + 127) / 128, 128, 0, h->stream>>>(h->dinst, h->db, h->ds, h->dbody_of, nbeads);
+            lbk::k_batch_wall<<<(nbeads + 127) / 128, 128, 0, h->stream>>>(h->dinst, h->db, h->ds, h->dbody_of, nbeads,
+                                                                          nb, h->derr);
             BCUDA(h, cudaGetLastError());
         }
     }
@@ -726,6 +743,10 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     a.tiles = coupled ? h->tiles[cur] : nullptr;
     a.step_base = h->step_dev;
     a.step_off = (uint32_t)k;
+    a.err = h->derr;
+    a.nmask = h->nmask;
+    a.nfluid = h->nfluidpos;
+    a.ttot = h->Ttot;
     if (record) BCUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
 #define BLAUNCH(T, C, NZ)                                                                                   \
     do {                                                                                                    \
@@ -902,12 +923,21 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         (s = balloc(h, &h->dinst, sizeof(BInst) * n)) != LB_OK ||
         (s = balloc(h, &h->dtile_start, sizeof(int) * (n + 1))) != LB_OK ||
         (s = balloc(h, &h->dflag_start, sizeof(long long) * (n + 1))) != LB_OK ||
-        (s = balloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK) {
+        (s = balloc(h, &h->step_dev, sizeof(unsigned long long))) != LB_OK ||
+        (s = balloc(h, &h->derr, sizeof(int))) != LB_OK) {
         g_batch_error = h->err;
         lb_batch_destroy(h);
         return s;
     }
+    if (cudaMallocHost((void **)&h->herr, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        h->herr = nullptr;
+        g_batch_error = "no pinned host memory for the error word";
+        lb_batch_destroy(h);
+        return LB_ERR_OOM;
+    }
     e = cudaMemsetAsync(h->step_dev, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->dflag_start, h->flag_start.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, h->stream);
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
@@ -937,9 +967,11 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask, h->dfluid};
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask, h->dfluid,
+                    h->derr};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    if (h->herr) cudaFreeHost(h->herr);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1087,6 +1119,23 @@ lb_status lb_batch_get_trajectory(lb_batch_handle h, int k, int body, int max_re
     return LB_OK;
 }
 
+namespace {
+
+// Synchronises the stream (completing the copies the caller queued) and
+// returns LB_ERR_STATE once if an index check of a checked build failed
+// since the last check (the word is then cleared).
+lb_status bcheck_device(lb_batch_ctx *h) {
+    BCUDA(h, cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    BCUDA(h, cudaStreamSynchronize(h->stream));
+    if (*h->herr & 2) {
+        BCUDA(h, cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream));
+        return bfail(h, LB_ERR_STATE, "an index check of the checked build failed (an index outside its array)");
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
 lb_status lb_batch_forces(lb_batch_handle h, int k, int body, double F[3], double T[3]) {
     lb_status s = check(h, k);
     if (s != LB_OK) return s;
@@ -1098,8 +1147,7 @@ lb_status lb_batch_forces(lb_batch_handle h, int k, int body, double F[3], doubl
     }
     if (F) BCUDA(h, cudaMemcpyAsync(F, &h->db[id].F_tot[0], 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (T) BCUDA(h, cudaMemcpyAsync(T, &h->db[id].T_tot[0], 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    BCUDA(h, cudaStreamSynchronize(h->stream));
-    return LB_OK;
+    return bcheck_device(h);
 }
 
 lb_status lb_batch_get_body(lb_batch_handle h, int k, int body, double X[3], double V[3], double q[4], double w[3]) {
@@ -1110,7 +1158,7 @@ lb_status lb_batch_get_body(lb_batch_handle h, int k, int body, double X[3], dou
     Body b = h->hb[id];
     if (h->uploaded) {
         BCUDA(h, cudaMemcpyAsync(&b, &h->db[id], sizeof(Body), cudaMemcpyDeviceToHost, h->stream));
-        BCUDA(h, cudaStreamSynchronize(h->stream));
+        if ((s = bcheck_device(h)) != LB_OK) return s;
     }
     for (int a = 0; a < 3; ++a) {
         if (X) X[a] = b.X[a];
@@ -1138,7 +1186,7 @@ lb_status lb_batch_get_populations(lb_batch_handle h, int k, double *host, size_
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("lb_batch_get_populations: ") + cudaGetErrorString(e));
-    return LB_OK;
+    return bcheck_device(h);
 }
 
 lb_status lb_batch_set_populations(lb_batch_handle h, int k, const double *host, size_t n) {
