@@ -698,12 +698,9 @@ lb_status launch_steps(lb_ctx *h, int n) {
 
 // end of a group of n steps: the last step's second half kick, counter advance
 lb_status finish_group(lb_ctx *h, int n) {
-    if (!h->hb.empty()) {
-        cudaError_t e = lbk::launch_kick2(h->db, (int)h->hb.size(), h->stream, 1.0 / h->p.md_substeps);
-        if (e != cudaSuccess) return cuda_fail(h, e, "kick2 launch");
-    }
-    cudaError_t e = lbk::launch_advance(h->step_dev, (unsigned)n, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "advance launch");
+    cudaError_t e = lbk::launch_finish(h->db, (int)h->hb.size(), 1.0 / h->p.md_substeps, h->step_dev, (unsigned)n,
+                                       h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "finish launch");
     return LB_OK;
 }
 

@@ -778,8 +778,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
 
 lb_status finish_steps(lb_batch_ctx *h, int nsteps) {
     const int nb = (int)h->hb.size();
-    if (nb > 0) BCUDA(h, lbk::launch_kick2(h->db, nb, h->stream));
-    BCUDA(h, lbk::launch_advance(h->step_dev, (unsigned)nsteps, h->stream));
+    BCUDA(h, lbk::launch_finish(h->db, nb, 1.0, h->step_dev, (unsigned)nsteps, h->stream));
     return LB_OK;
 }
 

@@ -48,13 +48,17 @@ __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *til
     }
 }
 
-__global__ void k_kick2(Body *bodies, int nb, double dt) {
-    const int b = blockIdx.x;          // one body per block, as in k_step_pre
-    if (threadIdx.x == 0 && b < nb) {
+// The end of a group of steps in one launch: the last step's second half
+// kick (one body per block) and the advance of the device step counter.
+__global__ void k_finish(Body *bodies, int nb, double dt, unsigned long long *step, unsigned int by) {
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    if (b < nb) {
         Body B = bodies[b];
         kick2(B, dt);
         bodies[b] = B;
     }
+    if (b == 0) *step += by;
 }
 
 // Between two MD substeps of one LB step: the finished substep's second half
@@ -117,9 +121,8 @@ cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s, double dt) {
-    if (nbodies <= 0) return cudaSuccess;
-    k_kick2<<<nbodies, 32, 0, s>>>(b, nbodies, dt);
+cudaError_t launch_finish(Body *b, int nbodies, double dt, unsigned long long *step, unsigned int by, cudaStream_t s) {
+    k_finish<<<nbodies > 0 ? nbodies : 1, 32, 0, s>>>(b, nbodies > 0 ? nbodies : 0, dt, step, by);
     return cudaGetLastError();
 }
 

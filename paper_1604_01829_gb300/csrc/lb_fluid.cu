@@ -362,8 +362,6 @@ __global__ void __launch_bounds__(256) k_moments_final(const double *partials, i
         for (int c = 0; c < 4; ++c) out[c] = red[c][0];
 }
 
-__global__ void k_advance(unsigned long long *step, unsigned int by) { *step += by; }
-
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -457,11 +455,6 @@ cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, do
     else if (fp32) k_moments<float><<<nblocks, 256, 0, s>>>((const float *)f, g, odd, partials);
     else k_moments<double><<<nblocks, 256, 0, s>>>((const double *)f, g, odd, partials);
     k_moments_final<<<1, 256, 0, s>>>(partials, nblocks, out4);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_advance(unsigned long long *step, unsigned int by, cudaStream_t s) {
-    k_advance<<<1, 1, 0, s>>>(step, by);
     return cudaGetLastError();
 }
 

@@ -140,7 +140,6 @@ cudaError_t launch_sample(const void *f, bool fp32, const Geom &g, bool odd, dou
                           const long long *nodes, int count, double *out, cudaStream_t s);
 cudaError_t launch_moments(const void *f, bool fp32, const Geom &g, bool odd, double *partials,
                            int nblocks, double *out4, cudaStream_t s);
-cudaError_t launch_advance(unsigned long long *step, unsigned int by, cudaStream_t s);
 
 // Trajectory recorder: after the drift of step t, if (t + 1) % every == 0,
 // the step prologue writes every body's centre and orientation (7 doubles,
@@ -167,7 +166,9 @@ cudaError_t copy_records(const double *ring, int every, int cap, long long k0, l
 cudaError_t launch_msd(const double *X, const double *q, int nrec, int nbodies, int max_lag, const double *p_ref,
                        double *work, double *out, cudaStream_t s);
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
-cudaError_t launch_kick2(Body *b, int nbodies, cudaStream_t s, double dt = 1.0);
+// end of a group of steps: second half kick of every body and the step
+// counter advance, in one launch (nbodies may be 0)
+cudaError_t launch_finish(Body *b, int nbodies, double dt, unsigned long long *step, unsigned int by, cudaStream_t s);
 // between MD substeps: second half kick, next first half kick and drift (dt each)
 cudaError_t launch_substep(Body *b, int nbodies, double dt, const Recorder &rec, cudaStream_t s);
 // force and torque of the pore-wall beads on every bead (after the coupling)

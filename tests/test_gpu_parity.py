@@ -90,6 +90,39 @@ def test_free_raspberry_periodic(precision):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+def test_external_forces_set_between_steps_and_read_back_together(precision):
+    """lb_set_external_forces between steps (all or the first bodies, with and
+    without torques; with the compensating fluid force) against the oracle's
+    set_external; lb_forces_all (every body in one read) equals lb_forces
+    body by body."""
+    params = dict(MRT, kT=1e-4, seed=13, gamma_bead=Wl.paper_gamma_to_lattice(50.0), compensate_force=1)
+    P = Pair(24, 20, 18, precision=precision, **params)
+    P.set_populations(perturbed_populations(P.N, seed=14))
+    sph = Wl.sphere_raspberry(2.0)
+    ell = Wl.ellipsoid_raspberry(3.0, 1.5, 1.5, seed=3)
+    P.add_body(sph, [6.2, 5.1, 4.3], mass=34.0, inertia=(50, 50, 50), F_ext=(1e-3, 0, 0))
+    P.add_body(ell, [16.7, 13.2, 11.1], q=[0.9, 0.1, -0.2, 0.3], mass=30.0, inertia=(10, 40, 40),
+               F_ext=(0, 5e-4, 0), T_ext=(0, 0, 1e-3))
+    P.add_body(sph, [8.8, 15.5, 13.9], mass=34.0, inertia=(50, 50, 50))
+    rng = np.random.default_rng(2)
+    tb = 1e-11 if precision == 64 else 2e-5
+    for n, nset, with_T in ((1, 3, True), (2, 2, False), (3, 3, True), (4, 1, True)):
+        F = rng.normal(scale=1e-3, size=(nset, 3))
+        T = rng.normal(scale=1e-3, size=(nset, 3)) if with_T else None
+        P.gpu.lb_set_external_forces(F, T)
+        for b in range(nset):
+            P.orc.set_external(b, F_ext=F[b], T_ext=T[b] if with_T else np.zeros(3))
+        P.step(n)
+        assert P.pop_error() <= TOL[precision]
+        Fa, Ta = P.gpu.lb_forces_all()
+        for b in range(3):
+            Fb, Tb = P.gpu.lb_forces(b)
+            assert np.array_equal(Fa[3 * b:3 * b + 3], Fb) and np.array_equal(Ta[3 * b:3 * b + 3], Tb)
+            e = P.body_errors(b)
+            assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb and e["X"] <= tb, (n, b, e)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("nsub", [2, 3])
 def test_md_substeps_match_oracle(precision, nsub):
     """MD substeps per LB step (the paper's MD step is half the LB step):
