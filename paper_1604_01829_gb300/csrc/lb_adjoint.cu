@@ -492,6 +492,7 @@ extern "C" lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int bo
         if (b.fixed != 1 && b.fixed != 2)
             return lbk::ctx_fail(h, LB_ERR_ARG, "the adjoint needs fixed (1) or translation-only (2) bodies");
     lb_status st = lbk::ctx_upload(h);
+    if (st == LB_OK) st = lbk::ctx_apply_external(h);
     if (st != LB_OK) return st;
     cudaStream_t s = h->stream;
     const long long N = h->g.N;

@@ -97,6 +97,21 @@ lb_status upload_bodies(lb_ctx *h) {
             LB_CUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
         }
         LB_CUDA(h, cudaMemsetAsync(h->dFbead, 0, sizeof(double) * 3 * (size_t)std::max(nbeads, 1), h->stream));
+        // host-mapped body I/O; without it (allocation refused) the copies below serve
+        if (cudaHostAlloc((void **)&h->io_map, sizeof(double) * (12 * (size_t)nb + 1), cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer((void **)&h->io_dmap, h->io_map, 0) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_io, cudaEventDisableTiming) == cudaSuccess) {
+            std::memset(h->io_map, 0, sizeof(double) * (12 * (size_t)nb + 1));
+            for (int b = 0; b < nb; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    h->io_map[3 * b + a] = h->hb[b].F_ext[a];
+                    h->io_map[3 * (size_t)nb + 3 * b + a] = h->hb[b].T_ext[a];
+                }
+        } else {
+            cudaGetLastError();
+            if (h->io_map) cudaFreeHost(h->io_map);
+            h->io_map = h->io_dmap = nullptr;
+        }
         const size_t fbytes = (h->fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)h->g.N;
         const long long ntiles = (long long)h->ntx * h->nty * h->ntz;
         const size_t tbytes = sizeof(int) * (size_t)ntiles;
@@ -120,8 +135,21 @@ lb_status upload_bodies(lb_ctx *h) {
 // refresh the host mirror of the bodies from the device
 lb_status pull_bodies(lb_ctx *h) {
     if (!h->uploaded || h->hb.empty()) return LB_OK;
+    // the host's external forces stay authoritative: the device records take
+    // them at the next step's prologue
+    std::vector<double> ext(6 * h->hb.size());
+    for (size_t b = 0; b < h->hb.size(); ++b)
+        for (int a = 0; a < 3; ++a) {
+            ext[6 * b + a] = h->hb[b].F_ext[a];
+            ext[6 * b + 3 + a] = h->hb[b].T_ext[a];
+        }
     LB_CUDA(h, cudaMemcpyAsync(h->hb.data(), h->db, sizeof(Body) * h->hb.size(), cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (size_t b = 0; b < h->hb.size(); ++b)
+        for (int a = 0; a < 3; ++a) {
+            h->hb[b].F_ext[a] = ext[6 * b + a];
+            h->hb[b].T_ext[a] = ext[6 * b + 3 + a];
+        }
     return LB_OK;
 }
 
@@ -140,6 +168,7 @@ lb_status check_device_error(lb_ctx *h) {
     LB_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
     const int e = *h->err_host;
+    if (e && h->io_map) h->io_map[12 * h->hb.size()] = 0.0;   // reported here, not again from the mapped copy
     if (e & 2) {
         LB_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
         return fail(h, LB_ERR_STATE, "an index check of the checked build failed (an index outside its array)");
@@ -261,6 +290,16 @@ lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
 namespace lbk {
 // host-side hooks used by the adjoint driver (lb_adjoint.cu)
 lb_status ctx_upload(lb_ctx *h) { return upload_bodies(h); }
+// the device body records take the host's external forces now (the adjoint
+// steps with kernels of its own, which do not read the mapped staging), and
+// the mapped totals are stale once it has run
+lb_status ctx_apply_external(lb_ctx *h) {
+    h->out_fresh = false;
+    if (!h->io_map || h->hb.empty()) return LB_OK;
+    lb_status s = pull_bodies(h);
+    if (s != LB_OK) return s;
+    return push_bodies(h);
+}
 lb_status ctx_fail(lb_ctx *h, lb_status s, const std::string &m) { return fail(h, s, m); }
 }  // namespace lbk
 
@@ -409,6 +448,8 @@ lb_status lb_destroy(lb_handle h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (h->err_host) cudaFreeHost(h->err_host);
+    if (h->io_map) cudaFreeHost(h->io_map);
+    if (h->ev_io) cudaEventDestroy(h->ev_io);
     delete h;
     return LB_OK;
 }
@@ -566,6 +607,19 @@ lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, 
             h->hb[b].T_ext[a] = T_ext ? T_ext[3 * b + a] : 0.0;
         }
     if (!h->uploaded || nbodies == 0) return LB_OK;
+    if (h->io_map) {
+        // into the host-mapped staging the next step's prologue reads; wait
+        // until the steps already queued have read the previous values
+        LB_CUDA(h, cudaEventSynchronize(h->ev_io));
+        const size_t nbt = h->hb.size();
+        for (int b = 0; b < nbodies; ++b)
+            for (int a = 0; a < 3; ++a) {
+                h->io_map[3 * b + a] = F_ext[3 * b + a];
+                h->io_map[3 * nbt + 3 * b + a] = T_ext ? T_ext[3 * b + a] : 0.0;
+            }
+        if (h->p.compensate_force) return push_gforce(h);
+        return LB_OK;
+    }
     // strided copies straight into the device body records
     LB_CUDA(h, cudaMemcpy2DAsync(&h->db[0].F_ext[0], sizeof(Body), F_ext, 3 * sizeof(double), 3 * sizeof(double),
                                  nbodies, cudaMemcpyHostToDevice, h->stream));
@@ -594,7 +648,7 @@ lb_status launch_step_prologue(lb_ctx *h, int k, bool finish_prev, cudaStream_t 
     const lbk::Recorder rec{nsub == 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
     cudaError_t e = lbk::launch_step_pre(h->db, nb, finish_prev, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
                                          coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
-                                         h->list_cap, h->g, h->ntx, h->nty, rec, st, 1.0 / nsub);
+                                         h->list_cap, h->g, h->ntx, h->nty, rec, st, 1.0 / nsub, h->io_dmap);
     if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
     // the list of this buffer restarts empty for this step's coupling
     if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), st));
@@ -699,7 +753,7 @@ lb_status launch_steps(lb_ctx *h, int n) {
 // end of a group of n steps: the last step's second half kick, counter advance
 lb_status finish_group(lb_ctx *h, int n) {
     cudaError_t e = lbk::launch_finish(h->db, (int)h->hb.size(), 1.0 / h->p.md_substeps, h->step_dev, (unsigned)n,
-                                       h->stream);
+                                       h->stream, h->io_dmap ? h->io_dmap + 6 * h->hb.size() : nullptr, h->err_dev);
     if (e != cudaSuccess) return cuda_fail(h, e, "finish launch");
     return LB_OK;
 }
@@ -740,8 +794,23 @@ lb_status ensure_graph(lb_ctx *h, int n = 2) {
 
 }  // namespace
 
+namespace {
+lb_status step_groups(lb_ctx *h, int nsteps);
+}
+
 lb_status lb_step(lb_handle h, int nsteps) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    const lb_status s = step_groups(h, nsteps);
+    if (s == LB_OK && nsteps > 0 && h->ev_io) {
+        // the external forces are read and the totals written by these steps
+        LB_CUDA(h, cudaEventRecord(h->ev_io, h->stream));
+        h->out_fresh = true;
+    }
+    return s;
+}
+
+namespace {
+lb_status step_groups(lb_ctx *h, int nsteps) {
     if (nsteps < 0) return fail(h, LB_ERR_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return LB_OK;
     lb_status s = upload_bodies(h);
@@ -777,6 +846,7 @@ lb_status lb_step(lb_handle h, int nsteps) {
     if (nsteps & 1) return eager_steps(h, 1);
     return LB_OK;
 }
+}  // namespace
 
 lb_status lb_forces(lb_handle h, int id, double F[3], double T[3], double *per_bead) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
@@ -806,6 +876,26 @@ lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T) {
     if (!h->uploaded) {
         if (F) std::memset(F, 0, sizeof(double) * 3 * nbodies);
         if (T) std::memset(T, 0, sizeof(double) * 3 * nbodies);
+        return LB_OK;
+    }
+    if (h->io_map && h->out_fresh) {
+        // the totals and the error word of the last group, written by its
+        // finishing launch into host-mapped memory: no copy
+        LB_CUDA(h, cudaStreamSynchronize(h->stream));
+        const size_t nbt = h->hb.size();
+        const double *out = h->io_map + 6 * nbt;
+        const int err = (int)out[6 * nbt];
+        if (err) {
+            h->io_map[12 * nbt] = 0.0;
+            LB_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+            if (err & 2) return fail(h, LB_ERR_STATE, "an index check of the checked build failed (an index outside its array)");
+            return fail(h, LB_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy did not complete in time)");
+        }
+        for (int b = 0; b < nbodies; ++b)
+            for (int a = 0; a < 3; ++a) {
+                if (F) F[3 * b + a] = out[6 * b + a];
+                if (T) T[3 * b + a] = out[6 * b + 3 + a];
+            }
         return LB_OK;
     }
     if (F) LB_CUDA(h, cudaMemcpy2DAsync(F, 3 * sizeof(double), &h->db[0].F_tot[0], sizeof(Body), 3 * sizeof(double),
@@ -978,6 +1068,8 @@ std::vector<std::pair<void *, size_t>> ckpt_sections(lb_ctx *h) {
             v.push_back({h->tlist[k], sizeof(int) * (size_t)h->list_cap});
             v.push_back({h->tcount[k], sizeof(int)});
         }
+        // the external forces staged for the next step
+        if (h->io_dmap) v.push_back({h->io_dmap, sizeof(double) * 6 * (size_t)nb});
     }
     return v;
 }
@@ -1058,6 +1150,16 @@ lb_status lb_checkpoint_load(lb_handle h, const void *host, size_t bytes) {
     LB_CUDA(h, cudaMemcpyAsync(h->step_dev, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
     LB_CUDA(h, cudaStreamSynchronize(h->stream));
     h->step = c.step;
+    h->out_fresh = false;                 // the loaded totals are read by copy until the next step
+    if (h->io_map) {                      // the loaded external forces become the host's
+        const size_t nb = h->hb.size();
+        for (size_t b = 0; b < nb; ++b)
+            for (int a = 0; a < 3; ++a) {
+                h->hb[b].F_ext[a] = h->io_map[3 * b + a];
+                h->hb[b].T_ext[a] = h->io_map[3 * nb + 3 * b + a];
+            }
+        return push_gforce(h);
+    }
     return LB_OK;
 }
 

@@ -19,13 +19,20 @@ namespace {
 // flagged 4x4x4 tiles of this step's spread-force buffer.
 template <typename T>
 __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
-                           const int *tcount, Geom g, int ntx, int nty, Recorder rec, double dt) {
+                           const int *tcount, Geom g, int ntx, int nty, Recorder rec, double dt, const double *ext) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     // one body per block, so the FP64 work of the bodies spreads over SMs;
     // a private copy means one read and one write of the record
     if (threadIdx.x == 0 && blockIdx.x < nb) {
         Body B = bodies[blockIdx.x];
         if (finish_prev) kick2(B, dt);
+        if (ext) {                     // this step's external force and torque (host-written, mapped)
+            const int b = blockIdx.x;
+            for (int a = 0; a < 3; ++a) {
+                B.F_ext[a] = ext[3 * b + a];
+                B.T_ext[a] = ext[3 * nb + 3 * b + a];
+            }
+        }
         kick_drift(B, dt);
         bodies[blockIdx.x] = B;
         record_body(rec, B, blockIdx.x, nb);
@@ -49,16 +56,27 @@ __global__ void k_step_pre(Body *bodies, int nb, int finish_prev, T *F, int *til
 }
 
 // The end of a group of steps in one launch: the last step's second half
-// kick (one body per block) and the advance of the device step counter.
-__global__ void k_finish(Body *bodies, int nb, double dt, unsigned long long *step, unsigned int by) {
+// kick (one body per block) and the advance of the device step counter;
+// with `out` (host-mapped) also every body's force and torque totals and the
+// device error word, so the host reads them without a copy.
+__global__ void k_finish(Body *bodies, int nb, double dt, unsigned long long *step, unsigned int by, double *out,
+                         const int *err) {
     const int b = blockIdx.x;
     if (threadIdx.x != 0) return;
     if (b < nb) {
         Body B = bodies[b];
         kick2(B, dt);
         bodies[b] = B;
+        if (out)
+            for (int a = 0; a < 3; ++a) {
+                out[6 * b + a] = B.F_tot[a];
+                out[6 * b + 3 + a] = B.T_tot[a];
+            }
     }
-    if (b == 0) *step += by;
+    if (b == 0) {
+        *step += by;
+        if (out) out[6 * nb] = err ? (double)*err : 0.0;
+    }
 }
 
 // Between two MD substeps of one LB step: the finished substep's second half
@@ -91,7 +109,7 @@ __global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
 
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
                             const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
-                            cudaStream_t s, double dt) {
+                            cudaStream_t s, double dt, const double *ext) {
     // one block per body, and for the tile clearing (grid-stride) at most a
     // quarter of the SMs' worth of blocks: the kernel runs beside the fluid
     // kernel of the previous step, whose blocks it would otherwise displace
@@ -101,8 +119,8 @@ cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, boo
     if (n > 38LL * 256) n = 38LL * 256;
     unsigned grid = (unsigned)((n + 255) / 256);
     if (grid < (unsigned)nbodies) grid = (unsigned)nbodies;
-    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt);
-    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt);
+    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);
+    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);
     return cudaGetLastError();
 }
 
@@ -121,8 +139,9 @@ cudaError_t launch_wall_beads(const WallBeads &w, Body *b, const double *s, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish(Body *b, int nbodies, double dt, unsigned long long *step, unsigned int by, cudaStream_t s) {
-    k_finish<<<nbodies > 0 ? nbodies : 1, 32, 0, s>>>(b, nbodies > 0 ? nbodies : 0, dt, step, by);
+cudaError_t launch_finish(Body *b, int nbodies, double dt, unsigned long long *step, unsigned int by, cudaStream_t s,
+                          double *out, const int *err) {
+    k_finish<<<nbodies > 0 ? nbodies : 1, 32, 0, s>>>(b, nbodies > 0 ? nbodies : 0, dt, step, by, out, err);
     return cudaGetLastError();
 }
 

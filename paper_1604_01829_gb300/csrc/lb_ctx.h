@@ -52,6 +52,15 @@ struct lb_ctx {
     float *dsf = nullptr;
     int *dbody_of = nullptr;
     double *dFbead = nullptr;
+    // per-step body I/O in host-mapped pinned memory (Grace-Blackwell: the
+    // GPU reads and writes it over the coherent chip-to-chip link, no copy):
+    // [0, 6 nb) external forces then torques ([3 nb] each, host-written, read
+    // by each step's prologue), [6 nb, 12 nb) force and torque totals per body
+    // and [12 nb] the error word (written at the end of each group of steps)
+    double *io_map = nullptr;          // host address
+    double *io_dmap = nullptr;         // device address of the same memory
+    cudaEvent_t ev_io = nullptr;       // after the last group that reads the external forces
+    bool out_fresh = false;            // the totals there are those of the current state
     bool uploaded = false;
     // reductions
     double *partials = nullptr;
@@ -81,5 +90,6 @@ struct lb_ctx {
 
 namespace lbk {
 lb_status ctx_upload(lb_ctx *h);
+lb_status ctx_apply_external(lb_ctx *h);
 lb_status ctx_fail(lb_ctx *h, lb_status s, const std::string &m);
 }  // namespace lbk

@@ -155,7 +155,7 @@ struct Recorder {
 // dt: the MD (sub)step, 1 without substeps
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
                             const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
-                            cudaStream_t s, double dt = 1.0);
+                            cudaStream_t s, double dt = 1.0, const double *ext = nullptr);
 
 // The valid records of body `id` in a recorder ring, oldest first (host
 // arrays; lb_traj.cu).
@@ -168,7 +168,8 @@ cudaError_t launch_msd(const double *X, const double *q, int nrec, int nbodies, 
 cudaError_t launch_couple(const CoupleArgs &a, cudaStream_t s);
 // end of a group of steps: second half kick of every body and the step
 // counter advance, in one launch (nbodies may be 0)
-cudaError_t launch_finish(Body *b, int nbodies, double dt, unsigned long long *step, unsigned int by, cudaStream_t s);
+cudaError_t launch_finish(Body *b, int nbodies, double dt, unsigned long long *step, unsigned int by, cudaStream_t s,
+                          double *out = nullptr, const int *err = nullptr);
 // between MD substeps: second half kick, next first half kick and drift (dt each)
 cudaError_t launch_substep(Body *b, int nbodies, double dt, const Recorder &rec, cudaStream_t s);
 // force and torque of the pore-wall beads on every bead (after the coupling)
