@@ -80,7 +80,7 @@ typedef struct {
                                 dt = 1/n and couples the beads to this LB step's fluid
                                 (bead noise of variance 2 kT gamma / dt); the fluid
                                 receives every substep's bead forces times dt. Not with
-                                the adjoint or the batched handle.                     */
+                                the adjoint; in a batch every instance has the same.   */
 } lb_params;
 
 /* Creates a lattice with every population at rest, f_i = w_i rho0.

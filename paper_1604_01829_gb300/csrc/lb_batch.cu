@@ -217,6 +217,8 @@ struct BatchCouple {
     uint32_t step_off;
     int *err;                     // index checks of checked builds, as BatchArgs
     int list_cap, nbodies;
+    double dt, noise_scale;       // MD substep length 1/n; bead noise amplitude factor sqrt(n)
+    uint32_t call;                // Philox call word of the bead noise: 4 + substep
 };
 
 template <typename T>
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.odd = b.odd;
     a.rho0 = I.rho0;
     a.gamma = I.gamma;
-    a.noise_amp = I.noise_amp;
+    a.noise_amp = I.noise_amp * b.noise_scale;
     a.gforce = I.gd;
     a.gforce_f = I.gf;
     a.Fprev = static_cast<const T *>(b.Fprev) + I.foff;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.s = b.s;
     a.sf = b.sf;
     a.gamma_f = I.gamma_f;
-    a.noise_amp_f = I.noise_amp_f;
+    a.noise_amp_f = (float)(I.noise_amp * b.noise_scale);
     a.bead_body = b.bead_body;
     a.bodies = b.bodies;
     a.F_bead = b.F_bead;
@@ -257,9 +259,9 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     a.ntiles = (long long)I.ntx * I.nty * I.ntz;
     a.list_cap = b.list_cap;
     a.nbodies = b.nbodies;
-    a.dt = 1.0;
-    a.dt_f = 1.0f;
-    a.call = 4u;
+    a.dt = b.dt;
+    a.dt_f = (float)b.dt;
+    a.call = b.call;
     a.key0 = I.key0;
     a.key1 = I.key1;
     a.instance = I.instance;
@@ -284,12 +286,12 @@ __global__ void k_batch_wall(const BInst *inst, Body *bodies, const double *s, c
 template <typename T>
 __global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *tiles, const int *tlist,
                             const int *tcount, const BInst *inst, const long long *flag_start, int n,
-                            Recorder rec, int list_cap, long long ttot, int *err) {
+                            Recorder rec, int list_cap, long long ttot, int *err, double dt) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (threadIdx.x == 0 && blockIdx.x < nb) {     // one body per block
         Body B = bodies[blockIdx.x];
-        if (finish_prev) kick2(B);
-        kick_drift(B);
+        if (finish_prev) kick2(B, dt);
+        kick_drift(B, dt);
         bodies[blockIdx.x] = B;
         record_body(rec, B, blockIdx.x, nb);
     }
@@ -427,6 +429,7 @@ struct lb_batch_ctx {
     // host copy; extents of the wall-mask and fluid-position tables
     int *derr = nullptr;
     int *herr = nullptr;
+    int nsub = 1;                           // MD substeps per LB step (shared by the instances)
     long long nmask = 0, nfluidpos = 0;
 };
 
@@ -504,7 +507,7 @@ lb_status validate(const lb_params &p) {
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p.body_force[a])) return LB_ERR_ARG;
     if (p.kT > 0.0 && p.collision == 0) return LB_ERR_ARG;
-    if (p.md_substeps != 0 && p.md_substeps != 1) return LB_ERR_ARG;
+    if (p.md_substeps < 0 || p.md_substeps > 4) return LB_ERR_ARG;
     return LB_OK;
 }
 
@@ -672,20 +675,23 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     const int cur = (int)((h->step + k) & 1), prev = cur ^ 1;
     const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
     const bool coupled = nb > 0 && nbeads > 0;
+    const int nsub = h->nsub;
+    const double dt = 1.0 / nsub;
     if (nb > 0) {
-        const lbk::Recorder rec{h->rec, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
+        // with MD substeps the record is taken after the last substep's drift
+        const lbk::Recorder rec{nsub == 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
         const long long nthreads = std::min<long long>(64LL * h->list_cap, 152LL * 2048);
         const unsigned pg = std::max<unsigned>((unsigned)((nthreads + 255) / 256), (unsigned)nb);
         if (h->fp32)
             lbk::k_batch_pre<float><<<pg, 256, 0, h->stream>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (float *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
-                rec, h->list_cap, h->Ttot, h->derr);
+                rec, h->list_cap, h->Ttot, h->derr, dt);
         else
             lbk::k_batch_pre<double><<<pg, 256, 0, h->stream>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (double *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
-                rec, h->list_cap, h->Ttot, h->derr);
+                rec, h->list_cap, h->Ttot, h->derr, dt);
         BCUDA(h, cudaGetLastError());
         if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
     }
@@ -712,14 +718,25 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
         c.err = h->derr;
         c.list_cap = h->list_cap;
         c.nbodies = nb;
+        // bead noise of variance 2 kT gamma / dt per substep (Philox call 4 + substep)
+        c.dt = dt;
+        c.noise_scale = std::sqrt((double)nsub);
         const unsigned grid = (unsigned)((8LL * nbeads + 127) / 128);
-        if (h->fp32) lbk::k_batch_couple<float><<<grid, 128, 0, h->stream>>>(c);
-        else lbk::k_batch_couple<double><<<grid, 128, 0, h->stream>>>(c);
-        BCUDA(h, cudaGetLastError());
-        if (h->any_wall) {
-            lbk::k_batch_wall<<<(nbeads + 127) / 128, 128, 0, h->stream>>>(h->dinst, h->db, h->ds, h->dbody_of, nbeads,
-                                                                          nb, h->derr);
+        for (int sub = 0; sub < nsub; ++sub) {
+            if (sub > 0) {   // bodies move by dt between the couplings of one LB step
+                const lbk::Recorder rec{sub == nsub - 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev,
+                                        (uint32_t)k};
+                BCUDA(h, lbk::launch_substep(h->db, nb, dt, rec, h->stream));
+            }
+            c.call = 4u + (uint32_t)sub;
+            if (h->fp32) lbk::k_batch_couple<float><<<grid, 128, 0, h->stream>>>(c);
+            else lbk::k_batch_couple<double><<<grid, 128, 0, h->stream>>>(c);
             BCUDA(h, cudaGetLastError());
+            if (h->any_wall) {
+                lbk::k_batch_wall<<<(nbeads + 127) / 128, 128, 0, h->stream>>>(h->dinst, h->db, h->ds, h->dbody_of,
+                                                                              nbeads, nb, h->derr);
+                BCUDA(h, cudaGetLastError());
+            }
         }
     }
     lbk::BatchArgs a{};
@@ -778,7 +795,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
 
 lb_status finish_steps(lb_batch_ctx *h, int nsteps) {
     const int nb = (int)h->hb.size();
-    BCUDA(h, lbk::launch_finish(h->db, nb, 1.0, h->step_dev, (unsigned)nsteps, h->stream));
+    BCUDA(h, lbk::launch_finish(h->db, nb, 1.0 / h->nsub, h->step_dev, (unsigned)nsteps, h->stream));
     return LB_OK;
 }
 
@@ -840,8 +857,10 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
     for (int k = 0; k < n; ++k) {
         if (validate(params[k]) != LB_OK) return bfail(nullptr, LB_ERR_ARG, "invalid parameters for instance " + std::to_string(k));
         if (params[k].precision != params[0].precision || params[k].collision != params[0].collision ||
-            (params[k].kT > 0.0) != (params[0].kT > 0.0))
-            return bfail(nullptr, LB_ERR_ARG, "all instances must share precision, collision type and noise on/off");
+            (params[k].kT > 0.0) != (params[0].kT > 0.0) ||
+            std::max(params[k].md_substeps, 1) != std::max(params[0].md_substeps, 1))
+            return bfail(nullptr, LB_ERR_ARG,
+                         "all instances must share precision, collision type, noise on/off and MD substeps");
     }
     if (params[0].precision != 32 && params[0].precision != 64) return bfail(nullptr, LB_ERR_ARG, "precision must be 32 or 64");
     int ndev = 0;
@@ -856,6 +875,7 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
     h->fp32 = params[0].precision == 32;
     h->collision = params[0].collision;
     h->noise = params[0].collision == 1 && params[0].kT > 0.0;
+    h->nsub = std::max(params[0].md_substeps, 1);
     h->hinst.resize(n);
     h->flag_start.assign(n + 1, 0);
     h->nfluid.assign(n, 0);

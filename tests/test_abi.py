@@ -84,7 +84,7 @@ def test_create_rejects_bad_arguments_before_any_device_call(lib, bad):
 
 def test_batch_rejects_mixed_precision_and_noise_without_a_device(lib):
     from paper_1604_01829_gb300 import lb
-    for second in (dict(precision=64), dict(collision=1, kT=1e-4)):
+    for second in (dict(precision=64), dict(collision=1, kT=1e-4), dict(md_substeps=2)):
         with pytest.raises(lb.LBError) as e:
             lb.LBBatch([dict(nx=8, ny=8, nz=8, precision=32, collision=1),
                         dict(dict(nx=8, ny=8, nz=8, precision=32, collision=1), **second)])

@@ -94,6 +94,21 @@ def test_batch_matches_oracle_per_instance(precision, noise):
         assert max(errs) <= TOL[precision], errs
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nsub", [2, 3])
+def test_batch_md_substeps_match_oracle(precision, nsub):
+    """MD substeps in a batch (every instance the same count): bodies move by
+    1/n between the couplings of one LB step, with per-substep bead noise."""
+    cases = [(dict(c[0], md_substeps=nsub), c[1], c[2]) for c in _cases(noise=True)]
+    B, orcs = _build(cases, precision)
+    for n in (1, 2, 3):
+        B.lb_batch_step(n)
+        for o in orcs:
+            o.step(n)
+        errs = _errors(B, orcs, cases)
+        assert max(errs) <= TOL[precision], errs
+
+
 @pytest.mark.parametrize("schedule", [(64, 4, 0), (128, 8, 1), (256, 4, 0), (256, 2, 1), (128, 2, 2)])
 def test_batch_schedule_does_not_change_results(schedule):
     cases = _cases(True)
