@@ -35,6 +35,8 @@ struct BInst {
     uint32_t mx, my;             // ceil(2^32 / nx), ceil(2^32 / ny) for exact quotients (fastdiv)
     int fastdiv;                 // 1 when n * nx and (n / nx) * ny stay below 2^32 for every node
     long long off;               // element offset of plane 0 in the population pool
+    long long ps;                // plane stride (elements): the node count rounded up to 32, so
+                                 // that every plane of every instance starts on a 128-byte line
     long long foff;              // offset of this instance's [3][N] block in a force pool
     long long toff;              // offset of its tile flags
     long long moff;              // pore instances: offset of the cross-section wall masks, else -1
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         const int k = chk(__ldg(a.tile_inst + t), a.n, a.err);
         const BInst &I = a.inst[k];
         const Geom g = I.g;
-        const uint32_t N = (uint32_t)g.N;
+        const uint32_t N = (uint32_t)I.ps;          // plane stride; nodes n < g.N
         const uint32_t w = (uint32_t)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
         if (w >= I.nwork) continue;
         uint32_t n = w;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         // re-read the plane layout for the stores instead of keeping 19 plane
         // offsets live across the collision (register pressure)
         const uint32_t base2 = *(const volatile uint32_t *)&a.inst[k].off;
-        const uint32_t N2 = *(const volatile uint32_t *)&a.inst[k].g.N;
+        const uint32_t N2 = *(const volatile uint32_t *)&a.inst[k].ps;
         auto at2 = [&](int i, uint32_t node) -> T & { return P[base2 + (uint32_t)i * N2 + chk(node, N2, a.err)]; };
         if (!ODD) {
 #pragma unroll
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     const BInst &I = b.inst[b.bodies[chk(b.bead_body[kk], b.nbodies, b.err)].inst];
     CoupleArgs a{};
     a.g = I.g;
+    a.g.N = I.ps;                 // the coupling indexes planes with g.N: the padded stride
     a.f = static_cast<const T *>(b.pool) + I.off;
     a.fp32 = b.fp32;
     a.odd = b.odd;
@@ -314,17 +317,18 @@ __global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *ti
             T *Fi = F + I.foff;
             const long long nn = nidx(I.g, x, y, z);
             Fi[nn] = T(0);
-            Fi[I.g.N + nn] = T(0);
-            Fi[2 * I.g.N + nn] = T(0);
+            Fi[I.ps + nn] = T(0);
+            Fi[2 * I.ps + nn] = T(0);
         }
         if (l == 0) tiles[gt] = 0;
     }
 }
 
 template <typename T>
-__global__ void k_batch_gather(const T *A, Geom g, bool odd, double rho0, double *out) {
+__global__ void k_batch_gather(const T *A, Geom g, long long Nn, bool odd, double rho0, double *out) {
+    // g.N is the plane stride of the pool, Nn the node count (the output's plane length)
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.N) return;
+    if (n >= Nn) return;
     const int x = (int)(n % g.nx);
     const long long r = n / g.nx;
     const int y = (int)(r % g.ny), z = (int)(r / g.ny);
@@ -332,21 +336,21 @@ __global__ void k_batch_gather(const T *A, Geom g, bool odd, double rho0, double
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const T v = wall ? A[(long long)i * g.N + n] : load_pre(A, g, x, y, z, n, i, odd);
-        out[(long long)i * g.N + n] = sizeof(T) == 4 ? (double)v + wq(i) * rho0 : (double)v;
+        out[(long long)i * Nn + n] = sizeof(T) == 4 ? (double)v + wq(i) * rho0 : (double)v;
     }
 }
 
 template <typename T>
-__global__ void k_batch_scatter(T *A, Geom g, bool odd, double rho0, const double *in) {
+__global__ void k_batch_scatter(T *A, Geom g, long long Nn, bool odd, double rho0, const double *in) {
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= g.N) return;
+    if (n >= Nn) return;
     const int x = (int)(n % g.nx);
     const long long r = n / g.nx;
     const int y = (int)(r % g.ny), z = (int)(r / g.ny);
     if (is_wall(g, x, y, z)) return;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const double v = in[(long long)i * g.N + n];
+        const double v = in[(long long)i * Nn + n];
         store_pre(A, g, x, y, z, n, i, odd, sizeof(T) == 4 ? (T)(v - wq(i) * rho0) : (T)v);
     }
 }
@@ -376,7 +380,8 @@ struct lb_batch_ctx {
     std::vector<BInst> hinst;
     std::vector<long long> flag_start;      // n + 1
     std::vector<long long> nfluid;
-    long long Ntot = 0, Ttot = 0, Ftot = 0;
+    long long Ntot = 0, Ttot = 0, Ftot = 0;  // padded plane strides summed (pool sizes)
+    long long Nnodes = 0;                    // nodes of all instances
     void *pool = nullptr;
     void *Fbuf[2] = {nullptr, nullptr};     // force pools, storage precision
     int *tiles[2] = {nullptr, nullptr};
@@ -911,8 +916,10 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         I.fastdiv = ((double)I.g.N * p.nx < 4294967296.0 && (double)(I.g.N / p.nx) * p.ny < 4294967296.0) ? 1 : 0;
         h->flag_start[k] = toff;
         h->nfluid[k] = I.g.N;
-        off += 19 * I.g.N;
-        foff += 3 * I.g.N;
+        I.ps = (I.g.N + 31) / 32 * 32;
+        h->Nnodes += I.g.N;
+        off += 19 * I.ps;
+        foff += 3 * I.ps;
         toff += (long long)I.ntx * I.nty * I.ntz;
     }
     h->flag_start[n] = toff;
@@ -961,8 +968,8 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         e = cudaMemcpyAsync(h->dflag_start, h->flag_start.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, h->stream);
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
         const BInst &I = h->hinst[k];
-        if (h->fp32) lbk::k_batch_init<float><<<(unsigned)((I.g.N + 255) / 256), 256, 0, h->stream>>>((float *)h->pool + I.off, I.g.N, h->p[k].rho0);
-        else lbk::k_batch_init<double><<<(unsigned)((I.g.N + 255) / 256), 256, 0, h->stream>>>((double *)h->pool + I.off, I.g.N, h->p[k].rho0);
+        if (h->fp32) lbk::k_batch_init<float><<<(unsigned)((I.ps + 255) / 256), 256, 0, h->stream>>>((float *)h->pool + I.off, I.ps, h->p[k].rho0);
+        else lbk::k_batch_init<double><<<(unsigned)((I.ps + 255) / 256), 256, 0, h->stream>>>((double *)h->pool + I.off, I.ps, h->p[k].rho0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1188,6 +1195,15 @@ lb_status lb_batch_get_body(lb_batch_handle h, int k, int body, double X[3], dou
     return LB_OK;
 }
 
+namespace {
+// an instance's geometry with N the plane stride of the pool (population I/O)
+lbk::Geom pool_geom(const BInst &I) {
+    lbk::Geom g = I.g;
+    g.N = I.ps;
+    return g;
+}
+}  // namespace
+
 lb_status lb_batch_get_populations(lb_batch_handle h, int k, double *host, size_t n) {
     lb_status s = check(h, k);
     if (s != LB_OK) return s;
@@ -1198,8 +1214,8 @@ lb_status lb_batch_get_populations(lb_batch_handle h, int k, double *host, size_
     h->dev_bytes -= sizeof(double) * n;
     const bool odd = (h->step & 1) != 0;
     const unsigned grid = (unsigned)((I.g.N + 255) / 256);
-    if (h->fp32) lbk::k_batch_gather<float><<<grid, 256, 0, h->stream>>>((const float *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
-    else lbk::k_batch_gather<double><<<grid, 256, 0, h->stream>>>((const double *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
+    if (h->fp32) lbk::k_batch_gather<float><<<grid, 256, 0, h->stream>>>((const float *)h->pool + I.off, pool_geom(I), I.g.N, odd, h->p[k].rho0, tmp);
+    else lbk::k_batch_gather<double><<<grid, 256, 0, h->stream>>>((const double *)h->pool + I.off, pool_geom(I), I.g.N, odd, h->p[k].rho0, tmp);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1220,8 +1236,8 @@ lb_status lb_batch_set_populations(lb_batch_handle h, int k, const double *host,
     const unsigned grid = (unsigned)((I.g.N + 255) / 256);
     cudaError_t e = cudaMemcpyAsync(tmp, host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) {
-        if (h->fp32) lbk::k_batch_scatter<float><<<grid, 256, 0, h->stream>>>((float *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
-        else lbk::k_batch_scatter<double><<<grid, 256, 0, h->stream>>>((double *)h->pool + I.off, I.g, odd, h->p[k].rho0, tmp);
+        if (h->fp32) lbk::k_batch_scatter<float><<<grid, 256, 0, h->stream>>>((float *)h->pool + I.off, pool_geom(I), I.g.N, odd, h->p[k].rho0, tmp);
+        else lbk::k_batch_scatter<double><<<grid, 256, 0, h->stream>>>((double *)h->pool + I.off, pool_geom(I), I.g.N, odd, h->p[k].rho0, tmp);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1480,7 +1496,7 @@ lb_status lb_batch_checkpoint_load(lb_batch_handle h, const void *host, size_t b
 
 lb_status lb_batch_info(lb_batch_handle h, long long *total_nodes, long long *step, int schedule[3]) {
     if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
-    if (total_nodes) *total_nodes = h->Ntot;
+    if (total_nodes) *total_nodes = h->Nnodes;
     if (step) *step = h->step;
     if (schedule) { schedule[0] = h->TS; schedule[1] = h->bpsm; schedule[2] = h->order; }
     return LB_OK;
