@@ -500,7 +500,8 @@ def test_md_substeps_conserve_momentum(nsub):
 def test_md_substeps_give_the_same_steady_drag():
     """The MD time step does not change the steady drag of a pulled colloid:
     terminal velocities with one and with two MD substeps per LB step agree
-    within 1 % (survey reading C-19)."""
+    within 1 % (the paper takes two MD steps per LB step, Sec. 2.3; one or
+    two give the same hydrodynamics)."""
     from paper_1604_01829_gb300 import workloads as W
     n = 12
     sph = W.sphere_raspberry(2.0)
