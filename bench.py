@@ -355,7 +355,9 @@ def run_ours(args, ws, rank, local):
                          "frac_of_copy_ceiling": round(achieved / copy_gbs, 4)},
             "e2e": {"value": None if e2e_value is None else round(e2e_value, 1), "unit": "MLUPS", "steps": e2e_steps,
                     "h2d_bytes_per_step": 2 * 3 * 8 * nb, "d2h_bytes_per_step": 2 * 3 * 8 * nb},
-            "gpu_launches": 3 * K + 2,
+            # per step the body prologue, the coupling and the fused collide-stream
+            # kernel; one finishing launch (last half kick, counter advance) per call
+            "gpu_launches": 3 * K + 1,
             "fp64": fp64_line,
             "batched": batched,
             "pore": pore,
