@@ -150,7 +150,13 @@ lb_status lb_set_body_state(lb_handle h, int body_id, const double X[3], const d
                             const double q[4], const double w[3]);
 
 /* Replaces the external forces and torques of the first nbodies bodies from
- * F_ext[3*nbodies], T_ext[3*nbodies] (lab frame; T_ext may be NULL = 0). */
+ * F_ext[3*nbodies], T_ext[3*nbodies] (lab frame; T_ext may be NULL = 0); the
+ * next lb_step uses them. The values are copied before the call returns
+ * (into host-mapped memory that the next step's prologue reads, after
+ * waiting for steps already queued to have read the previous ones; where
+ * that memory could not be allocated, by copies queued on the stream, which
+ * read the caller's arrays later). Errors: LB_ERR_ARG (bad count, NULL
+ * F_ext, non-finite values). */
 lb_status lb_set_external_forces(lb_handle h, int nbodies, const double *F_ext, const double *T_ext);
 
 /* Advances nsteps LB steps. One step: (1) bodies half-kick and drift,
@@ -166,7 +172,10 @@ lb_status lb_step(lb_handle h, int nsteps);
  * 3*nbeads bead forces of that body. Synchronises. */
 lb_status lb_forces(lb_handle h, int body_id, double F[3], double T[3], double *per_bead_xyz);
 
-/* F[3*nbodies], T[3*nbodies] for the first nbodies bodies. Synchronises. */
+/* F[3*nbodies], T[3*nbodies] for the first nbodies bodies (as lb_forces,
+ * every body in one call: after a step the totals and the device error word
+ * are read from host-mapped memory the step wrote, without a copy).
+ * Synchronises; returns LB_ERR_TIMEOUT / LB_ERR_STATE as lb_forces. */
 lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T);
 
 /* Body state X[3], V[3], q[4], body-frame w[3] (any may be NULL). */
