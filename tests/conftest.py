@@ -26,3 +26,22 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the worst parity errors the tests observed (helpers.observe) to
+    the JSON file named by LB_PARITY_LOG, if set."""
+    path = os.environ.get("LB_PARITY_LOG")
+    if not path:
+        return
+    try:
+        import helpers
+    except Exception:  # pragma: no cover
+        return
+    import json
+    rows = [{"test": t, "quantity": k, "max_error": v} for (t, k), v in sorted(helpers.OBSERVED.items())]
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
+    with open(path, "w") as fh:
+        json.dump(rows, fh, indent=0)

@@ -6,7 +6,7 @@ test_gpu_parity.py."""
 import numpy as np
 import pytest
 
-from helpers import W19, oracle_kw, perturbed_populations
+from helpers import W19, observe, oracle_kw, perturbed_populations
 from oracle import oracle as O
 from paper_1604_01829_gb300 import workloads as Wl
 
@@ -73,11 +73,11 @@ def _errors(B, orcs, cases):
         fg = B.lb_batch_get_populations(k)
         fo = o.populations()
         fl = np.ones(fg.shape[1], bool) if o.mask is None else o.mask == 0
-        out.append(float(np.max(np.abs(fg[:, fl] - fo[:, fl]) / W19[:, None])))
+        out.append(observe("pop", np.max(np.abs(fg[:, fl] - fo[:, fl]) / W19[:, None])))
         for j in range(len(cases[k][2])):
             F, _ = B.lb_batch_forces(k, j)
             Fo = o.body(j)["F"]
-            out.append(float(np.abs(F - Fo).max() / max(np.abs(Fo).max(), 1e-30)) * 1e-1)
+            out.append(observe("F", np.abs(F - Fo).max() / max(np.abs(Fo).max(), 1e-30)) * 1e-1)
     return out
 
 

@@ -23,7 +23,7 @@ same relative to the magnitudes of the bead terms they sum."""
 import numpy as np
 import pytest
 
-from helpers import W19, oracle_kw
+from helpers import W19, observe, oracle_kw
 from oracle import oracle as O
 from paper_1604_01829_gb300 import workloads as Wl
 
@@ -58,7 +58,7 @@ def _pop_error(fg, o):
     err = 0.0
     for i in range(19):                                  # plane by plane: bounded host memory
         err = max(err, float(np.max(np.abs(fg[i][fl] - fo[i][fl]))) / W19[i])
-    return err
+    return observe("pop", err)
 
 
 def _body_errors(g, o, bodies):
@@ -81,6 +81,8 @@ def _body_errors(g, o, bodies):
         worst["bead"] = max(worst["bead"], np.abs(pbg - pbo).max() / max(np.abs(pbo).max(), 1e-300))
         worst["X"] = max(worst["X"], np.abs(gb["X"] - ob["X"]).max())
         worst["q"] = max(worst["q"], np.abs(gb["q"] - ob["q"]).max())
+    for k, v in worst.items():
+        observe(k, v)
     return worst
 
 
