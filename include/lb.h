@@ -355,10 +355,15 @@ const char *lb_batch_last_error(lb_batch_handle h);
  * queued on cuda_stream (NULL = legacy default stream) without waiting.
  * err (may be NULL) receives a message of at most err_len bytes on failure.
  * Lattices of more than LB_NOALLOC_MAX_NODES nodes are rejected with
- * LB_ERR_ARG. All calls share the one scratch array, so calls that overlap
- * on the GPU race and give wrong sums. The first call on a device looks up
- * the array's device address with that device current; make that first call
- * before any stream capture. */
+ * LB_ERR_ARG. Lattices with moving channel walls (lb_set_channel_walls) are
+ * not supported: at odd parity their wall rows hold the wall's momentum
+ * terms, which this reduction does not add back. All calls share the one
+ * scratch array, so calls that overlap on the GPU race and give wrong sums.
+ * Each call made outside stream capture looks up the array's device address
+ * with the current device (so a reset of the device's primary context is
+ * harmless); a call made while cuda_stream is being captured uses the
+ * address found by the device's last call outside capture, so make one call
+ * on each device before capturing (LB_ERR_STATE otherwise). */
 #define LB_NOALLOC_NODES_PER_BLOCK 4096
 #define LB_NOALLOC_MAX_BLOCKS 8192
 #define LB_NOALLOC_MAX_NODES (LB_NOALLOC_NODES_PER_BLOCK * LB_NOALLOC_MAX_BLOCKS)

@@ -12,8 +12,9 @@
 // LB_NOALLOC_MAX_NODES nodes are rejected. Every call on a device uses the
 // same array; each block overwrites its own partial, so nothing needs
 // clearing, but calls that overlap on the GPU (other streams, other host
-// threads) race on it. The array's device address is looked up once per
-// device on the first call with that device current.
+// threads) race on it. The array's device address is looked up with the
+// device current on every call made outside stream capture; a captured call
+// uses the address of the device's last call outside capture.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -105,19 +106,30 @@ lb_status noalloc_fail(const ErrOut &eo, lb_status s, const std::string &m) {
     return s;
 }
 
-// Device address of the scratch array on the current device; looked up once.
-lb_status scratch_address(const ErrOut &eo, double **out) {
+// Device address of the scratch array on the current device. Outside stream
+// capture it is looked up on every call (a cheap host query), so an address
+// cached before a reset of the device's primary context is never used
+// again; while `s` is being captured the address cached by an earlier call
+// on this device is used, and a capture with no earlier call is refused.
+lb_status scratch_address(const ErrOut &eo, cudaStream_t s, double **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(eo, LB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(eo, LB_ERR_ARG, "device ordinal out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    const bool capturing = e != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (e != cudaSuccess) (void)cudaGetLastError();
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
+    if (!capturing) {
         double *ptr = nullptr;
         e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_partials);
         if (e != cudaSuccess || !ptr)
             return noalloc_fail(eo, LB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch[dev] = ptr;
+    } else if (!g_scratch[dev]) {
+        return noalloc_fail(eo, LB_ERR_STATE,
+                            "lb_moments_noalloc: the first call on a device must come before any stream capture");
     }
     *out = g_scratch[dev];
     return LB_OK;
@@ -156,10 +168,10 @@ extern "C" lb_status lb_moments_noalloc(const void *d_populations, int precision
             }
         nfluid = c * nl;
     }
-    double *scratch = nullptr;
-    lb_status st = scratch_address(eo, &scratch);
-    if (st != LB_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    double *scratch = nullptr;
+    lb_status st = scratch_address(eo, s, &scratch);
+    if (st != LB_OK) return st;
     const int nblocks = (int)((N + kNodesPerBlock - 1) / kNodesPerBlock);
     if (precision == 32)
         k_moments_blocks<float><<<nblocks, kThreads, 0, s>>>((const float *)d_populations, g, odd_parity != 0, scratch);
