@@ -12,7 +12,7 @@ from paper_1604_01829_gb300 import workloads as Wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {64: 1e-12, 32: 2e-5}
+TOL = {64: 1e-12, 32: 1e-5}
 MRT = dict(collision=1, gamma_shear=-0.45, gamma_bulk=-0.2, gamma_odd=0.3, gamma_even=-0.1)
 
 

@@ -17,8 +17,8 @@ lb_step):
   central difference of two FP64 forward runs, a property at any size (the
   oracle's reverse pass stores every state, too much for 3000 steps at 96^3).
 
-Tolerances as in test_gpu_parity.py: populations 1e-12 (FP64) / 2e-5 (FP32)
-of w_i rho0; bead forces 1e-11 / 2e-5 relative; body force and torque the
+Tolerances as in test_gpu_parity.py: populations 1e-12 (FP64) / 1e-5 (FP32)
+of w_i rho0; bead forces 1e-11 / 1e-5 relative; body force and torque the
 same relative to the magnitudes of the bead terms they sum."""
 import numpy as np
 import pytest
@@ -29,8 +29,8 @@ from paper_1604_01829_gb300 import workloads as Wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {64: 1e-12, 32: 2e-5}
-TOL_F = {64: 1e-11, 32: 2e-5}
+TOL = {64: 1e-12, 32: 1e-5}
+TOL_F = {64: 1e-11, 32: 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -5,8 +5,11 @@ Tolerances (written here, derived in the design notes):
   FP64 populations: |f_gpu - f_oracle| <= 1e-12 w_i rho0 after the stated
   steps (summation order and FMA contraction differ; atomics reorder the
   bead-force sums);
-  FP32 storage of f - w_i rho0: <= 2e-5 w_i rho0 (FP32 rounding of
-  deviations of order 1e-2 w_i rho0 over tens of steps).
+  FP32 storage of f - w_i rho0: <= 1e-5 w_i rho0 for populations, and
+  1e-5 relative for bead forces, body force and torque (FP32 rounding of
+  deviations of order 1e-2 w_i rho0 over tens of steps; the worst errors
+  these tests have shown on GB300 are 1.4e-7 for populations and 1.7e-6 for
+  body torques).
 Sizes span several 4x4x4 force tiles and several thread blocks with a ragged
 tail in every direction; odd and even step counts exercise both AA parities.
 """
@@ -20,7 +23,7 @@ from paper_1604_01829_gb300 import workloads as Wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {64: 1e-12, 32: 2e-5}
+TOL = {64: 1e-12, 32: 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -80,13 +83,13 @@ def test_free_raspberry_periodic(precision):
         P.step(3 if k % 2 == 0 else 2)
         assert P.pop_error() <= TOL[precision]
         e = P.body_errors(b)
-        tb = 1e-11 if precision == 64 else 2e-5
+        tb = 1e-11 if precision == 64 else 1e-5
         assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb, e
         assert e["X"] <= tb and e["V"] <= tb * 1e-2 and e["q"] <= tb and e["w"] <= tb * 1e-2, e
     # spread force field of the last step
     Fg = P.gpu.lb_get_node_force()
     Fo = P.orc.Fnode.reshape(3, -1)
-    assert np.abs(Fg - Fo).max() <= (1e-12 if precision == 64 else 2e-5) * np.abs(Fo).max()
+    assert np.abs(Fg - Fo).max() <= (1e-12 if precision == 64 else 1e-5) * np.abs(Fo).max()
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -105,7 +108,7 @@ def test_external_forces_set_between_steps_and_read_back_together(precision):
                F_ext=(0, 5e-4, 0), T_ext=(0, 0, 1e-3))
     P.add_body(sph, [8.8, 15.5, 13.9], mass=34.0, inertia=(50, 50, 50))
     rng = np.random.default_rng(2)
-    tb = 1e-11 if precision == 64 else 2e-5
+    tb = 1e-11 if precision == 64 else 1e-5
     for n, nset, with_T in ((1, 3, True), (2, 2, False), (3, 3, True), (4, 1, True)):
         F = rng.normal(scale=1e-3, size=(nset, 3))
         T = rng.normal(scale=1e-3, size=(nset, 3)) if with_T else None
@@ -137,7 +140,7 @@ def test_md_substeps_match_oracle(precision, nsub):
     P.add_body(ell, [11.5, 12.2, 14.7], [0.8, 0.1, 0.5, -0.2], mass=m,
                inertia=tuple(Wl.solid_ellipsoid_inertia(m, 4.0, 2.0, 2.0)), F_ext=(0, 0, 2e-3), T_ext=(1e-3, 0, 0))
     P.gpu.lb_record_bodies(2, 20)
-    tb = 1e-11 if precision == 64 else 5e-5
+    tb = 1e-11 if precision == 64 else 1e-5
     for n in (3, 2, 5):
         P.step(n)
         assert P.pop_error() <= TOL[precision]
@@ -165,7 +168,7 @@ def test_raspberry_in_pore_with_noise(precision):
         assert P.pop_error() <= TOL[precision]
         for b in range(2):
             e = P.body_errors(b)
-            tb = 1e-11 if precision == 64 else 5e-5
+            tb = 1e-11 if precision == 64 else 1e-5
             assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb, (b, e)
 
 
@@ -361,7 +364,7 @@ def test_tma_ring_depths_with_coupling(stages, ctas):
         P.step(3)
         assert P.pop_error() <= TOL[32]
         e = P.body_errors(0)
-        assert e["bead"] <= 5e-5 and e["F"] <= 5e-5, e
+        assert e["bead"] <= 1e-5 and e["F"] <= 1e-5, e
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -385,7 +388,7 @@ def test_pore_wall_beads_match_oracle(precision, spacing, R, rp, rs, off):
         P.step(3)
         assert P.pop_error() <= TOL[precision]
         e = P.body_errors(0)
-        tb = 1e-11 if precision == 64 else 5e-5
+        tb = 1e-11 if precision == 64 else 1e-5
         assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb and e["X"] <= tb, e
 
 
@@ -417,7 +420,7 @@ def test_step_pairs_replayed_from_a_graph(precision):
     P.add_body(ell, [11.3, 11.8, 9.2], [0.9, 0.2, -0.3, 0.1], mass=80.0, inertia=(40, 120, 120),
                F_ext=(1e-3, 5e-4, 0))
     P.gpu.lb_record_bodies(3, 50)
-    tb = 1e-11 if precision == 64 else 5e-5
+    tb = 1e-11 if precision == 64 else 1e-5
     for n in (9, 6, 4, 5, 16):
         if n == 4:
             P.gpu.lb_set_pore_beads(2.5, 2.5, 0.5, 2e-3)
@@ -446,7 +449,7 @@ def test_channel_walls_match_oracle(precision, nsteps):
     P.orc.set_channel_walls(ulo, uhi)
     P.set_populations(perturbed_populations(P.N, seed=9))
     P.add_body(Wl.sphere_raspberry(2.0), [6.3, 2.4, 4.8], mass=34.0, inertia=(50, 50, 50), F_ext=(0, -1e-3, 0))
-    tb = 1e-11 if precision == 64 else 5e-5
+    tb = 1e-11 if precision == 64 else 1e-5
     for n in nsteps:
         P.step(n)
         assert P.pop_error() <= TOL[precision]

@@ -17,6 +17,7 @@ import math
 import numpy as np
 import pytest
 
+from helpers import observe
 from oracle import construction as C
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +62,7 @@ def test_relaxation_matches_oracle(precision, tol, project, search):
                              project_final=project, pair_search=search)
     for ax, X0, X in zip(SHAPES, starts, out):
         ref = C.relax_shell(X0, ax, steps, dt=0.01, eta=100.0, project_final=project)
-        err = np.abs(X - ref).max()
+        err = observe("X", np.abs(X - ref).max())
         assert err <= tol, (precision, ax, err)
         assert np.abs(X - X0).max() > 100 * tol          # the beads did move
 
@@ -76,7 +77,7 @@ def test_paper_time_step_matches_oracle():
                                  pair_search=search)
         for ax, X0, X in zip(SHAPES, starts, out):
             ref = C.relax_shell(X0, ax, 200, project_final=False)
-            assert np.abs(X - ref).max() <= tol, (precision, ax, np.abs(X - ref).max())
+            assert observe(f"X{precision}", np.abs(X - ref).max()) <= tol, (precision, ax, np.abs(X - ref).max())
             assert np.abs(X - X0).max() > 100 * tol
 
 

@@ -99,7 +99,7 @@ def test_recorder_matches_body_states_and_oracle(precision):
         for k, s in enumerate(steps):
             Xg, qg, o = expect[(s, b)]
             assert np.array_equal(X[k], Xg) and np.array_equal(q[k], qg)
-            tol = 1e-11 if precision == 64 else 2e-5
+            tol = 1e-11 if precision == 64 else 1e-5
             assert np.abs(X[k] - o["X"]).max() <= tol * 10 and np.abs(q[k] - o["q"]).max() <= tol, (s, b)
     # turning it off and on restarts the ring
     P.gpu.lb_record_bodies(0)
