@@ -273,6 +273,53 @@ const char *lb_status_string(lb_status s);
 lb_status lb_adjoint_drag(lb_handle h, int nsteps, int window, int body, int axis, int checkpoints,
                           double *J, double *dJ_dgamma, double *dJ_dbeads);
 
+/* Checkpointing schedules of the adjoint sweep (the states a reversed step
+ * needs are kept or recomputed; the paper itself has no adjoint).
+ *   LB_ADJ_TWO_LEVEL: `snapshots` slots (0 = ceil(sqrt(nsteps))) hold one
+ *     state every K = ceil(nsteps/slots) steps during the forward sweep; each
+ *     segment is re-run from its slot with every step taped, then reversed.
+ *     Memory ~ (slots + K) states, cost one extra forward sweep.
+ *   LB_ADJ_BINOMIAL: at most `snapshots` states (>= 1; 0 = 16), the start
+ *     state included, placed by the binomial rule of Griewank and Walther
+ *     (revolve): with s states and r repetitions, C(s + r, s) steps can be
+ *     reversed, so r is the smallest repetition count with
+ *     C(s + r, s) >= nsteps, and no step is re-run more than r times. Each
+ *     reversed step re-runs only its body prologue and bead coupling from the
+ *     restored state (the reverse pass needs no stored populations). Memory
+ *     (snapshots + 1) states, cost about r forward sweeps. */
+#define LB_ADJ_TWO_LEVEL 0
+#define LB_ADJ_BINOMIAL 1
+typedef struct {
+    int schedule;   /* LB_ADJ_TWO_LEVEL or LB_ADJ_BINOMIAL */
+    int snapshots;  /* see above */
+} lb_adjoint_opts;
+
+/* Where the time of one lb_adjoint_drag_ex call went (device times from
+ * CUDA events on the handle's stream). */
+typedef struct {
+    double alloc_ms;          /* host time allocating the workspace; 0 when a
+                                 previous call's workspace was reused */
+    double forward_ms;        /* the first forward sweep (to the first reversed step) */
+    double recompute_ms;      /* re-run forward steps, taping, saves and restores after it */
+    double reverse_ms;        /* the reverse-pass kernels alone */
+    long long forward_steps;  /* steps of the first sweep */
+    long long recompute_steps;/* forward steps re-run after it (a turn's prologue and
+                                 coupling are not counted) */
+    long long reversed_steps;
+    double workspace_bytes;   /* device memory held by the adjoint's workspace */
+} lb_adjoint_stats;
+
+/* lb_adjoint_drag with a chosen schedule (opts NULL = two-level with
+ * ceil(sqrt(nsteps)) slots) and, if stats is not NULL, the time split above
+ * (the events cost a little; stats = NULL times nothing). The workspace
+ * (snapshots, tapes, adjoint fields) stays allocated with the handle and is
+ * reused by later calls that need no more of it; lb_destroy frees it.
+ * Results are those of lb_adjoint_drag up to the summation order of
+ * atomics in re-run steps. Errors: as lb_adjoint_drag; LB_ERR_ARG for an
+ * unknown schedule or snapshots < 0. */
+lb_status lb_adjoint_drag_ex(lb_handle h, int nsteps, int window, int body, int axis, const lb_adjoint_opts *opts,
+                             double *J, double *dJ_dgamma, double *dJ_dbeads, lb_adjoint_stats *stats);
+
 /* ------------------------------------------------------------------ batches
  * Many independent lattices of uneven size advanced together: the same step
  * as above for every instance (Sec. 1.1, Eq. (latticeboltzmannfriction),

@@ -436,6 +436,7 @@ lb_status lb_destroy(lb_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
+    lbk::adj_free(h);
     void *bufs[] = {h->f, h->gforce, h->gforce_f, h->step_dev, h->err_dev, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1],
                     h->tlist[0], h->tlist[1], h->tcount[0], h->tcount[1],
                     h->db, h->ds, h->dsf, h->dbody_of, h->dFbead, h->partials, h->out4, h->rec, h->dmask, h->dwchan};
@@ -847,6 +848,23 @@ lb_status step_groups(lb_ctx *h, int nsteps) {
     return LB_OK;
 }
 }  // namespace
+
+}  // extern "C"
+
+namespace lbk {
+// The first part of step h->step as the adjoint's turn needs it: the body
+// prologue (kick, drift, clearing of the step's spread-force tiles) and the
+// bead coupling, both on the main stream, without the fluid kernel and the
+// group's finishing launch. The handle is left partly stepped; the caller
+// restores a whole state before stepping it again.
+lb_status ctx_turn(lb_ctx *h) {
+    lb_status s = launch_step_prologue(h, 0, false, h->stream);
+    if (s == LB_OK && !h->hbody_of.empty()) s = launch_step_coupling(h, 0, 0);
+    return s;
+}
+}  // namespace lbk
+
+extern "C" {
 
 lb_status lb_forces(lb_handle h, int id, double F[3], double T[3], double *per_bead) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;

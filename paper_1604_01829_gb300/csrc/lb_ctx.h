@@ -10,6 +10,8 @@
 
 using lbk::Body;
 
+struct AdjWork;   // the adjoint's device workspace (lb_adjoint.cu), kept between calls
+
 struct lb_ctx {
     lb_params p{};
     lbk::Geom g{};
@@ -82,6 +84,7 @@ struct lb_ctx {
     long long timed_n = 0;
     dim3 block{128, 1, 1};
     size_t dev_bytes = 0;
+    AdjWork *adjw = nullptr;
     double g_host[3] = {};
     float gf_host[3] = {};
     std::string err;
@@ -92,4 +95,6 @@ namespace lbk {
 lb_status ctx_upload(lb_ctx *h);
 lb_status ctx_apply_external(lb_ctx *h);
 lb_status ctx_fail(lb_ctx *h, lb_status s, const std::string &m);
+lb_status ctx_turn(lb_ctx *h);
+void adj_free(lb_ctx *h);
 }  // namespace lbk

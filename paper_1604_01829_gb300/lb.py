@@ -38,6 +38,20 @@ class lb_params(C.Structure):
                 ("compensate_force", C.c_int), ("md_substeps", C.c_int)]
 
 
+LB_ADJ_TWO_LEVEL = 0
+LB_ADJ_BINOMIAL = 1
+
+
+class lb_adjoint_opts(C.Structure):
+    _fields_ = [("schedule", C.c_int), ("snapshots", C.c_int)]
+
+
+class lb_adjoint_stats(C.Structure):
+    _fields_ = [("alloc_ms", C.c_double), ("forward_ms", C.c_double), ("recompute_ms", C.c_double),
+                ("reverse_ms", C.c_double), ("forward_steps", C.c_longlong), ("recompute_steps", C.c_longlong),
+                ("reversed_steps", C.c_longlong), ("workspace_bytes", C.c_double)]
+
+
 class lb_info_t(C.Structure):
     _fields_ = [("nodes", C.c_longlong), ("fluid_nodes", C.c_longlong), ("step", C.c_longlong),
                 ("nbodies", C.c_int), ("nbeads", C.c_int), ("precision", C.c_int),
@@ -74,6 +88,8 @@ _SIGS = {
     "lb_checkpoint_save": [C.c_void_p, C.c_void_p, C.c_size_t],
     "lb_checkpoint_load": [C.c_void_p, C.c_void_p, C.c_size_t],
     "lb_adjoint_drag": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
+    "lb_adjoint_drag_ex": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, _dp, _dp, _dp,
+                           C.c_void_p],
     "lb_kernel_time": [C.c_void_p, _dp, _llp],
     "lb_record_bodies": [C.c_void_p, C.c_int, C.c_int],
     "lb_get_trajectory": [C.c_void_p, C.c_int, C.c_int, _llp, _dp, _dp, _ip],
@@ -418,6 +434,20 @@ class LB:
         _check(self.h, load().lb_adjoint_drag(self.h, int(nsteps), int(window), int(body), int(axis),
                                               int(checkpoints), C.byref(J), C.byref(dg), _d(ds)))
         return J.value, dg.value, ds.reshape(-1, 3)
+
+    def lb_adjoint_drag_ex(self, nsteps, window, body=0, axis=2, schedule=LB_ADJ_TWO_LEVEL, snapshots=0,
+                           with_stats=False):
+        """(J, dJ/dgamma, dJ/ds[nbeads, 3], stats dict or None) with a chosen
+        checkpointing schedule (LB_ADJ_TWO_LEVEL or LB_ADJ_BINOMIAL)."""
+        J, dg = C.c_double(), C.c_double()
+        ds = np.zeros(3 * sum(self.bead_counts))
+        o = lb_adjoint_opts(int(schedule), int(snapshots))
+        st = lb_adjoint_stats()
+        _check(self.h, load().lb_adjoint_drag_ex(self.h, int(nsteps), int(window), int(body), int(axis),
+                                                 C.byref(o), C.byref(J), C.byref(dg), _d(ds),
+                                                 C.byref(st) if with_stats else None))
+        stats = {k: getattr(st, k) for k, _ in lb_adjoint_stats._fields_} if with_stats else None
+        return J.value, dg.value, ds.reshape(-1, 3), stats
 
     def lb_kernel_time(self):
         ms = C.c_double()
