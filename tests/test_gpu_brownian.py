@@ -1,0 +1,180 @@
+"""Brownian colloids on the CUDA path (Sec. 2.4: translational diffusion
+from mean squared displacements, Eqs. (dt_lab) and (hasimoto); Sec. 1.1,
+Eq. (latticeboltzmannfriction): the bead noise obeys fluctuation-
+dissipation).
+
+* Equipartition: the set-ups of the oracle pin (tests/test_fdt_pins.py) on
+  the GPU, FP64 and FP32, with longer runs: point colloids (one and two MD
+  substeps) and a six-bead body (translation and rotation) take the fluid's
+  temperature, <M V^2> = <I w^2> = kT within 5 %.
+* Einstein relation: free sphere raspberries (R = 2, gamma = 0.3) in thermal
+  periodic boxes L = 16, 24, 32 (one sphere per box, many independent boxes
+  in one batched handle, the device recorder every 10 steps), FP32. The
+  lab-frame MSD from lb_msd_trajectory grows linearly at lags beyond the
+  fluid's slowest relaxation, with slope 2 D(L) per axis (Eq. (dt_lab)).
+  With the total momentum held at zero (fluid and bead noise both conserve
+  it), the body's displacement is that of the body relative to the fluid,
+  scaled by 1/(1 + M/(rho L^3)); so D(L) (1 + M/(rho L^3))^2 = kT / xi(L),
+  where xi(L) is the drag of the same sphere pulled through the same box
+  with the compensating force on the fluid (deterministic run). Measured on
+  GB300: 0.989, 0.974, 0.992 of kT / xi(L) (standard errors 0.8-1.9 %).
+  Extrapolated with Hasimoto's law, D(L) = D0 - 2.837 kT/(6 pi eta L), the
+  diffusion data give D0 = kT / xi0, xi0 the pulled drag extrapolated the
+  same way, and the 1/L slope of D(L) is Hasimoto's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import observe
+from paper_1604_01829_gb300 import workloads as Wl
+
+pytestmark = pytest.mark.gpu
+
+ZERO_RATES = dict(collision=1, gamma_shear=0.0, gamma_bulk=0.0, gamma_odd=0.0, gamma_even=0.0)
+KT = 1e-4
+ETA = 1.0 / 6.0                       # all rates 0: nu = 1/6, rho0 = 1
+HASIMOTO = -2.837 / (6 * math.pi * ETA)
+OCTAHEDRON = 0.6 * np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1604_01829_gb300 import build
+    build.build()
+
+
+def _equipartition(precision, nbodies, beads, gamma, mass, inertia, nsub=1, steps=24000, burn=400, seed=7, L=10):
+    from paper_1604_01829_gb300 import lb
+    h = lb.LB(L, L, L, precision=precision, kT=KT, seed=seed, gamma_bead=gamma, md_substeps=nsub, **ZERO_RATES)
+    rng = np.random.default_rng(seed)
+    for _ in range(nbodies):
+        h.lb_add_raspberry(beads, rng.uniform(0, L, 3), (1, 0, 0, 0), mass, (inertia,) * 3)
+    h.lb_step(burn)
+    V2 = np.zeros((steps, nbodies, 3))
+    W2 = np.zeros((steps, nbodies, 3))
+    for k in range(steps):
+        h.lb_step(1)
+        for b in range(nbodies):
+            s = h.lb_get_body(b)
+            V2[k, b] = s["V"] ** 2
+            W2[k, b] = s["w"] ** 2
+    h.close()
+    nblk = 20
+
+    def stat(a, m):
+        blk = (a * m / KT).reshape(nblk, -1).mean(axis=1)
+        return blk.mean(), blk.std(ddof=1) / math.sqrt(nblk)
+
+    return stat(V2, mass) + stat(W2, inertia)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nsub", [1, 2])
+def test_point_colloids_take_the_fluid_temperature(precision, nsub):
+    t, st, _, _ = _equipartition(precision, 6, np.zeros((1, 3)), 0.25, 1.0, 1.0, nsub=nsub)
+    observe("T_trans", abs(t - 1))
+    assert st < 0.01, st
+    assert abs(t - 1.0) < 0.05, (t, st)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_a_small_raspberry_takes_the_fluid_temperature(precision):
+    t, st, r, sr = _equipartition(precision, 4, OCTAHEDRON, 0.08, 2.0, 0.4)
+    observe("T_trans", abs(t - 1))
+    observe("T_rot", abs(r - 1))
+    assert st < 0.01 and sr < 0.01, (st, sr)
+    assert abs(t - 1.0) < 0.05 and abs(r - 1.0) < 0.05, (t, r)
+
+
+R_SPHERE, GAMMA = 2.0, 0.3
+
+
+def _mass():
+    return 4.0 / 3.0 * math.pi * R_SPHERE ** 3
+
+
+def _pulled_drag(L, F=1e-3):
+    """xi(L) = F / (V - mean fluid velocity) of the sphere pulled along x
+    with the compensating force on the fluid, deterministic FP64, same
+    rates, friction and bead set as the thermal runs."""
+    from paper_1604_01829_gb300 import lb
+    h = lb.LB(L, L, L, precision=64, gamma_bead=GAMMA, compensate_force=1, **ZERO_RATES)
+    m = _mass()
+    h.lb_add_raspberry(Wl.sphere_raspberry(R_SPHERE), [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], mass=m,
+                       inertia=(0.4 * m * R_SPHERE ** 2,) * 3, F_ext=(F, 0, 0), fixed=2)
+    h.lb_step(int(1.5 * L * L))
+    rel = []
+    for _ in range(10):
+        h.lb_step(max(1, int(0.03 * L * L)))
+        mass, p = h.lb_conservation()
+        rel.append(h.lb_get_body(0)["V"][0] - p[0] / mass)
+    h.close()
+    return F / float(np.mean(rel))
+
+
+def _diffusion(L, ninst, steps, every=10, seed=1604):
+    """D(L) from the lab-frame MSD of ninst independent thermal boxes (one
+    free sphere each, FP32, batched handle, device recorder): the slope of
+    the MSD, averaged over boxes and axes, fitted over lags from 6 to 18
+    relaxation times of the slowest shear mode (L^2 / (4 pi^2 nu)); and its
+    standard error from the spread of the per-box slopes."""
+    from paper_1604_01829_gb300 import lb
+    m = _mass()
+    params = [dict(nx=L, ny=L, nz=L, precision=32, kT=KT, seed=seed, instance=k, gamma_bead=GAMMA, **ZERO_RATES)
+              for k in range(ninst)]
+    B = lb.LBBatch(params)
+    rng = np.random.default_rng(seed + L)
+    beads = Wl.sphere_raspberry(R_SPHERE)
+    for k in range(ninst):
+        B.lb_batch_add_raspberry(k, beads, rng.uniform(0, L, 3), (1, 0, 0, 0), m, (0.4 * m * R_SPHERE ** 2,) * 3)
+    B.lb_batch_step(1000)                            # thermalise
+    nrec = steps // every
+    B.lb_batch_record_bodies(every, nrec)
+    B.lb_batch_step(steps)
+    traj = [B.lb_batch_get_trajectory(k, 0) for k in range(ninst)]
+    X = np.stack([t[1] for t in traj])
+    q = np.stack([t[2] for t in traj])
+    B.close()
+    assert X.shape == (ninst, nrec, 3)
+    t_relax = L * L / (4 * math.pi ** 2 * ETA)
+    lag1, lag2 = int(6 * t_relax / every), int(18 * t_relax / every)
+    msd = lb.lb_msd_trajectory(X, q, lag2)[:, :, 0:3].mean(axis=2)      # per axis: 2 D t
+    lags = np.arange(lag1, lag2 + 1)
+    A = np.stack([np.ones(len(lags)), 2.0 * every * lags], axis=1)
+    per_box = np.linalg.lstsq(A, msd[:, lags - 1].T, rcond=None)[0][1]
+    return float(per_box.mean()), float(per_box.std(ddof=1) / math.sqrt(ninst))
+
+
+def test_einstein_relation_and_hasimoto_law_from_diffusion():
+    Ls = [16, 24, 32]
+    runs = {16: (128, 60000), 24: (96, 60000), 32: (64, 90000)}
+    m = _mass()
+    D, sD, xi = [], [], []
+    for L in Ls:
+        d, s = _diffusion(L, *runs[L])
+        eps = m / L ** 3
+        D.append(d * (1 + eps) ** 2)
+        sD.append(s * (1 + eps) ** 2)
+        xi.append(_pulled_drag(L))
+    D, sD, xi = np.array(D), np.array(sD), np.array(xi)
+    ratio = D * xi / KT
+    print("D(L)", D, "+-", sD, "kT/xi(L)", KT / xi, "ratio", ratio)
+    for L, r, s in zip(Ls, ratio, sD / D):
+        observe(f"einstein_L{L}", abs(r - 1))
+        assert s < 0.025, (L, s)
+        assert abs(r - 1) < 0.06, (L, r, s)
+    # Hasimoto: D(L) = D0 + kT H / L (+ O(L^-3)); slope from the diffusion data
+    x = 1.0 / np.array(Ls, float)
+    wts = 1.0 / sD
+    A = np.stack([np.ones(3), x], axis=1) * wts[:, None]
+    D0, slope = np.linalg.lstsq(A, D * wts, rcond=None)[0]
+    x3 = np.stack([np.ones(3), x ** 3], axis=1)
+    c = np.linalg.lstsq(x3, 1.0 / xi - HASIMOTO * x, rcond=None)[0]
+    xi0 = 1.0 / c[0]
+    print("D0", D0, "kT/xi0", KT / xi0, "slope/(kT H)", slope / (KT * HASIMOTO))
+    observe("D0_vs_kT_over_xi0", abs(D0 * xi0 / KT - 1))
+    observe("hasimoto_slope", abs(slope / (KT * HASIMOTO) - 1))
+    assert abs(D0 * xi0 / KT - 1) < 0.06, (D0, KT / xi0)
+    assert abs(slope / (KT * HASIMOTO) - 1) < 0.3, (slope, KT * HASIMOTO)

@@ -29,6 +29,7 @@ import math
 import numpy as np
 import pytest
 
+from helpers import observe
 from oracle import factors as Fc
 from paper_1604_01829_gb300 import workloads as Wl
 
@@ -79,32 +80,16 @@ HASIMOTO = -2.837 / (6 * math.pi * ETA)
 
 def _pulled_drag(L, beads, mass, axis, F=1e-3):
     """Drag of a translation-only raspberry pulled by F along `axis` in a
-    periodic L^3 box, with the compensating force on the fluid (zero total
-    momentum): xi = F / (V - mean fluid velocity) once the viscous
-    transient (time ~ L^2 / (4 pi^2 nu)) has died out."""
-    from paper_1604_01829_gb300 import lb
-    Fe = [0.0, 0.0, 0.0]
-    Fe[axis] = F
-    h = lb.LB(L, L, L, precision=64, collision=0, tau=1.0, gamma_bead=0.3, compensate_force=1)
-    h.lb_add_raspberry(beads, [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], mass=mass, inertia=(mass,) * 3,
-                       F_ext=Fe, fixed=2)
-    h.lb_step(int(1.5 * L * L))
-    rel = []
-    for _ in range(10):
-        h.lb_step(max(1, int(0.03 * L * L)))
-        m, p = h.lb_conservation()
-        rel.append(h.lb_get_body(0)["V"][axis] - p[axis] / m)
-    h.close()
-    return F / float(np.mean(rel))
+    periodic L^3 box with the compensating force on the fluid (BGK tau = 1,
+    gamma = 0.3, FP64; paper_1604_01829_gb300.drag.pulled_drag)."""
+    from paper_1604_01829_gb300 import drag as D
+    return D.pulled_drag(L, beads, mass, axis, F)
 
 
 def _unbounded(xis, Ls):
-    """xi_0 from 1/xi(L) = 1/xi_0 + HASIMOTO / L + c3 / L^3 (Hasimoto slope
-    fixed, c3 fitted)."""
-    x = 1.0 / np.asarray(Ls, float)
-    y = 1.0 / np.asarray(xis) - HASIMOTO * x
-    c = np.linalg.lstsq(np.stack([np.ones_like(x), x ** 3], axis=1), y, rcond=None)[0]
-    return 1.0 / c[0]
+    """xi_0 by Hasimoto's law (slope fixed, L^-3 term fitted)."""
+    from paper_1604_01829_gb300 import drag as D
+    return D.unbounded(xis, Ls, ETA)
 
 
 def test_prolate_drag_anisotropy_matches_happel_brenner():
@@ -122,56 +107,54 @@ def test_prolate_drag_anisotropy_matches_happel_brenner():
     assert abs(perp / par / expect - 1) < 0.04, (par, perp, perp / par, expect)
 
 
-def _bohlin(lam):
-    return 1.0 / (1 - 2.10444 * lam + 2.08877 * lam ** 3 - 0.94813 * lam ** 5 - 1.372 * lam ** 6
-                  + 3.87 * lam ** 8 - 4.19 * lam ** 10)
+def test_pore_drag_enhancement_across_radial_offsets():
+    """The confinement workload's drag readout (Sec. 2.8 and Sec. 3.3): a
+    sphere raspberry (R = 4) in a periodic pore (R_pore = 20, 48 x 48 x 96,
+    halfway bounce-back) at d = 0, 0.2, 0.4, 0.6 R_pore from the axis,
+    deterministic, FP64 and FP32 (deviation storage); enhancement
+    S = xi_pore / xi_0, xi_0 from the periodic-box extrapolation of the same
+    raspberry (paper_1604_01829_gb300.drag).
 
-
-def test_centreline_pore_drag_matches_bohlin():
-    """Sphere raspberry (R = 4) on the axis of a periodic pore (R_pore = 20,
-    48 x 48 x 96, halfway bounce-back). A sphere moving through fluid at rest
-    far away is the superposition of (A) the sphere pulled by F with no
-    force on the fluid and (B) a free sphere in fluid driven by a uniform
-    force, weighted so that the net flux through the pore vanishes; then
-    K = xi_pore / xi_0, with xi_0 = 6 pi eta a from the periodic-box
-    extrapolation (same raspberry) and lambda = a / R_h, R_h the pore radius
-    seen by Poiseuille flow. Within 2 % of Bohlin's K(lambda)
-    (measured 0.3 %)."""
-    from paper_1604_01829_gb300 import lb
+    * Axial motion (z^p): on the axis S is within 2 % of Bohlin's K(lambda)
+      (lambda = a / R_h, a = xi_0 / (6 pi eta), R_h the pore radius seen by
+      Poiseuille flow) and beyond its leading term 1 + 2.104 lambda. Off the
+      axis S first falls and then rises towards the wall: Sec. 3.3 states that
+      the reference values for this direction have their minimum at an
+      off-centre position (the pressure force is largest at the centre, the
+      lubrication force at the wall), a minimum the paper's own simulations
+      did not capture. Measured on GB300: 1.600, 1.588, 1.568, 1.614.
+    * Radial motion towards the wall (x^p, head-on): S rises monotonically
+      with the offset, as Sec. 3.3 describes, and on the axis it is below the
+      axial value (a sphere on the axis is hindered less moving across the
+      pore than along it).
+    * FP32 gives the FP64 values within 2e-4.
+    The off-axis values themselves (Happel-Brenner / Higdon-Muldowney) are
+    not available here: parity unpinned beyond these shapes."""
+    from paper_1604_01829_gb300 import drag as D
     beads = Wl.sphere_raspberry(4.0)
     mass = 4.0 / 3.0 * math.pi * 64.0
-    R, nx, nz, g = 20.0, 48, 96, 1e-6
-
-    def pore(F=0.0, gz=0.0, body=True):
-        h = lb.LB(nx, nx, nz, precision=64, collision=0, tau=1.0, gamma_bead=0.3, body_force=(0, 0, gz))
-        h.lb_set_pore(R, 2)
-        if body:
-            h.lb_add_raspberry(beads, [nx / 2, nx / 2, nz / 2 + 0.3], mass=mass, inertia=(1e3,) * 3,
-                               F_ext=(0, 0, F), fixed=2)
-        h.lb_step(6000)
-        U, P = [], []
-        for _ in range(20):
-            h.lb_step(100)
-            P.append(h.lb_conservation()[1][2])
-            if body:
-                U.append(h.lb_get_body(0)["V"][2])
-        h.close()
-        return (float(np.mean(U)) if body else None), float(np.mean(P))
-
-    _, P0 = pore(gz=g, body=False)
-    R_h = (8 * ETA * (P0 / nz) / (math.pi * g)) ** 0.25     # Poiseuille flux pi g R^4 / (8 eta)
+    R, nx, nz = 20.0, 48, 96
+    R_h = D.pore_flux_radius(nx, nz, R, ETA)
     assert abs(R_h - R) < 0.05, R_h                          # halfway wall at R
-    F = 1e-3
-    UA, PA = pore(F=F)
-    UB, PB = pore(gz=g)
-    U = UA - PA / PB * UB
-    xi_pore = F / U
     Ls = [32, 48, 64, 80]
-    xi0 = _unbounded([_pulled_drag(L, beads, mass, 0) for L in Ls], Ls)
+    xi0 = D.unbounded([D.pulled_drag(L, beads, mass, 0) for L in Ls], Ls, ETA)
     lam = xi0 / (6 * math.pi * ETA) / R_h
-    K = xi_pore / xi0
-    assert abs(K / _bohlin(lam) - 1) < 0.02, (K, lam, _bohlin(lam))
-    assert K > 1 + 2.104 * lam                               # beyond the leading term
+    offs = [0.0, 0.2, 0.4, 0.6]
+    Sz = {p: np.array([D.pore_drag(nx, nz, R, beads, mass, offset=b * R, precision=p) / xi0 for b in offs])
+          for p in (64, 32)}
+    Sx = {p: np.array([D.pore_radial_drag(nx, nz, R, beads, mass, offset=b * R, precision=p) / xi0 for b in offs])
+          for p in (64, 32)}
+    print("lambda", lam, "Bohlin", D.bohlin(lam), "Sz64", Sz[64], "Sz32", Sz[32], "Sx64", Sx[64], "Sx32", Sx[32])
+    assert abs(Sz[64][0] / D.bohlin(lam) - 1) < 0.02, (Sz[64][0], lam, D.bohlin(lam))
+    assert Sz[64][0] > 1 + 2.104 * lam
+    for p in (64, 32):
+        kmin = int(np.argmin(Sz[p]))
+        assert 0 < kmin < len(offs) - 1, (p, Sz[p])         # off-centre minimum of the axial drag
+        assert np.all(np.diff(Sx[p]) > 0), (p, Sx[p])       # head-on: rising towards the wall
+        assert Sx[p][0] < Sz[p][0], (p, Sx[p], Sz[p])
+    rel = max(np.abs(Sz[32] / Sz[64] - 1).max(), np.abs(Sx[32] / Sx[64] - 1).max())
+    observe("S32_vs_S64", rel)
+    assert rel < 2e-4, rel
 
 
 def test_stokes_flow_set_up_gives_the_unbounded_drag():

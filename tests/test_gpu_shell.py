@@ -10,8 +10,10 @@ Tolerances: FP64 differs from the oracle by contraction (FMA) and division
 rounding only, O(1e-15) per operation, and the damped scheme does not amplify
 it over the short runs compared: 1e-9 absolute on positions of order 1-10.
 FP32 rounds positions to 2^-21 ~ 5e-7 at |x| < 8 and forces to ~1e-6
-relative each step; over 150 contracting steps that stays below 1e-4
-absolute."""
+relative each step, and the damped, contracting scheme does not amplify
+it: over the 150-200 steps compared the errors stay below 1e-5 absolute
+(worst seen on GB300: 4.0e-6; the FP32 kernel sums in a fixed order, so the
+figure repeats run to run)."""
 import math
 
 import numpy as np
@@ -51,7 +53,7 @@ def test_nearest_surface_points_match_oracle(precision, tol):
         assert np.abs(((X / np.array(ax)) ** 2).sum(1) - 1).max() < (1e-12 if precision == 64 else 2e-6)
 
 
-@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
 @pytest.mark.parametrize("project", [False, True])
 @pytest.mark.parametrize("search", [1, 2])
 def test_relaxation_matches_oracle(precision, tol, project, search):
@@ -72,7 +74,7 @@ def test_paper_time_step_matches_oracle():
     0.8 beads per unit area, FP64 and FP32."""
     from paper_1604_01829_gb300 import lb
     starts = _spread_starts()
-    for precision, tol, search in ((64, 1e-9, 1), (64, 1e-9, 2), (32, 1e-4, 2)):
+    for precision, tol, search in ((64, 1e-9, 1), (64, 1e-9, 2), (32, 1e-5, 2)):
         out = lb.lb_relax_shells(SHAPES, starts, steps=200, precision=precision, project_final=False,
                                  pair_search=search)
         for ax, X0, X in zip(SHAPES, starts, out):
@@ -107,7 +109,7 @@ def test_one_step_at_full_shell_sizes_on_sampled_beads(n, search):
         assert np.allclose(X[i], X0[i] + dt * dt * F, rtol=0, atol=1e-10 if p64 == 64 else 1e-5), i
     (X32,) = lb.lb_relax_shells([ax], [X0], steps=1, dt=dt, eta=1000.0, precision=32, project_final=False,
                                 pair_search=search)
-    assert np.abs(X32 - X).max() < 1e-4
+    assert observe("X32_vs_64", np.abs(X32 - X).max()) < 1e-4
 
 
 @pytest.mark.parametrize("precision", [64, 32])
