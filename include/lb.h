@@ -335,7 +335,11 @@ typedef struct lb_batch_ctx *lb_batch_handle;
 lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_batch_handle *out);
 lb_status lb_batch_destroy(lb_batch_handle h);
 /* As lb_set_pore / lb_add_raspberry for instance `inst` (before the first
- * step); *body_id is the body's index within its instance. */
+ * step); *body_id is the body's index within its instance. From the first
+ * step on, a pore instance stores its fluid nodes only (populations set
+ * before are carried over; wall nodes read back as fluid at rest), which
+ * limits its cross-section to 65534 fluid positions (the first step returns
+ * LB_ERR_ARG for a larger one). */
 /* Pore-wall beads of one instance, as lb_set_pore_beads (after its pore,
  * before the first step). */
 lb_status lb_batch_set_pore_beads(lb_batch_handle h, int inst, double spacing, double r_pore_bead,

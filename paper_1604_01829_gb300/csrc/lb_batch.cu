@@ -35,11 +35,13 @@ struct BInst {
     uint32_t mx, my;             // ceil(2^32 / nx), ceil(2^32 / ny) for exact quotients (fastdiv)
     int fastdiv;                 // 1 when n * nx and (n / nx) * ny stay below 2^32 for every node
     long long off;               // element offset of plane 0 in the population pool
-    long long ps;                // plane stride (elements): the node count rounded up to 32, so
-                                 // that every plane of every instance starts on a 128-byte line
+    long long ps;                // population plane stride (elements): the node count rounded up
+                                 // to 32 (dense), or the fluid node count rounded up to 32 (compact
+                                 // pore layout), so that every plane starts on a 128-byte line
+    long long fs;                // force-pool plane stride: the node count rounded up to 32
+    int cmode;                   // 1: compact pore layout (g.cmap, g.cnbr), from the first upload on
     long long foff;              // offset of this instance's [3][N] block in a force pool
     long long toff;              // offset of its tile flags
-    long long moff;              // pore instances: offset of the cross-section wall masks, else -1
     // work items of the fluid kernel: all N nodes of a periodic instance; the
     // fluid nodes only of a pore instance, as (position across the axis j,
     // coordinate along it a): node = fluid[loff + j] + a * astride, with j
@@ -71,17 +73,70 @@ struct BatchArgs {
     void *pool;
     const void *F;               // spread force of this step (pool, storage precision), nullptr without bodies
     const int *tiles;
-    const uint32_t *masks;       // per pore cross-section position: bit 31 wall node, bit i upstream of link i is wall
     const uint32_t *fluid;       // fluid positions across the axis of the pore instances (BInst::loff)
     const unsigned long long *step_base;
     uint32_t step_off;
     // index checks of checked builds (-DLB_CHECKS): the error word and the
     // extents of the shared tables (other builds compile the checks out)
     int *err;
-    long long nmask, nfluid, ttot;
+    long long nfluid, ttot;
 };
 
 namespace {
+
+// Odd-step loads and stores of one fluid node of a compact pore instance,
+// with the pore axis AX known at compile time so that each link's in-plane
+// direction and shift along the axis are constants: the node's 8 in-plane
+// neighbours come in one 16-byte load (rec), then per link one compare and
+// one address. m = the node's compact index, j its position across the axis,
+// l its coordinate along the axis (nl nodes), sj / sa the compact strides of
+// the position across and along the axis.
+__device__ __forceinline__ int nbr_of(const uint4 &rec, int d) {
+    const uint32_t w = d < 2 ? rec.x : (d < 4 ? rec.y : (d < 6 ? rec.z : rec.w));
+    return (int)((d & 1) ? (w >> 16) : (w & 0xFFFFu));
+}
+
+template <int AX>
+__device__ __forceinline__ void axis_parts(int i, int &u, int &v, int &al) {
+    if (AX == 2) { u = cx(i); v = cy(i); al = cz(i); }
+    else if (AX == 1) { u = cx(i); v = cz(i); al = cy(i); }
+    else { u = cy(i); v = cz(i); al = cx(i); }
+}
+
+template <int AX, typename T, typename R>
+__device__ __forceinline__ void compact_odd_load(const T *P, uint32_t base, uint32_t N, const uint4 &rec,
+                                                 uint32_t j, uint32_t l, uint32_t nl, uint32_t sj, uint32_t sa,
+                                                 uint32_t m, R (&f)[19], int *err) {
+    // along-axis part of the upstream node x - c_i for c_i's component -1, 0, +1
+    const uint32_t o[3] = {(l + 1 == nl ? 0 : l + 1) * sa, l * sa, (l == 0 ? nl - 1 : l - 1) * sa};
+    f[0] = P[base + chk(m, N, err)];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        int u, v, al;
+        axis_parts<AX>(i, u, v, al);
+        const int js = (u == 0 && v == 0) ? (int)j : nbr_of(rec, dir8(-u, -v));
+        const uint32_t idx = js == 0xFFFF ? (uint32_t)i * N + m : (uint32_t)opp(i) * N + (uint32_t)js * sj + o[al + 1];
+        f[i] = P[base + chk(idx, 19LL * N, err)];
+    }
+}
+
+template <int AX, typename T, typename R>
+__device__ __forceinline__ void compact_odd_store(T *P, uint32_t base, uint32_t N, const uint4 &rec,
+                                                  uint32_t j, uint32_t l, uint32_t nl, uint32_t sj, uint32_t sa,
+                                                  uint32_t m, const R (&f)[19], int *err) {
+    // along-axis part of the downstream node x + c_i for c_i's component -1, 0, +1
+    const uint32_t o[3] = {(l == 0 ? nl - 1 : l - 1) * sa, l * sa, (l + 1 == nl ? 0 : l + 1) * sa};
+    P[base + chk(m, N, err)] = f[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        int u, v, al;
+        axis_parts<AX>(i, u, v, al);
+        const int jd = (u == 0 && v == 0) ? (int)j : nbr_of(rec, dir8(u, v));
+        // a wall downstream returns the population into this node's opposite slot
+        const uint32_t idx = jd == 0xFFFF ? (uint32_t)opp(i) * N + m : (uint32_t)i * N + (uint32_t)jd * sj + o[al + 1];
+        P[base + chk(idx, 19LL * N, err)] = f[i];
+    }
+}
 
 template <typename T, int COLL, bool NOISE, bool ODD, bool COMMON>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_batch_collide(const BatchArgs a) {
@@ -98,16 +153,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         const int k = chk(__ldg(a.tile_inst + t), a.n, a.err);
         const BInst &I = a.inst[k];
         const Geom g = I.g;
-        const uint32_t N = (uint32_t)I.ps;          // plane stride; nodes n < g.N
+        const uint32_t N = (uint32_t)I.ps;          // population plane stride
         const uint32_t w = (uint32_t)(t - __ldg(a.tile_start + k)) * blockDim.x + threadIdx.x;
         if (w >= I.nwork) continue;
-        uint32_t n = w;
-        if (I.loff >= 0) {                   // compacted pore instance: fluid nodes only
+        // a pore instance stores its fluid nodes only (compact layout): work
+        // item w is compact node w, at position j across the axis and l along
+        // it; n is the node's index in the dense numbering (coordinates,
+        // forces, noise counter)
+        const bool compact = I.cmode != 0;
+        uint32_t n = w, j = 0, l = 0;
+        if (compact) {
             const uint32_t d = g.pore_axis == 0 ? I.nax : I.ncs;
             const uint32_t q = I.wfast ? __umulhi(w, I.mw) : w / d;
             const uint32_t rm = w - q * d;
-            const uint32_t j = g.pore_axis == 0 ? q : rm, ax = g.pore_axis == 0 ? rm : q;
-            n = __ldg(a.fluid + chk(I.loff + j, a.nfluid, a.err)) + ax * I.astride;
+            j = g.pore_axis == 0 ? q : rm;
+            l = g.pore_axis == 0 ? rm : q;
+            n = __ldg(a.fluid + chk(I.loff + j, a.nfluid, a.err)) + l * I.astride;
         }
         uint32_t r, z;
         if (I.fastdiv) {
@@ -118,18 +179,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
             z = r / (uint32_t)g.ny;
         }
         const int x = (int)(n - r * (uint32_t)g.nx), y = (int)(r - z * (uint32_t)g.ny);
-        // bit i set: the upstream neighbour x - c_i is a wall node; the
-        // masks depend only on the position across the pore axis and are
-        // tabulated once per instance (bit 31: the node itself is a wall)
-        uint32_t wall_up = 0;
-        if (g.pore_axis >= 0) {
-            const uint32_t cs = g.pore_axis == 2 ? (uint32_t)x + (uint32_t)g.nx * (uint32_t)y
-                              : (g.pore_axis == 1 ? (uint32_t)x + (uint32_t)g.nx * z
-                                                  : (uint32_t)y + (uint32_t)g.ny * z);
-            const uint32_t m = __ldg(a.masks + chk(I.moff + cs, a.nmask, a.err));
-            if (m >> 31) continue;
-            if (ODD) wall_up = m;
-        }
         // 32-bit element indices into the pool (the pool holds < 2^32 elements)
         T *P = static_cast<T *>(a.pool);
         const uint32_t base = (uint32_t)I.off;
@@ -141,25 +190,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         auto at = [&](int i, uint32_t node) -> T & { return P[base + (uint32_t)i * N + chk(node, N, a.err)]; };
         R f[19];
         if (!ODD) {
+            const uint32_t m = compact ? w : n;
 #pragma unroll
-            for (int i = 0; i < 19; ++i) f[i] = at(i, n);
-        } else {
+            for (int i = 0; i < 19; ++i) f[i] = at(i, m);
+        } else if (!compact) {
             f[0] = at(0, n);
 #pragma unroll
-            for (int i = 1; i < 19; ++i) {
-                const uint32_t src = (uint32_t)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]);
-                if ((wall_up >> i) & 1u) f[i] = at(i, n);
-                else f[i] = at(opp(i), src);
-            }
+            for (int i = 1; i < 19; ++i) f[i] = at(opp(i), (uint32_t)(xo[1 - cx(i)] + yo[1 - cy(i)] + zo[1 - cz(i)]));
+        } else {
+            // the upstream node x - c_i: its compact position from the
+            // neighbour table, -1 for a wall node (the population bounced back)
+            const uint4 rec = __ldg(reinterpret_cast<const uint4 *>(g.cnbr) + chk(j, (long long)I.ncs, a.err));
+            const uint32_t nl = I.nax, sj = (uint32_t)g.csj, sa = (uint32_t)g.csa;
+            if (g.pore_axis == 2) compact_odd_load<2>(P, base, N, rec, j, l, nl, sj, sa, w, f, a.err);
+            else if (g.pore_axis == 1) compact_odd_load<1>(P, base, N, rec, j, l, nl, sj, sa, w, f, a.err);
+            else compact_odd_load<0>(P, base, N, rec, j, l, nl, sj, sa, w, f, a.err);
         }
         R Fx, Fy, Fz;
         if constexpr (DEV) { Fx = I.gf[0]; Fy = I.gf[1]; Fz = I.gf[2]; }
         else { Fx = I.gd[0]; Fy = I.gd[1]; Fz = I.gd[2]; }
         if (a.tiles && a.tiles[chk(I.toff + tile_of(x, y, (int)z, I.ntx, I.nty), a.ttot, a.err)]) {
             const T *Fn = static_cast<const T *>(a.F) + I.foff;
-            Fx += Fn[chk(n, N, a.err)];
-            Fy += Fn[(size_t)N + n];
-            Fz += Fn[2 * (size_t)N + n];
+            const size_t FS = (size_t)I.fs;
+            Fx += Fn[chk((long long)n, (long long)FS, a.err)];
+            Fy += Fn[FS + n];
+            Fz += Fn[2 * FS + n];
         }
         uint32_t step = 0;
         if (NOISE) step = (uint32_t)(*a.step_base) + a.step_off;
@@ -172,29 +227,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_bat
         const uint32_t N2 = *(const volatile uint32_t *)&a.inst[k].ps;
         auto at2 = [&](int i, uint32_t node) -> T & { return P[base2 + (uint32_t)i * N2 + chk(node, N2, a.err)]; };
         if (!ODD) {
+            const uint32_t m = compact ? w : n;
 #pragma unroll
-            for (int i = 0; i < 19; ++i) at2(opp(i), n) = f[i];
-        } else {
-            // the wall mask again from the table (L1) rather than held in a
-            // register across the collision
-            uint32_t wall_dn = 0;
-            const int axis2 = *(const volatile int *)&a.inst[k].g.pore_axis;
-            if (axis2 >= 0) {
-                const long long moff2 = *(const volatile long long *)&a.inst[k].moff;
-                uint32_t cs;
-                if (axis2 == 2) cs = (uint32_t)(xo[1] + yo[1]);
-                else if (axis2 == 1) cs = (uint32_t)(xo[1] + zo[1] / *(const volatile int *)&a.inst[k].g.ny);
-                else cs = (uint32_t)((yo[1] + zo[1]) / *(const volatile int *)&a.inst[k].g.nx);
-                wall_dn = __ldg(a.masks + chk(moff2 + cs, a.nmask, a.err));
-            }
+            for (int i = 0; i < 19; ++i) at2(opp(i), m) = f[i];
+        } else if (!compact) {
             at2(0, n) = f[0];
 #pragma unroll
-            for (int i = 1; i < 19; ++i) {
-                const uint32_t dst = (uint32_t)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]);
-                // downstream node x + c_i is upstream node x - c_opp(i)
-                if ((wall_dn >> opp(i)) & 1u) at2(opp(i), n) = f[i];
-                else at2(i, dst) = f[i];
-            }
+            for (int i = 1; i < 19; ++i) at2(i, (uint32_t)(xo[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)])) = f[i];
+        } else {
+            // the downstream node x + c_i; a wall there returns the population
+            // into this node's opposite slot (halfway bounce-back)
+            const int axis2 = *(const volatile int *)&a.inst[k].g.pore_axis;
+            const uint16_t *cnb = *(const uint16_t *const volatile *)&a.inst[k].g.cnbr;
+            const uint32_t nl = *(const volatile uint32_t *)&a.inst[k].nax;
+            const uint4 rec = __ldg(reinterpret_cast<const uint4 *>(cnb) + chk(j, (long long)a.inst[k].ncs, a.err));
+            const uint32_t sj = (uint32_t)*(const volatile int *)&a.inst[k].g.csj;
+            const uint32_t sa = (uint32_t)*(const volatile int *)&a.inst[k].g.csa;
+            if (axis2 == 2) compact_odd_store<2>(P, base2, N2, rec, j, l, nl, sj, sa, w, f, a.err);
+            else if (axis2 == 1) compact_odd_store<1>(P, base2, N2, rec, j, l, nl, sj, sa, w, f, a.err);
+            else compact_odd_store<0>(P, base2, N2, rec, j, l, nl, sj, sa, w, f, a.err);
         }
     }
 }
@@ -233,7 +284,7 @@ __global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
     const BInst &I = b.inst[b.bodies[chk(b.bead_body[kk], b.nbodies, b.err)].inst];
     CoupleArgs a{};
     a.g = I.g;
-    a.g.N = I.ps;                 // the coupling indexes planes with g.N: the padded stride
+    a.g.N = I.fs;                 // force planes (and dense population planes): the padded node count
     a.f = static_cast<const T *>(b.pool) + I.off;
     a.fp32 = b.fp32;
     a.odd = b.odd;
@@ -317,8 +368,8 @@ __global__ void k_batch_pre(Body *bodies, int nb, int finish_prev, T *F, int *ti
             T *Fi = F + I.foff;
             const long long nn = nidx(I.g, x, y, z);
             Fi[nn] = T(0);
-            Fi[I.ps + nn] = T(0);
-            Fi[2 * I.ps + nn] = T(0);
+            Fi[I.fs + nn] = T(0);
+            Fi[2 * I.fs + nn] = T(0);
         }
         if (l == 0) tiles[gt] = 0;
     }
@@ -332,10 +383,13 @@ __global__ void k_batch_gather(const T *A, Geom g, long long Nn, bool odd, doubl
     const int x = (int)(n % g.nx);
     const long long r = n / g.nx;
     const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    // wall nodes hold no populations (compact layout) or stale ones: they
+    // read as fluid at rest
     const bool wall = is_wall(g, x, y, z);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const T v = wall ? A[(long long)i * g.N + n] : load_pre(A, g, x, y, z, n, i, odd);
+        const T v = wall ? (sizeof(T) == 4 ? T(0) : T(wq(i) * rho0))
+                         : (g.cmap ? compact_load_pre(A, g, x, y, z, i, odd) : load_pre(A, g, x, y, z, n, i, odd));
         out[(long long)i * Nn + n] = sizeof(T) == 4 ? (double)v + wq(i) * rho0 : (double)v;
     }
 }
@@ -351,7 +405,9 @@ __global__ void k_batch_scatter(T *A, Geom g, long long Nn, bool odd, double rho
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const double v = in[(long long)i * Nn + n];
-        store_pre(A, g, x, y, z, n, i, odd, sizeof(T) == 4 ? (T)(v - wq(i) * rho0) : (T)v);
+        const T tv = sizeof(T) == 4 ? (T)(v - wq(i) * rho0) : (T)v;
+        if (g.cmap) compact_store_pre(A, g, x, y, z, i, odd, tv);
+        else store_pre(A, g, x, y, z, n, i, odd, tv);
     }
 }
 
@@ -415,8 +471,10 @@ struct lb_batch_ctx {
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
     bool any_wall = false;                  // some instance has pore-wall beads
-    // wall masks (BInst::moff) and fluid positions (BInst::loff) of the pore instances
-    uint32_t *dmask = nullptr;
+    // fluid positions (BInst::loff) of the pore instances and their compact
+    // layout's position map and neighbour table (Geom::cmap, Geom::cnbr)
+    int *dcmap = nullptr;
+    uint16_t *dcnbr = nullptr;
     uint32_t *dfluid = nullptr;
     // trajectory recorder ([rec_cap][nbodies][7], records k >= rec_k0)
     double *rec = nullptr;
@@ -435,7 +493,7 @@ struct lb_batch_ctx {
     int *derr = nullptr;
     int *herr = nullptr;
     int nsub = 1;                           // MD substeps per LB step (shared by the instances)
-    long long nmask = 0, nfluidpos = 0;
+    long long nfluidpos = 0;
 };
 
 namespace {
@@ -575,29 +633,13 @@ lb_status rebuild_schedule(lb_batch_ctx *h) {
 
 lb_status upload(lb_batch_ctx *h) {
     if (h->uploaded) return LB_OK;
-    // wall masks of the pore instances, one per position across the axis
-    long long mtot = 0;
-    for (int k = 0; k < h->n; ++k) {
-        BInst &I = h->hinst[k];
-        I.moff = -1;
-        if (I.g.pore_axis < 0) continue;
-        I.moff = mtot;
-        mtot += I.g.pore_axis == 2 ? (long long)I.g.nx * I.g.ny
-              : (I.g.pore_axis == 1 ? (long long)I.g.nx * I.g.nz : (long long)I.g.ny * I.g.nz);
-    }
-    h->nmask = mtot;
-    if (mtot > 0) {
-        lb_status s = balloc(h, &h->dmask, sizeof(uint32_t) * (size_t)mtot);
-        if (s != LB_OK) return s;
-        for (int k = 0; k < h->n; ++k) {
-            const BInst &I = h->hinst[k];
-            if (I.moff < 0) continue;
-            BCUDA(h, lbk::launch_build_masks(I.g, h->dmask + I.moff, h->stream));
-        }
-    }
     // fluid positions across the axis of each pore instance: the fluid
-    // kernel's work items are its fluid nodes only
+    // kernel's work items are its fluid nodes only, and from here on the
+    // instance stores only those (compact layout, converted in place below)
     std::vector<uint32_t> fl;
+    std::vector<int> cm;
+    std::vector<uint16_t> cn;
+    std::vector<long long> cmap_off, cnbr_off;
     for (int k = 0; k < h->n; ++k) {
         BInst &I = h->hinst[k];
         if (I.g.pore_axis < 0) continue;
@@ -614,6 +656,37 @@ lb_status upload(lb_batch_ctx *h) {
                 fl.push_back((uint32_t)node);
             }
         I.ncs = (uint32_t)((long long)fl.size() - I.loff);
+        if (I.ncs >= 0xFFFF)
+            return bfail(h, LB_ERR_ARG, "instance " + std::to_string(k) + ": a batched pore's cross-section holds at "
+                                        "most 65534 fluid positions (the compact layout indexes them in 16 bits)");
+        // compact layout: dense position across the axis -> compact position
+        // (-1 for a wall), and the 9 in-plane neighbours of each compact
+        // position (periodic across the box, -1 where the neighbour is a wall)
+        const long long coff = (long long)cm.size();
+        for (int b = 0; b < nb; ++b)
+            for (int a = 0; a < na; ++a) {
+                const long long da = 2LL * a + 1 - na, db = 2LL * b + 1 - nb;
+                cm.push_back(da * da + db * db >= I.g.pore_t ? -1 : 0);
+            }
+        int jc = 0;
+        for (long long q = coff; q < (long long)cm.size(); ++q)
+            if (cm[q] >= 0) cm[q] = jc++;
+        const long long noff = (long long)cn.size();
+        for (int b = 0; b < nb; ++b)
+            for (int a = 0; a < na; ++a) {
+                if (cm[coff + a + (long long)na * b] < 0) continue;
+                uint16_t rec[8];
+                for (int v = -1; v <= 1; ++v)
+                    for (int u = -1; u <= 1; ++u) {
+                        if (u == 0 && v == 0) continue;
+                        const int a2 = (a + u + na) % na, b2 = (b + v + nb) % nb;
+                        const int q = cm[coff + a2 + (long long)na * b2];
+                        rec[lbk::dir8(u, v)] = q < 0 ? (uint16_t)0xFFFF : (uint16_t)q;
+                    }
+                cn.insert(cn.end(), rec, rec + 8);
+            }
+        cmap_off.push_back(coff);
+        cnbr_off.push_back(noff);
         I.nax = (uint32_t)(ax == 0 ? I.g.nx : (ax == 1 ? I.g.ny : I.g.nz));
         I.astride = (uint32_t)(ax == 0 ? 1 : (ax == 1 ? I.g.nx : I.g.nx * I.g.ny));
         I.nwork = I.ncs * I.nax;
@@ -626,9 +699,59 @@ lb_status upload(lb_batch_ctx *h) {
     if (!fl.empty()) {
         lb_status s = balloc(h, &h->dfluid, sizeof(uint32_t) * fl.size());
         if (s != LB_OK) return s;
+        if ((s = balloc(h, &h->dcmap, sizeof(int) * cm.size())) != LB_OK) return s;
+        if ((s = balloc(h, &h->dcnbr, sizeof(uint16_t) * cn.size())) != LB_OK) return s;
         BCUDA(h, cudaMemcpyAsync(h->dfluid, fl.data(), sizeof(uint32_t) * fl.size(), cudaMemcpyHostToDevice,
                                  h->stream));
-        BCUDA(h, cudaStreamSynchronize(h->stream));
+        BCUDA(h, cudaMemcpyAsync(h->dcmap, cm.data(), sizeof(int) * cm.size(), cudaMemcpyHostToDevice, h->stream));
+        BCUDA(h, cudaMemcpyAsync(h->dcnbr, cn.data(), sizeof(uint16_t) * cn.size(), cudaMemcpyHostToDevice, h->stream));
+        // convert each pore instance to the compact layout in place (its
+        // region keeps its dense size): the populations in the dense layout
+        // (step 0, even parity) go out through the gather and come back
+        // through the compact scatter
+        long long nmax = 0;
+        for (int k = 0; k < h->n; ++k)
+            if (h->hinst[k].g.pore_axis >= 0) nmax = std::max(nmax, h->hinst[k].g.N);
+        double *tmp = nullptr;
+        if (cudaMalloc((void **)&tmp, sizeof(double) * 19 * (size_t)nmax) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(h, LB_ERR_OOM, "no device memory to convert the pore instances' layout");
+        }
+        int pi = 0;
+        for (int k = 0; k < h->n && s == LB_OK; ++k) {
+            BInst &I = h->hinst[k];
+            if (I.g.pore_axis < 0) continue;
+            const long long N = I.g.N;
+            const unsigned grid = (unsigned)((N + 255) / 256);
+            lbk::Geom gd = I.g;
+            gd.N = I.ps;
+            gd.cmap = nullptr;
+            if (h->fp32) lbk::k_batch_gather<float><<<grid, 256, 0, h->stream>>>((const float *)h->pool + I.off, gd, N, false, h->p[k].rho0, tmp);
+            else lbk::k_batch_gather<double><<<grid, 256, 0, h->stream>>>((const double *)h->pool + I.off, gd, N, false, h->p[k].rho0, tmp);
+            I.cmode = 1;
+            I.ps = ((long long)I.ncs * I.nax + 31) / 32 * 32;
+            I.g.cmap = h->dcmap + cmap_off[pi];
+            I.g.cnbr = h->dcnbr + cnbr_off[pi];
+            I.g.cps = I.ps;
+            I.g.csj = I.g.pore_axis == 0 ? (int)I.nax : 1;
+            I.g.csa = I.g.pore_axis == 0 ? 1 : (int)I.ncs;
+            ++pi;
+            lbk::Geom gc = I.g;
+            gc.N = I.ps;
+            if (h->fp32) {
+                lbk::k_batch_init<float><<<(unsigned)((I.ps + 255) / 256), 256, 0, h->stream>>>((float *)h->pool + I.off, I.ps, h->p[k].rho0);
+                lbk::k_batch_scatter<float><<<grid, 256, 0, h->stream>>>((float *)h->pool + I.off, gc, N, false, h->p[k].rho0, tmp);
+            } else {
+                lbk::k_batch_init<double><<<(unsigned)((I.ps + 255) / 256), 256, 0, h->stream>>>((double *)h->pool + I.off, I.ps, h->p[k].rho0);
+                lbk::k_batch_scatter<double><<<grid, 256, 0, h->stream>>>((double *)h->pool + I.off, gc, N, false, h->p[k].rho0, tmp);
+            }
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) s = bfail(h, LB_ERR_CUDA, std::string("compact layout: ") + cudaGetErrorString(e));
+        }
+        const cudaError_t e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        if (s != LB_OK) return s;
+        if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("compact layout: ") + cudaGetErrorString(e));
         if ((s = rebuild_schedule(h)) != LB_OK) return s;   // tile counts follow the work items
     }
     // instance table with final body forces / compensation
@@ -759,14 +882,12 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     a.order = h->order == 1 ? 1 : 0;
     a.chunk = (h->ntiles + grid - 1) / grid;
     a.pool = h->pool;
-    a.masks = h->dmask;
     a.fluid = h->dfluid;
     a.F = coupled ? h->Fbuf[cur] : nullptr;
     a.tiles = coupled ? h->tiles[cur] : nullptr;
     a.step_base = h->step_dev;
     a.step_off = (uint32_t)k;
     a.err = h->derr;
-    a.nmask = h->nmask;
     a.nfluid = h->nfluidpos;
     a.ttot = h->Ttot;
     if (record) BCUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
@@ -894,7 +1015,6 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         I.g.nx = p.nx; I.g.ny = p.ny; I.g.nz = p.nz;
         I.g.N = (long long)p.nx * p.ny * p.nz;
         I.g.pore_axis = -1;
-        I.moff = -1;
         I.loff = -1;
         I.nwork = (uint32_t)I.g.N;
         I.off = off;
@@ -917,9 +1037,10 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         h->flag_start[k] = toff;
         h->nfluid[k] = I.g.N;
         I.ps = (I.g.N + 31) / 32 * 32;
+        I.fs = I.ps;
         h->Nnodes += I.g.N;
         off += 19 * I.ps;
-        foff += 3 * I.ps;
+        foff += 3 * I.fs;
         toff += (long long)I.ntx * I.nty * I.ntz;
     }
     h->flag_start[n] = toff;
@@ -993,7 +1114,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dmask, h->dfluid,
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dcmap, h->dcnbr, h->dfluid,
                     h->derr};
     for (void *b : bufs)
         if (b) cudaFree(b);

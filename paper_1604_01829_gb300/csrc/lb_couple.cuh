@@ -15,7 +15,10 @@ template <typename R, typename T>
 __device__ __forceinline__ void node_rho_j(const T *A, const Geom &g, int x, int y, int z, long long n,
                                            bool odd, R rho0, R &rho, R j[3], int *err = nullptr) {
     R v[19];
-    if (g.pore_axis < 0 && !g.chan) {
+    if (g.cmap) {                        // compact pore layout (batched pore instances)
+#pragma unroll
+        for (int i = 0; i < 19; ++i) v[i] = (R)compact_load_pre(A, g, x, y, z, i, odd);
+    } else if (g.pore_axis < 0 && !g.chan) {
         const int nx = g.nx, nxy = g.nx * g.ny;
         const int xo[3] = {(x == 0 ? nx : x) - 1, x, x + 1 == nx ? 0 : x + 1};
         const int yo[3] = {((y == 0 ? g.ny : y) - 1) * nx, y * nx, (y + 1 == g.ny ? 0 : y + 1) * nx};

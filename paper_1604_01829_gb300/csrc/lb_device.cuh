@@ -73,6 +73,18 @@ struct Geom {
     int chan;           // 1: moving walls at y = -1/2 and y = ny - 1/2, the box not periodic in y
     const double *wchan;  // device, chan: [2][19] bounce-back terms 6 w_i rho0 (c_i . u_wall) of the
                           // lower and upper wall, then [2][3] the wall velocities
+    // Compact layout of a pore (batched pore instances; nullptr: the dense
+    // layout): only fluid nodes are stored. A node at position p across the
+    // axis (p = a + na b, (a, b) = (x, y), (x, z) or (y, z) for an axis z, y
+    // or x) and coordinate l along it has index m = cmap[p] * csj + l * csa in
+    // planes cps apart; cnbr[8 j + dir8(u, v)] is the compact position of the
+    // in-plane neighbour (a + u, b + v) of compact position j (periodic),
+    // 0xFFFF if that is a wall node: one 16-byte record per position, read
+    // by one vector load.
+    const int *cmap;
+    const uint16_t *cnbr;
+    long long cps;
+    int csj, csa;
 };
 
 __device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -144,6 +156,60 @@ __device__ __forceinline__ void store_pre(T *A, const Geom &g, int x, int y, int
     const int xs = wrapm(x - cx(i), g.nx), ys = wrapm(yr, g.ny), zs = wrapm(z - cz(i), g.nz);
     if (is_wall(g, xs, ys, zs)) { A[(long long)i * g.N + n] = v; return; }
     A[(long long)opp(i) * g.N + nidx(g, xs, ys, zs)] = v;
+}
+
+// Slot of the in-plane direction (u, v) != (0, 0) in a position's record of
+// 8 neighbours (compact layout).
+__host__ __device__ constexpr int dir8(int u, int v) {
+    return (u + 1) + 3 * (v + 1) < 4 ? (u + 1) + 3 * (v + 1) : (u + 1) + 3 * (v + 1) - 1;
+}
+
+// In-plane components (u, v) and the component along the pore axis of link
+// i, for the compact layout.
+__device__ __forceinline__ void link_axes(int axis, int i, int &u, int &v, int &al) {
+    if (axis == 2) { u = cx(i); v = cy(i); al = cz(i); }
+    else if (axis == 1) { u = cx(i); v = cz(i); al = cy(i); }
+    else { u = cy(i); v = cz(i); al = cx(i); }
+}
+
+// Compact index of fluid node (x, y, z) and its position j across the axis
+// and coordinate l along it.
+__device__ __forceinline__ long long compact_node(const Geom &g, int x, int y, int z, int &j, int &l) {
+    int a, b, na;
+    if (g.pore_axis == 2) { a = x; b = y; na = g.nx; l = z; }
+    else if (g.pore_axis == 1) { a = x; b = z; na = g.nx; l = y; }
+    else { a = y; b = z; na = g.ny; l = x; }
+    j = g.cmap[a + na * b];
+    return (long long)j * g.csj + (long long)l * g.csa;
+}
+
+// load_pre and store_pre for the compact layout (fluid node (x, y, z)).
+template <typename T>
+__device__ __forceinline__ T compact_load_pre(const T *A, const Geom &g, int x, int y, int z, int i, bool odd) {
+    int j, l;
+    const long long m = compact_node(g, x, y, z, j, l);
+    if (!odd || i == 0) return A[(long long)i * g.cps + m];
+    int u, v, al;
+    link_axes(g.pore_axis, i, u, v, al);
+    const int js = (u == 0 && v == 0) ? j : (int)g.cnbr[8 * j + dir8(-u, -v)];
+    if (js == 0xFFFF) return A[(long long)i * g.cps + m];
+    const int nl = g.pore_axis == 2 ? g.nz : (g.pore_axis == 1 ? g.ny : g.nx);
+    const int ls = wrapm(l - al, nl);
+    return A[(long long)opp(i) * g.cps + (long long)js * g.csj + (long long)ls * g.csa];
+}
+
+template <typename T>
+__device__ __forceinline__ void compact_store_pre(T *A, const Geom &g, int x, int y, int z, int i, bool odd, T val) {
+    int j, l;
+    const long long m = compact_node(g, x, y, z, j, l);
+    if (!odd || i == 0) { A[(long long)i * g.cps + m] = val; return; }
+    int u, v, al;
+    link_axes(g.pore_axis, i, u, v, al);
+    const int js = (u == 0 && v == 0) ? j : (int)g.cnbr[8 * j + dir8(-u, -v)];
+    if (js == 0xFFFF) { A[(long long)i * g.cps + m] = val; return; }
+    const int nl = g.pore_axis == 2 ? g.nz : (g.pore_axis == 1 ? g.ny : g.nx);
+    const int ls = wrapm(l - al, nl);
+    A[(long long)opp(i) * g.cps + (long long)js * g.csj + (long long)ls * g.csa] = val;
 }
 
 // 4x4x4 tiles flag where bead forces were spread
