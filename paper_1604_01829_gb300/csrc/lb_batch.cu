@@ -275,7 +275,7 @@ struct BatchCouple {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_batch_couple(const BatchCouple b) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_batch_couple(const BatchCouple b) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = t >> 3;
     const bool active = k < b.nbeads;
