@@ -357,7 +357,8 @@ lb_status lb_batch_get_populations(lb_batch_handle h, int inst, double *host, si
 lb_status lb_batch_set_populations(lb_batch_handle h, int inst, const double *host, size_t n);
 /* Work schedule of the fluid kernel: tile_nodes (64, 128, 256) consecutive
  * nodes of one instance per CTA iteration, blocks_per_sm resident CTAs of
- * the persistent grid (tile_nodes * blocks_per_sm <= 1024), order 0 =
+ * the persistent grid (tile_nodes * blocks_per_sm <= 2048; each step's grid is
+ * further capped at the CTAs of that step's kernel that fit at once), order 0 =
  * tiles dealt round-robin to CTAs, 1 = contiguous chunks, 2 = no persistent
  * grid: one CTA per tile, left to the hardware block scheduler
  * (blocks_per_sm is then not used). Results do not depend on it. */

@@ -467,7 +467,7 @@ struct lb_batch_ctx {
     bool uploaded = false;
     // schedule
     int TS = 128, bpsm = 8, order = 0, ntiles = 0, sms = 0;
-    int resident = 0;                       // resident CTAs per SM of the fluid kernel at TS threads
+    int resident[2] = {0, 0};               // resident CTAs per SM of the even / odd fluid kernel at TS threads
     // graph of two steps
     cudaGraphExec_t gexec = nullptr;
     bool any_wall = false;                  // some instance has pore-wall beads
@@ -609,25 +609,30 @@ lb_status rebuild_schedule(lb_batch_ctx *h) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
     }
-    // resident CTAs of the (even-step) fluid kernel at this tile size: the
-    // persistent grid never exceeds it, so every CTA runs concurrently
-    int occ = 0;
-    cudaError_t e;
-#define BOCC(T, C, NZ)                                                                                            \
-    e = h->common ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::k_batch_collide<T, C, NZ, false, true>, h->TS, 0) \
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::k_batch_collide<T, C, NZ, false, false>, h->TS, 0)
-    if (h->fp32) {
-        if (h->collision == 0) BOCC(float, 0, false);
-        else if (h->noise) BOCC(float, 1, true);
-        else BOCC(float, 1, false);
-    } else {
-        if (h->collision == 0) BOCC(double, 0, false);
-        else if (h->noise) BOCC(double, 1, true);
-        else BOCC(double, 1, false);
-    }
+    // resident CTAs of the even- and odd-step fluid kernels at this tile size
+    // (their register counts differ): each parity's persistent grid never
+    // exceeds its own, so every CTA runs concurrently
+    for (int odd = 0; odd < 2; ++odd) {
+        int occ = 0;
+        cudaError_t e;
+#define BOCC(T, C, NZ, O)                                                                                           \
+        e = h->common ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::k_batch_collide<T, C, NZ, O, true>, h->TS, 0) \
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::k_batch_collide<T, C, NZ, O, false>, h->TS, 0)
+#define BOCC2(T, C, NZ) do { if (odd) BOCC(T, C, NZ, true); else BOCC(T, C, NZ, false); } while (0)
+        if (h->fp32) {
+            if (h->collision == 0) BOCC2(float, 0, false);
+            else if (h->noise) BOCC2(float, 1, true);
+            else BOCC2(float, 1, false);
+        } else {
+            if (h->collision == 0) BOCC2(double, 0, false);
+            else if (h->noise) BOCC2(double, 1, true);
+            else BOCC2(double, 1, false);
+        }
+#undef BOCC2
 #undef BOCC
-    if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
-    h->resident = occ > 0 ? occ : 1;
+        if (e != cudaSuccess) return bfail(h, LB_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+        h->resident[odd] = occ > 0 ? occ : 1;
+    }
     return LB_OK;
 }
 
@@ -875,7 +880,8 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
     a.ntiles = h->ntiles;
     a.pd = h->hinst[0].pd;
     a.pf = h->hinst[0].pf;
-    int grid = h->sms * std::min(h->bpsm, h->resident > 0 ? h->resident : h->bpsm);
+    const int res = h->resident[odd ? 1 : 0];
+    int grid = h->sms * std::min(h->bpsm, res > 0 ? res : h->bpsm);
     if (h->order == 2) grid = h->ntiles;    // one CTA per tile, round-robin loop runs once
     if (grid > h->ntiles) grid = h->ntiles;
     if (grid < 1) grid = 1;
@@ -1369,10 +1375,11 @@ lb_status lb_batch_set_populations(lb_batch_handle h, int k, const double *host,
 
 lb_status lb_batch_set_schedule(lb_batch_handle h, int tile_nodes, int blocks_per_sm, int order) {
     if (!h) return bfail(nullptr, LB_ERR_ARG, "null handle");
-    // the fluid kernel is capped at 64 registers, so 1024 threads per SM are resident
+    // the persistent grid is capped at the CTAs that are resident at once (at
+    // most 2048 threads per SM; fewer as the registers allow)
     if ((tile_nodes != 64 && tile_nodes != 128 && tile_nodes != 256) || blocks_per_sm < 1 ||
-        blocks_per_sm * tile_nodes > 1024 || order < 0 || order > 2)
-        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 1024, order 0/1/2");
+        blocks_per_sm * tile_nodes > 2048 || order < 0 || order > 2)
+        return bfail(h, LB_ERR_ARG, "tile_nodes 64/128/256, blocks_per_sm * tile_nodes <= 2048, order 0/1/2");
     h->TS = tile_nodes;
     h->bpsm = blocks_per_sm;
     h->order = order;
@@ -1450,7 +1457,7 @@ lb_status lb_batch_autotune(lb_batch_handle h, int trial_steps, int chosen[3], d
     double best = 1e30;
     int bt = h->TS, bb = h->bpsm, bo = h->order;
     for (int ts : tiles)
-        for (int bps = 2; bps * ts <= 1024; bps *= 2)
+        for (int bps = 2; bps * ts <= 2048; bps *= 2)
             for (int order = 0; order < 3; ++order) {
                 if (order == 2 && bps != 2) continue;     // blocks_per_sm unused: one trial per tile size
                 if ((s = lb_batch_set_schedule(h, ts, bps, order)) != LB_OK) break;

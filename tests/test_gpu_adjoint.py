@@ -131,6 +131,50 @@ def test_schedules_agree_and_the_workspace_is_reused():
         assert np.abs(ds - ds0).max() <= 1e-12 * np.abs(ds0).max()
 
 
+def test_fp32_drag_against_the_fp64_oracle():
+    """The drag error of FP32 deviation storage against the FP64 oracle, on
+    a reduced form of the adjoint workload (the same physics: MRT at the
+    paper's nu = 0.016, kT = 0, the paper's bead friction, a 1:3 prolate
+    raspberry pulled along its long axis with the compensating force on the
+    fluid): 24^3 box, semi-axes 6 x 2 x 2, 400 steps, J = mean velocity over
+    the last 50. FP64 on the GPU gives the oracle's J to 1e-12; FP32 within
+    1e-4 (measured on GB300 is recorded; the 96^3 / 3000-step bench workload
+    gives 2.2e-5 between the FP32 and FP64 GPU runs)."""
+    import math
+    from paper_1604_01829_gb300 import lb
+    beads = Wl.ellipsoid_raspberry(6.0, 2.0, 2.0, seed=1609)
+    mass = 4.0 / 3.0 * math.pi * 6 * 4
+    inertia = tuple(Wl.solid_ellipsoid_inertia(mass, 6, 2, 2))
+    params = dict(collision=1, rho0=1.0, kT=0.0, gamma_bead=Wl.paper_gamma_to_lattice(20.0), compensate_force=1,
+                  **Wl.mrt_rates(Wl.NU_PAPER))
+    T, W = 400, 50
+    X = [12.0, 12.0, 12.0]
+
+    def run_gpu(precision):
+        h = lb.LB(24, 24, 24, precision=precision, **params)
+        h.lb_add_raspberry(beads, X, (1, 0, 0, 0), mass, inertia, (1e-3, 0, 0), None, 2)
+        h.lb_step(T - W)
+        v = []
+        for _ in range(W):
+            h.lb_step(1)
+            v.append(h.lb_get_body(0)["V"][0])
+        h.close()
+        return float(np.mean(v))
+
+    o = O.OracleLB(24, 24, 24, **oracle_kw(params))
+    o.add_raspberry(beads, X, (1, 0, 0, 0), mass, inertia, (1e-3, 0, 0), (0, 0, 0), 2)
+    o.step(T - W)
+    vo = []
+    for _ in range(W):
+        o.step(1)
+        vo.append(o.body(0)["V"][0])
+    Jo = float(np.mean(vo))
+    J64, J32 = run_gpu(64), run_gpu(32)
+    e32 = observe("drag_fp32_vs_oracle", abs(J32 / Jo - 1))
+    assert abs(J64 / Jo - 1) <= 1e-12
+    assert e32 <= 1e-4, e32
+
+
 def test_adjoint_rejects_noise_and_free_rotation():
     from paper_1604_01829_gb300 import lb
     g = lb.LB(8, 8, 8, precision=64, kT=1e-4, gamma_bead=0.1, **MRT)
