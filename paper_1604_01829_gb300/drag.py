@@ -18,6 +18,8 @@ Sec. 2.8 of Ustach & Faller, arXiv:1604.01829).
   through the pore vanishes, and xi = F / U.
 * pore_radial_drag: the same raspberry moving radially towards the wall
   (the x^p direction of Sec. 3.3), whose momentum the walls take up.
+* spin_drag: rotational drag xi_r = -T / omega of a raspberry held in place
+  and spinning at omega in a periodic box.
 
 Everything here only drives the library (steps, body state, conservation
 sums); the arithmetic of the step is the library's.
@@ -130,6 +132,28 @@ def pore_radial_drag(nx, nz, R, beads, mass, offset=0.0, F=1e-4, gamma=0.3, prec
     finally:
         h.close()
     return F / float(np.mean(U))
+
+
+def spin_drag(L, beads, omega=1e-4, axis=2, gamma=0.3, precision=64, params=None):
+    """Rotational drag of a raspberry held in place (fixed = 1) and spinning
+    at omega about `axis` at the centre of a periodic L^3 box:
+    xi_r = -T_axis / omega at steady state (after 1.2 L^2 steps, mean of 5
+    samples 0.02 L^2 apart)."""
+    params = dict(BGK1 if params is None else params)
+    h = lb.LB(L, L, L, precision=precision, gamma_bead=gamma, **params)
+    try:
+        h.lb_add_raspberry(beads, [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], fixed=1)
+        w = [0.0, 0.0, 0.0]
+        w[axis] = omega
+        h.lb_set_body_state(0, w=tuple(w))
+        h.lb_step(int(1.2 * L * L))
+        T = []
+        for _ in range(5):
+            h.lb_step(max(1, int(0.02 * L * L)))
+            T.append(h.lb_forces(0)[1][axis])
+    finally:
+        h.close()
+    return -float(np.mean(T)) / omega
 
 
 def bohlin(lam):

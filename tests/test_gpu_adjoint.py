@@ -137,8 +137,10 @@ def test_fp32_drag_against_the_fp64_oracle():
     paper's nu = 0.016, kT = 0, the paper's bead friction, a 1:3 prolate
     raspberry pulled along its long axis with the compensating force on the
     fluid): 24^3 box, semi-axes 6 x 2 x 2, 400 steps, J = mean velocity over
-    the last 50. FP64 on the GPU gives the oracle's J to 1e-12; FP32 within
-    1e-4 (measured on GB300 is recorded; the 96^3 / 3000-step bench workload
+    the last 50. FP64 on the GPU gives the oracle's J to 1e-9 relative (the
+    two differ in summation order and FMA contraction, O(1e-16) per operation
+    accumulated over 400 steps; measured on GB300: 5.5e-11); FP32 within
+    1e-4 (measured on GB300: 2.7e-6; the 96^3 / 3000-step bench workload
     gives 2.2e-5 between the FP32 and FP64 GPU runs)."""
     import math
     from paper_1604_01829_gb300 import lb
@@ -171,7 +173,7 @@ def test_fp32_drag_against_the_fp64_oracle():
     Jo = float(np.mean(vo))
     J64, J32 = run_gpu(64), run_gpu(32)
     e32 = observe("drag_fp32_vs_oracle", abs(J32 / Jo - 1))
-    assert abs(J64 / Jo - 1) <= 1e-12
+    assert observe("drag_fp64_vs_oracle", abs(J64 / Jo - 1)) <= 1e-9
     assert e32 <= 1e-4, e32
 
 

@@ -218,18 +218,9 @@ def test_fluctuating_fluid_thermalises_on_the_cuda_path(precision):
 
 def _spin_drag(L, beads, omega=1e-4):
     """Rotational drag of a raspberry held in place and spinning at omega
-    about z in a periodic L^3 box: xi_r = -T_z / omega at steady state."""
-    from paper_1604_01829_gb300 import lb
-    h = lb.LB(L, L, L, precision=64, collision=0, tau=1.0, gamma_bead=0.3)
-    h.lb_add_raspberry(beads, [L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07], fixed=1)
-    h.lb_set_body_state(0, w=(0.0, 0.0, omega))
-    h.lb_step(int(1.2 * L * L))
-    T = []
-    for _ in range(5):
-        h.lb_step(max(1, int(0.02 * L * L)))
-        T.append(h.lb_forces(0)[1][2])
-    h.close()
-    return -float(np.mean(T)) / omega
+    about z in a periodic L^3 box (paper_1604_01829_gb300.drag.spin_drag)."""
+    from paper_1604_01829_gb300 import drag as D
+    return D.spin_drag(L, beads, omega)
 
 
 def test_resistance_grows_with_radius_through_a_renormalised_radius():
