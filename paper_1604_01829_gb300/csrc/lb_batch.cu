@@ -23,9 +23,13 @@
 #include "lb_collide.cuh"
 #include "lb_couple.cuh"
 
-// resident 256-thread CTAs per SM requested for the FP32 fluid kernel
-#ifndef LB_BATCH_MINB
-#define LB_BATCH_MINB 4
+// register caps of the FP32 fluid kernel per parity (resident CTAs of 128
+// threads per SM: 65536 / (128 x cap), rounded down)
+#ifndef LB_BATCH_REGS_EVEN
+#define LB_BATCH_REGS_EVEN 64
+#endif
+#ifndef LB_BATCH_REGS_ODD
+#define LB_BATCH_REGS_ODD 64
 #endif
 
 namespace lbk {
@@ -139,7 +143,8 @@ __device__ __forceinline__ void compact_odd_store(T *P, uint32_t base, uint32_t 
 }
 
 template <typename T, int COLL, bool NOISE, bool ODD, bool COMMON>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? LB_BATCH_MINB : 1) k_batch_collide(const BatchArgs a) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? (ODD ? LB_BATCH_REGS_ODD : LB_BATCH_REGS_EVEN) : 255)
+    k_batch_collide(const BatchArgs a) {
     using R = T;
     constexpr bool DEV = sizeof(T) == 4;
     for (int it = 0;; ++it) {
@@ -433,6 +438,10 @@ struct lb_batch_ctx {
     bool noise = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the prologue of step k + 1 runs on this stream beside the fluid kernel
+    // of step k (see launch_step)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<BInst> hinst;
     std::vector<long long> flag_start;      // n + 1
     std::vector<long long> nfluid;
@@ -803,7 +812,13 @@ lb_status upload(lb_batch_ctx *h) {
     return LB_OK;
 }
 
-lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
+// Step k of a group. With bodies, its prologue (kick and drift, clearing of
+// the force tiles of step k - 2) runs on the side stream: it needs the
+// coupling of step k - 1 (body sums, and the force buffer it clears is the one
+// that coupling read as the previous step's) but nothing the fluid kernel of
+// step k - 1 reads or writes, so it is forked after that coupling (`more`: a
+// step of the same group follows) and joined before the coupling of step k.
+lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record, bool more) {
     const bool odd = ((h->step + k) & 1) != 0;
     const int cur = (int)((h->step + k) & 1), prev = cur ^ 1;
     const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
@@ -815,18 +830,24 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
         const lbk::Recorder rec{nsub == 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
         const long long nthreads = std::min<long long>(64LL * h->list_cap, 152LL * 2048);
         const unsigned pg = std::max<unsigned>((unsigned)((nthreads + 255) / 256), (unsigned)nb);
+        if (k == 0) {
+            BCUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+            BCUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        }
         if (h->fp32)
-            lbk::k_batch_pre<float><<<pg, 256, 0, h->stream>>>(
+            lbk::k_batch_pre<float><<<pg, 256, 0, h->side>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (float *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
                 rec, h->list_cap, h->Ttot, h->derr, dt);
         else
-            lbk::k_batch_pre<double><<<pg, 256, 0, h->stream>>>(
+            lbk::k_batch_pre<double><<<pg, 256, 0, h->side>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (double *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
                 rec, h->list_cap, h->Ttot, h->derr, dt);
         BCUDA(h, cudaGetLastError());
-        if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->stream));
+        if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->side));
+        BCUDA(h, cudaEventRecord(h->ev_join, h->side));
+        BCUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     }
     if (coupled) {
         lbk::BatchCouple c{};
@@ -871,6 +892,10 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record) {
                 BCUDA(h, cudaGetLastError());
             }
         }
+    }
+    if (nb > 0 && more) {                       // the next prologue may start now
+        BCUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+        BCUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     }
     lbk::BatchArgs a{};
     a.inst = h->dinst;
@@ -943,7 +968,7 @@ lb_status eager_steps(lb_batch_ctx *h, int nsteps) {
                 }
             rec = true;
         }
-        lb_status s = launch_step(h, k, k > 0, rec);
+        lb_status s = launch_step(h, k, k > 0, rec, k + 1 < nsteps);
         if (s != LB_OK) return s;
     }
     lb_status s = finish_steps(h, nsteps);
@@ -956,8 +981,8 @@ lb_status ensure_graph(lb_batch_ctx *h) {
     if (h->gexec) return LB_OK;
     cudaGraph_t graph = nullptr;
     BCUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    lb_status s = launch_step(h, 0, false, false);
-    if (s == LB_OK) s = launch_step(h, 1, true, false);
+    lb_status s = launch_step(h, 0, false, false, true);
+    if (s == LB_OK) s = launch_step(h, 1, true, false, false);
     if (s == LB_OK) s = finish_steps(h, 2);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (s != LB_OK) {
@@ -1067,6 +1092,14 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         if (e != cudaSuccess) { delete h; return bfail(nullptr, LB_ERR_CUDA, "cudaStreamCreate failed"); }
         h->own_stream = true;
     }
+    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        g_batch_error = std::string("side stream: ") + cudaGetErrorString(e);
+        lb_batch_destroy(h);
+        return LB_ERR_CUDA;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1117,6 +1150,7 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
 lb_status lb_batch_destroy(lb_batch_handle h) {
     if (!h) return LB_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
@@ -1126,6 +1160,9 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
         if (b) cudaFree(b);
     if (h->herr) cudaFreeHost(h->herr);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return LB_OK;

@@ -224,3 +224,24 @@ def test_batch_checkpoint_resume(precision):
     with pytest.raises(lb.LBError) as e:
         C2.lb_batch_checkpoint_load(ck[:50])
     assert e.value.status == lb.LB_ERR_ARG
+
+
+def test_pore_cross_section_beyond_the_compact_limit_is_refused():
+    """A batched pore instance stores its fluid nodes only from the first step
+    on, indexing a cross-section's fluid positions in 16 bits: a pore of
+    radius 150 (about 70,700 fluid positions across the axis) is refused at
+    the first step with LB_ERR_ARG and a message naming the limit, and a
+    pore just inside it steps."""
+    from paper_1604_01829_gb300 import lb
+    big = lb.LBBatch([dict(nx=304, ny=304, nz=2, **MRT)])
+    big.lb_batch_set_pore(0, 150.0, 2)
+    with pytest.raises(lb.LBError) as ei:
+        big.lb_batch_step(1)
+    assert ei.value.status == lb.LB_ERR_ARG and "65534" in str(ei.value)
+    big.close()
+    ok = lb.LBBatch([dict(nx=290, ny=290, nz=2, **MRT)])
+    ok.lb_batch_set_pore(0, 144.0, 2)                      # about 65,100 fluid positions
+    ok.lb_batch_step(2)
+    f = ok.lb_batch_get_populations(0)
+    assert np.isfinite(f).all()
+    ok.close()
