@@ -557,12 +557,13 @@ struct Snapshot {
 };
 
 // What the reverse pass of one step reads, taped by the two-level schedule.
+// The first step of a segment reads its populations and previous spread
+// force from the segment's snapshot, every later one from the entry before
+// it (its Fnew), so entry 0 holds no populations.
 struct Tape {
-    void *f = nullptr;        // populations before the step
-    void *Fprev = nullptr;    // spread force the step reads
+    void *f = nullptr;        // populations before the step (entries >= 1)
     void *Fnew = nullptr;     // spread force the step writes
     Body *bodies = nullptr;   // bodies before the step
-    long long step = 0;
 };
 
 }  // namespace
@@ -608,7 +609,7 @@ size_t snapshot_bytes(const Sizes &z) {
     return z.fbytes + 2 * (z.Fbytes + z.tbytes + z.lbytes + sizeof(int)) + z.bbytes + sizeof(unsigned long long);
 }
 
-size_t tape_bytes(const Sizes &z) { return z.fbytes + 2 * z.Fbytes + z.bbytes; }
+size_t tape_bytes(const Sizes &z) { return z.fbytes + z.Fbytes + z.bbytes; }
 
 template <typename P>
 cudaError_t walloc(AdjWork &w, P **p, size_t bytes) {
@@ -665,9 +666,14 @@ lb_status ensure_work(lb_ctx *h, int nsnap, int ntape, int nsteps, double *alloc
         if (e == cudaSuccess) e = walloc(*w, &S.bodies, z.bbytes);
         if (e == cudaSuccess) e = walloc(*w, &S.dstep, sizeof(unsigned long long));
     }
-    for (auto &T : w->tape) {
-        if (e == cudaSuccess) e = walloc(*w, &T.f, z.fbytes);
-        if (e == cudaSuccess) e = walloc(*w, &T.Fprev, z.Fbytes);
+    for (size_t k = 0; k < w->tape.size(); ++k) {
+        Tape &T = w->tape[k];
+        if (k > 0 && e == cudaSuccess) {
+            // out-of-place steps write the slots of fluid nodes only: the
+            // wall-node slots (never read) start as zeros, not garbage
+            e = walloc(*w, &T.f, z.fbytes);
+            if (e == cudaSuccess) e = cudaMemsetAsync(T.f, 0, z.fbytes, h->stream);
+        }
         if (e == cudaSuccess) e = walloc(*w, &T.Fnew, z.Fbytes);
         if (e == cudaSuccess) e = walloc(*w, &T.bodies, z.bbytes);
     }
@@ -723,8 +729,15 @@ struct Run {
         return lbk::ctx_fail(h, LB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
     }
 
+    // Where the current state's populations are: the handle's array (null),
+    // or a snapshot's or tape entry's, which the next step or turn reads in
+    // place (an out-of-place step leaves its result in the handle's array).
+    const void *cf = nullptr;
+    const void *pops() const { return cf ? cf : h->f; }
+
     cudaError_t save(Snapshot &S) {
-        cudaError_t e = cudaMemcpyAsync(S.f, h->f, z.fbytes, cudaMemcpyDeviceToDevice, s);
+        cudaError_t e = cudaSuccess;
+        if (pops() != S.f) e = cudaMemcpyAsync(S.f, pops(), z.fbytes, cudaMemcpyDeviceToDevice, s);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaMemcpyAsync(S.F[k], h->Fbuf[k], z.Fbytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(S.tiles[k], h->tiles[k], z.tbytes, cudaMemcpyDeviceToDevice, s);
@@ -737,8 +750,17 @@ struct Run {
         S.step = h->step;
         return e;
     }
-    cudaError_t restore(const Snapshot &S) {
-        cudaError_t e = cudaMemcpyAsync(h->f, S.f, z.fbytes, cudaMemcpyDeviceToDevice, s);
+    // Everything but the populations, which stay in the snapshot for the next
+    // step or turn to read; whole: the populations too (the handle is left
+    // holding the state).
+    cudaError_t restore(const Snapshot &S, bool whole = false) {
+        cudaError_t e = cudaSuccess;
+        if (whole) {
+            e = cudaMemcpyAsync(h->f, S.f, z.fbytes, cudaMemcpyDeviceToDevice, s);
+            cf = nullptr;
+        } else {
+            cf = S.f;
+        }
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaMemcpyAsync(h->Fbuf[k], S.F[k], z.Fbytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->tiles[k], S.tiles[k], z.tbytes, cudaMemcpyDeviceToDevice, s);
@@ -759,14 +781,24 @@ struct Run {
         if (!first_sweep) recompute_steps += b - a;
         else forward_steps += b - a;
         const int wstart = nsteps - window;
-        const int n1 = std::max(a, std::min(b, wstart));
-        lb_status st;
-        if (n1 > a && (st = lb_step(h, n1 - a)) != LB_OK) return st;
-        for (int n = n1; n < b; ++n) {
-            if ((st = lb_step(h, 1)) != LB_OK) return st;
+        auto record = [&](int n) -> lb_status {
             lbk::k_record_v<<<1, 1, 0, s>>>(h->db, body, axis, w->vhist, n);
             cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return fail_cuda(e, "record launch");
+            return e == cudaSuccess ? LB_OK : fail_cuda(e, "record launch");
+        };
+        lb_status st;
+        int n0s = a;
+        if (cf) {                       // the first step reads the snapshot's populations
+            if ((st = lbk::ctx_step_oop(h, cf, h->f)) != LB_OK) return st;
+            cf = nullptr;
+            if (a >= wstart && (st = record(a)) != LB_OK) return st;
+            ++n0s;
+        }
+        const int n1 = std::max(n0s, std::min(b, wstart));
+        if (n1 > n0s && (st = lb_step(h, n1 - n0s)) != LB_OK) return st;
+        for (int n = n1; n < b; ++n) {
+            if ((st = lb_step(h, 1)) != LB_OK) return st;
+            if ((st = record(n)) != LB_OK) return st;
         }
         return LB_OK;
     }
@@ -851,10 +883,10 @@ struct Run {
         mark_first();
         cudaError_t e = cudaMemcpyAsync(w->turn_bodies, h->db, z.bbytes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return fail_cuda(e, "turn copy");
-        lb_status st = lbk::ctx_turn(h);
+        lb_status st = lbk::ctx_turn(h, pops());
         if (st != LB_OK) return st;
         const int curb = (int)((n0 + n) & 1), prev = curb ^ 1;
-        return reverse_step(n, h->f, h->Fbuf[prev], h->Fbuf[curb], w->turn_bodies);
+        return reverse_step(n, pops(), h->Fbuf[prev], h->Fbuf[curb], w->turn_bodies);
     }
 };
 
@@ -876,29 +908,36 @@ lb_status run_two_level(Run &R, int c) {
     if (e != cudaSuccess) return R.fail_cuda(e, "snapshot");
     R.mark_first();
     for (int sg = nseg - 1; sg >= 0; --sg) {
-        if ((e = R.restore(w->snaps[sg])) != cudaSuccess) return R.fail_cuda(e, "restore");
+        const Snapshot &Sg = w->snaps[sg];
+        if ((e = R.restore(Sg)) != cudaSuccess) return R.fail_cuda(e, "restore");
         const int a0 = sg * K, a1 = std::min(T, a0 + K);
         R.recompute_steps += a1 - a0;
+        // each step reads the populations where the one before left them (the
+        // snapshot, then tape entries) and leaves its own in the next entry:
+        // the tape is written by the steps themselves, not copied
         for (int n = a0; n < a1; ++n) {
             Tape &Tp = w->tape[n - a0];
-            const int curb = (int)((R.n0 + n) & 1), prev = curb ^ 1;
-            e = cudaMemcpyAsync(Tp.f, h->f, R.z.fbytes, cudaMemcpyDeviceToDevice, R.s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(Tp.Fprev, h->Fbuf[prev], R.z.Fbytes, cudaMemcpyDeviceToDevice, R.s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(Tp.bodies, h->db, R.z.bbytes, cudaMemcpyDeviceToDevice, R.s);
+            const int curb = (int)((R.n0 + n) & 1);
+            e = cudaMemcpyAsync(Tp.bodies, h->db, R.z.bbytes, cudaMemcpyDeviceToDevice, R.s);
             if (e != cudaSuccess) return R.fail_cuda(e, "tape");
-            lb_status st = lb_step(h, 1);
+            void *dst = n + 1 < a1 ? w->tape[n + 1 - a0].f : h->f;
+            lb_status st = lbk::ctx_step_oop(h, R.pops(), dst);
             if (st != LB_OK) return st;
+            R.cf = dst != h->f ? dst : nullptr;
             e = cudaMemcpyAsync(Tp.Fnew, h->Fbuf[curb], R.z.Fbytes, cudaMemcpyDeviceToDevice, R.s);
             if (e != cudaSuccess) return R.fail_cuda(e, "tape");
         }
+        const int prev0 = (int)((R.n0 + a0) & 1) ^ 1;
         for (int n = a1 - 1; n >= a0; --n) {
             const Tape &Tp = w->tape[n - a0];
-            lb_status st = R.reverse_step(n, Tp.f, Tp.Fprev, Tp.Fnew, Tp.bodies);
+            const void *fn = n == a0 ? Sg.f : Tp.f;
+            const void *Fprev = n == a0 ? Sg.F[prev0] : w->tape[n - 1 - a0].Fnew;
+            lb_status st = R.reverse_step(n, fn, Fprev, Tp.Fnew, Tp.bodies);
             if (st != LB_OK) return st;
         }
     }
     // leave the handle where the forward sweep ended
-    if ((e = R.restore(w->snaps[nseg])) != cudaSuccess) return R.fail_cuda(e, "restore");
+    if ((e = R.restore(w->snaps[nseg], true)) != cudaSuccess) return R.fail_cuda(e, "restore");
     return LB_OK;
 }
 
@@ -1000,7 +1039,7 @@ lb_status run_binomial(Run &R, int S) {
     if (e != cudaSuccess) return R.fail_cuda(e, "snapshot");
     lb_status st = B.reverse(0, R.nsteps, 0);
     if (st != LB_OK) return st;
-    if ((e = R.restore(R.w->snaps[S])) != cudaSuccess) return R.fail_cuda(e, "restore");
+    if ((e = R.restore(R.w->snaps[S], true)) != cudaSuccess) return R.fail_cuda(e, "restore");
     return LB_OK;
 }
 

@@ -230,7 +230,14 @@ lbk::FluidArgs fluid_args(const lb_ctx *h, int cur, uint32_t step_off) {
     a.step_off = step_off;
     a.err = h->err_dev;
     const size_t es = h->fp32 ? 4 : 8;
-    for (int i = 0; i < 19; ++i) a.plane[i] = static_cast<char *>(h->f) + (size_t)i * (size_t)h->g.N * es;
+    // in place, or (f_src / f_dst set) from one buffer into another
+    char *src = static_cast<char *>(const_cast<void *>(h->f_src ? h->f_src : h->f));
+    char *dst = static_cast<char *>(h->f_dst ? h->f_dst : h->f);
+    a.f = src;
+    for (int i = 0; i < 19; ++i) {
+        a.plane[i] = src + (size_t)i * (size_t)h->g.N * es;
+        a.out[i] = dst + (size_t)i * (size_t)h->g.N * es;
+    }
     return a;
 }
 
@@ -273,8 +280,10 @@ lb_status timed_collide(lb_ctx *h, const lbk::FluidArgs &a, bool odd) {
         }
         LB_CUDA(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
     }
-    const bool tma = h->cs_variant == 2 && lbk::tma_collide_supported(h->g, h->fp32);
-    cudaError_t e = tma ? lbk::launch_collide_stream_tma(a, h->p.collision, noise, odd, h->tma_stages, h->tma_ctas,
+    const bool oop = a.out[0] != a.plane[0];
+    const bool tma = !oop && h->cs_variant == 2 && lbk::tma_collide_supported(h->g, h->fp32);
+    cudaError_t e = oop ? lbk::launch_collide_stream_oop(a, h->fp32, h->p.collision, odd, h->block, h->stream)
+                  : tma ? lbk::launch_collide_stream_tma(a, h->p.collision, noise, odd, h->tma_stages, h->tma_ctas,
                                                          h->wait_limit, h->stream)
                         : lbk::launch_collide_stream(a, h->fp32, h->p.collision, noise, odd, h->block, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "collide_stream launch");
@@ -664,7 +673,7 @@ lb_status launch_step_coupling(lb_ctx *h, int k, int sub) {
     const int cur = (int)(t & 1), prev = cur ^ 1;
     lbk::CoupleArgs c{};
     c.g = h->g;
-    c.f = h->f;
+    c.f = h->f_src ? h->f_src : h->f;
     c.fp32 = h->fp32;
     c.odd = odd;
     c.rho0 = h->p.rho0;
@@ -857,9 +866,28 @@ namespace lbk {
 // bead coupling, both on the main stream, without the fluid kernel and the
 // group's finishing launch. The handle is left partly stepped; the caller
 // restores a whole state before stepping it again.
-lb_status ctx_turn(lb_ctx *h) {
+lb_status ctx_turn(lb_ctx *h, const void *src) {
+    h->f_src = src != h->f ? src : nullptr;
     lb_status s = launch_step_prologue(h, 0, false, h->stream);
     if (s == LB_OK && !h->hbody_of.empty()) s = launch_step_coupling(h, 0, 0);
+    h->f_src = nullptr;
+    return s;
+}
+
+// One whole step (deterministic fluid, launched eagerly) that reads the
+// populations at src and leaves the next state's at dst (either may be the
+// handle's own array; src == dst == f is the ordinary in-place step). The
+// handle's other state (bodies, forces, tiles, step count) advances in place.
+lb_status ctx_step_oop(lb_ctx *h, const void *src, void *dst) {
+    if (src == dst && dst != h->f) return ctx_fail(h, LB_ERR_ARG, "out-of-place step into its own source");
+    if (h->p.collision == 1 && h->p.kT > 0.0) return ctx_fail(h, LB_ERR_STATE, "out-of-place steps are deterministic");
+    lb_status s = upload_bodies(h);
+    if (s != LB_OK) return s;
+    h->f_src = src != h->f ? src : nullptr;
+    h->f_dst = dst != h->f ? dst : nullptr;
+    s = eager_steps(h, 1);
+    h->f_src = nullptr;
+    h->f_dst = nullptr;
     return s;
 }
 }  // namespace lbk

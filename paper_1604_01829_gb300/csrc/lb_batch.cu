@@ -279,8 +279,11 @@ struct BatchCouple {
     uint32_t call;                // Philox call word of the bead noise: 4 + substep
 };
 
+#ifndef LB_BATCH_COUPLE_REGS
+#define LB_BATCH_COUPLE_REGS 64
+#endif
 template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_batch_couple(const BatchCouple b) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? LB_BATCH_COUPLE_REGS : 255) k_batch_couple(const BatchCouple b) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = t >> 3;
     const bool active = k < b.nbeads;
@@ -818,7 +821,11 @@ lb_status upload(lb_batch_ctx *h) {
 // that coupling read as the previous step's) but nothing the fluid kernel of
 // step k - 1 reads or writes, so it is forked after that coupling (`more`: a
 // step of the same group follows) and joined before the coupling of step k.
+// Steps timed kernel by kernel (lb_batch_set_timing) keep it on the main
+// stream, so that the fluid kernel's events time it alone.
 lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record, bool more) {
+    const bool side = !h->timing;
+    cudaStream_t ps = side ? h->side : h->stream;
     const bool odd = ((h->step + k) & 1) != 0;
     const int cur = (int)((h->step + k) & 1), prev = cur ^ 1;
     const int nb = (int)h->hb.size(), nbeads = (int)h->hbody_of.size();
@@ -830,24 +837,26 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record, boo
         const lbk::Recorder rec{nsub == 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
         const long long nthreads = std::min<long long>(64LL * h->list_cap, 152LL * 2048);
         const unsigned pg = std::max<unsigned>((unsigned)((nthreads + 255) / 256), (unsigned)nb);
-        if (k == 0) {
+        if (k == 0 && side) {
             BCUDA(h, cudaEventRecord(h->ev_fork, h->stream));
             BCUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         }
         if (h->fp32)
-            lbk::k_batch_pre<float><<<pg, 256, 0, h->side>>>(
+            lbk::k_batch_pre<float><<<pg, 256, 0, ps>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (float *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
                 rec, h->list_cap, h->Ttot, h->derr, dt);
         else
-            lbk::k_batch_pre<double><<<pg, 256, 0, h->side>>>(
+            lbk::k_batch_pre<double><<<pg, 256, 0, ps>>>(
                 h->db, nb, finish_prev ? 1 : 0, coupled ? (double *)h->Fbuf[cur] : nullptr,
                 coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur], h->dinst, h->dflag_start, h->n,
                 rec, h->list_cap, h->Ttot, h->derr, dt);
         BCUDA(h, cudaGetLastError());
-        if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), h->side));
-        BCUDA(h, cudaEventRecord(h->ev_join, h->side));
-        BCUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        if (coupled) BCUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), ps));
+        if (side) {
+            BCUDA(h, cudaEventRecord(h->ev_join, h->side));
+            BCUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        }
     }
     if (coupled) {
         lbk::BatchCouple c{};
@@ -893,7 +902,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record, boo
             }
         }
     }
-    if (nb > 0 && more) {                       // the next prologue may start now
+    if (nb > 0 && more && side) {               // the next prologue may start now
         BCUDA(h, cudaEventRecord(h->ev_fork, h->stream));
         BCUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     }

@@ -98,8 +98,13 @@ __global__ void k_wall_beads(const WallBeads w, Body *bodies, const double *s, c
     if (k < nbeads) wall_bead_body(w, bodies, s, bead_body, k);
 }
 
+// register cap of the FP32 coupling kernel (resident CTAs of 128 per SM:
+// 65536 / (128 x cap))
+#ifndef LB_COUPLE_REGS
+#define LB_COUPLE_REGS 64
+#endif
 template <typename T>
-__global__ void __launch_bounds__(128) k_couple(const CoupleArgs a) {
+__global__ void __launch_bounds__(128) __maxnreg__(sizeof(T) == 4 ? LB_COUPLE_REGS : 255) k_couple(const CoupleArgs a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = t >> 3;
     couple_bead<T>(a, k, k, t & 7, threadIdx.x & 31, k < a.nbeads);

@@ -21,6 +21,10 @@ struct lb_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool own_stream = false;
     void *f = nullptr;
+    // an out-of-place step (adjoint): the populations it reads (coupling and
+    // fluid kernel) and where the fluid kernel stores them; null = f
+    const void *f_src = nullptr;
+    void *f_dst = nullptr;
     double *gforce = nullptr;               // device (3)
     float *gforce_f = nullptr;              // device (3), FP32 copy
     unsigned long long *step_dev = nullptr; // device step counter
@@ -95,6 +99,8 @@ namespace lbk {
 lb_status ctx_upload(lb_ctx *h);
 lb_status ctx_apply_external(lb_ctx *h);
 lb_status ctx_fail(lb_ctx *h, lb_status s, const std::string &m);
-lb_status ctx_turn(lb_ctx *h);
+// the prologue and coupling of the next step, reading the populations at src
+lb_status ctx_turn(lb_ctx *h, const void *src);
+lb_status ctx_step_oop(lb_ctx *h, const void *src, void *dst);
 void adj_free(lb_ctx *h);
 }  // namespace lbk

@@ -85,7 +85,7 @@ __device__ __forceinline__ uint32_t pore_section_index(const Geom &g, int x, int
 
 // ------------------------------------------------------- collide and stream
 
-template <typename T, int COLL, bool NOISE, bool ODD, bool PORE>
+template <typename T, int COLL, bool NOISE, bool ODD, bool PORE, bool OOP = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOISE : LB_CS_MINB) : 1)
     k_collide_stream(const FluidArgs a) {
     using R = T;
@@ -126,6 +126,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOIS
         return (unsigned)(xo[1 + dx] + yo[1 + dy] + zo[1 + dz]);
     };
     auto plane = [&](int i) { return static_cast<T *>(a.plane[i]); };
+    // stores: in place, or (OOP) into the output planes
+    T *AO = OOP ? static_cast<T *>(a.out[0]) : A;
+    auto oplane = [&](int i) { return static_cast<T *>(OOP ? a.out[i] : a.plane[i]); };
 
     R f[19];
     // odd step: population i arrives from the upstream node n - c_i, where it
@@ -172,17 +175,17 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOIS
     // odd step: f*_i goes to the downstream node n + c_i, the upstream node of
     // link opp(i) there; a wall downstream returns it into the own slot
     auto store_odd = [&](auto nb) {
-        A[n] = f[0];
+        AO[n] = f[0];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             if (PORE && ((wmask >> opp(i)) & 1u))
-                plane(opp(i))[n] = g.chan ? (T)((double)f[i] - chan_term(g, cy(i) < 0 ? 0 : 1, i)) : (T)f[i];
-            else plane(i)[chk(nb(cx(i), cy(i), cz(i)), N, a.err)] = f[i];
+                oplane(opp(i))[n] = g.chan ? (T)((double)f[i] - chan_term(g, cy(i) < 0 ? 0 : 1, i)) : (T)f[i];
+            else oplane(i)[chk(nb(cx(i), cy(i), cz(i)), N, a.err)] = f[i];
         }
     };
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) plane(opp(i))[chk(n, N, a.err)] = f[i];
+        for (int i = 0; i < 19; ++i) oplane(opp(i))[chk(n, N, a.err)] = f[i];
     } else if (row_in) {
         store_odd(nb_in);
     } else {
@@ -190,16 +193,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (NOISE ? LB_CS_MINB_NOIS
     }
 }
 
-template <typename T, int COLL, bool NOISE>
+template <typename T, int COLL, bool NOISE, bool OOP = false>
 cudaError_t launch_cs_t(const FluidArgs &a, bool odd, dim3 block, cudaStream_t s) {
     const dim3 grid((a.g.nx + block.x - 1) / block.x, (a.g.ny + block.y - 1) / block.y, a.g.nz);
     const bool pore = a.g.pore_axis >= 0 || a.g.chan;       // bounded: per-position wall masks
     if (odd) {
-        if (pore) k_collide_stream<T, COLL, NOISE, true, true><<<grid, block, 0, s>>>(a);
-        else k_collide_stream<T, COLL, NOISE, true, false><<<grid, block, 0, s>>>(a);
+        if (pore) k_collide_stream<T, COLL, NOISE, true, true, OOP><<<grid, block, 0, s>>>(a);
+        else k_collide_stream<T, COLL, NOISE, true, false, OOP><<<grid, block, 0, s>>>(a);
     } else {
-        if (pore) k_collide_stream<T, COLL, NOISE, false, true><<<grid, block, 0, s>>>(a);
-        else k_collide_stream<T, COLL, NOISE, false, false><<<grid, block, 0, s>>>(a);
+        if (pore) k_collide_stream<T, COLL, NOISE, false, true, OOP><<<grid, block, 0, s>>>(a);
+        else k_collide_stream<T, COLL, NOISE, false, false, OOP><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -382,6 +385,16 @@ cudaError_t launch_collide_stream(const FluidArgs &a, bool fp32, int collision, 
     if (collision == 0) return launch_cs_t<double, 0, false>(a, odd, block, s);
     if (noise) return launch_cs_t<double, 1, true>(a, odd, block, s);
     return launch_cs_t<double, 1, false>(a, odd, block, s);
+}
+
+cudaError_t launch_collide_stream_oop(const FluidArgs &a, bool fp32, int collision, bool odd, dim3 block,
+                                      cudaStream_t s) {
+    if (fp32) {
+        if (collision == 0) return launch_cs_t<float, 0, false, true>(a, odd, block, s);
+        return launch_cs_t<float, 1, false, true>(a, odd, block, s);
+    }
+    if (collision == 0) return launch_cs_t<double, 0, false, true>(a, odd, block, s);
+    return launch_cs_t<double, 1, false, true>(a, odd, block, s);
 }
 
 bool make_wall_beads(const Geom &g, double pore_R, double spacing, double r_pore_bead, double r_bead, double eps,

@@ -43,6 +43,8 @@ struct FluidArgs {
     void *plane[19];             // base of each population plane (f + i N), uniform per launch
     const uint32_t *masks;       // pore: per position across the axis, bit 31 wall node, bit i the
                                  // upstream node of link i is a wall (launch_build_masks)
+    void *out[19];               // out-of-place step (launch_collide_stream_oop): where each plane's
+                                 // populations are stored; the loads read f / plane
 };
 
 // Rigid bodies (FP64, array of structs; few bodies, one thread each).
@@ -122,6 +124,11 @@ struct CoupleArgs {
 cudaError_t launch_init(void *f, bool fp32, long long N, double rho0, cudaStream_t s);
 cudaError_t launch_collide_stream(const FluidArgs &a, bool fp32, int collision, bool noise, bool odd,
                                   dim3 block, cudaStream_t s);
+// the same step out of place (deterministic fluid): loads from f / plane,
+// stores into out, in the AA layout of the next step; every slot of a fluid
+// node is written, the slots of wall nodes are not
+cudaError_t launch_collide_stream_oop(const FluidArgs &a, bool fp32, int collision, bool odd, dim3 block,
+                                      cudaStream_t s);
 // TMA-staged variant (FP32 storage, periodic, nx % 4 == 0); cudaErrorNotSupported otherwise
 bool tma_collide_supported(const Geom &g, bool fp32);
 // positions across the pore axis: nx*ny (axis z), nx*nz (axis y), ny*nz (axis x)
