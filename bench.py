@@ -267,7 +267,7 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the C ABI with host buffers: per step the host sets
     # the external forces of every body (H2D) and reads every body's force
-    # and torque back (D2H)
+    # and torque back (D2H), in one library call (lb_step_io)
     L, w = main["L"], main["w"]
     nb = len(w.bodies)
     # page-locked host buffers (torch pins them; numpy views share the memory)
@@ -277,9 +277,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        L.lb_set_external_forces(Fext, Text)
-        L.lb_step(1)
-        L.lb_forces_all(Fout, Tout)
+        L.lb_step_io(Fext, Text, Fout, Tout)
     t1 = time.perf_counter()
     e2e_ms = barrier_max((t1 - t0) * 1e3 / max(e2e_steps, 1))
     e2e_value = N * ws / (e2e_ms * 1e-3) / 1e6 if e2e_steps else None

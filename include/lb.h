@@ -178,6 +178,16 @@ lb_status lb_forces(lb_handle h, int body_id, double F[3], double T[3], double *
  * Synchronises; returns LB_ERR_TIMEOUT / LB_ERR_STATE as lb_forces. */
 lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T);
 
+/* One round of a host control loop in one call: lb_set_external_forces(h,
+ * nbodies, F_ext, T_ext) (skipped when F_ext is NULL), lb_step(h, nsteps),
+ * then lb_forces_all(h, nbodies, F, T) (skipped when F and T are both NULL),
+ * with the same arguments, layouts ([3 nbodies] each, lab frame) and errors
+ * as those three calls; the first failing part's status is returned and the
+ * later parts are not run. Host arrays are the caller's and are used only
+ * during the call. Synchronises when F or T is given. */
+lb_status lb_step_io(lb_handle h, int nsteps, int nbodies, const double *F_ext, const double *T_ext, double *F,
+                     double *T);
+
 /* Body state X[3], V[3], q[4], body-frame w[3] (any may be NULL). */
 lb_status lb_get_body(lb_handle h, int body_id, double X[3], double V[3], double q[4], double w[3]);
 

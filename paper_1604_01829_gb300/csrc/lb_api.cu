@@ -915,6 +915,16 @@ lb_status lb_forces(lb_handle h, int id, double F[3], double T[3], double *per_b
     return check_device_error(h);
 }
 
+lb_status lb_step_io(lb_handle h, int nsteps, int nbodies, const double *F_ext, const double *T_ext, double *F,
+                     double *T) {
+    if (check_handle(h) != LB_OK) return LB_ERR_ARG;
+    lb_status s = LB_OK;
+    if (F_ext) s = lb_set_external_forces(h, nbodies, F_ext, T_ext);
+    if (s == LB_OK) s = lb_step(h, nsteps);
+    if (s == LB_OK && (F || T)) s = lb_forces_all(h, nbodies, F, T);
+    return s;
+}
+
 lb_status lb_forces_all(lb_handle h, int nbodies, double *F, double *T) {
     if (check_handle(h) != LB_OK) return LB_ERR_ARG;
     if (nbodies < 0 || nbodies > (int)h->hb.size()) return fail(h, LB_ERR_ARG, "bad body count");

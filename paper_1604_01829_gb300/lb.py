@@ -74,6 +74,8 @@ _SIGS = {
     "lb_step": [C.c_void_p, C.c_int],
     "lb_forces": [C.c_void_p, C.c_int, _dp, _dp, _dp],
     "lb_forces_all": [C.c_void_p, C.c_int, _dp, _dp],
+    # raw addresses (ints): the per-step call of a host control loop
+    "lb_step_io": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lb_get_body": [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp],
     "lb_get_populations": [C.c_void_p, _dp, C.c_size_t],
     "lb_set_populations": [C.c_void_p, _dp, C.c_size_t],
@@ -362,6 +364,24 @@ class LB:
         pb = np.zeros(3 * self.bead_counts[body]) if per_bead else None
         _check(self.h, load().lb_forces(self.h, int(body), _d(F), _d(T), _d(pb)))
         return (F, T, pb.reshape(-1, 3)) if per_bead else (F, T)
+
+    def lb_step_io(self, F_ext, T_ext, F_out, T_out, n=1):
+        """Sets the external forces and torques, takes n steps and reads every
+        body's force and torque back into F_out / T_out, in one library call.
+        Every array is float64, C-contiguous, 3 * nbodies long (F_ext None:
+        keep the forces; F_out and T_out None: no read-back)."""
+        nb = len(self.bead_counts)
+
+        def addr(a, out):
+            if a is None:
+                return None
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                    and a.size == 3 * nb and (not out or a.flags.writeable)):
+                raise ValueError("lb_step_io: float64 C-contiguous arrays of 3 * nbodies values")
+            return a.ctypes.data
+
+        _check(self.h, load().lb_step_io(self.h, int(n), nb, addr(F_ext, False), addr(T_ext, False),
+                                         addr(F_out, True), addr(T_out, True)))
 
     def lb_forces_all(self, F=None, T=None):
         n = len(self.bead_counts)

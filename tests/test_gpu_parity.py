@@ -18,7 +18,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import Pair, W19, perturbed_populations
+from helpers import Pair, W19, observe, perturbed_populations
 from paper_1604_01829_gb300 import workloads as Wl
 
 pytestmark = pytest.mark.gpu
@@ -123,6 +123,59 @@ def test_external_forces_set_between_steps_and_read_back_together(precision):
             assert np.array_equal(Fa[3 * b:3 * b + 3], Fb) and np.array_equal(Ta[3 * b:3 * b + 3], Tb)
             e = P.body_errors(b)
             assert e["bead"] <= tb and e["F"] <= tb and e["T"] <= tb and e["X"] <= tb, (n, b, e)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_step_io_equals_the_three_calls(precision):
+    """lb_step_io (external forces in, steps, every body's totals out, one
+    library call) leaves the same state and returns the same totals as
+    lb_set_external_forces + lb_step + lb_forces_all on a twin handle, to the
+    rounding of the atomics that sum bead forces in an unspecified order
+    (FP64 1e-11, FP32 1e-5 of the largest value); F_ext None keeps the
+    forces, no output arrays skips the read-back; wrong arrays are refused
+    before the call."""
+    from paper_1604_01829_gb300 import lb
+    params = dict(MRT, kT=1e-4, seed=21, gamma_bead=Wl.paper_gamma_to_lattice(50.0), compensate_force=1)
+    sph = Wl.sphere_raspberry(2.0)
+    ell = Wl.ellipsoid_raspberry(3.0, 1.5, 1.5, seed=3)
+    hs = []
+    for _ in range(2):
+        h = lb.LB(20, 18, 16, precision=precision, **params)
+        h.lb_add_raspberry(sph, [6.2, 5.1, 4.3], mass=34.0, inertia=(50, 50, 50), F_ext=(1e-3, 0, 0))
+        h.lb_add_raspberry(ell, [13.7, 11.2, 9.1], [0.9, 0.1, -0.2, 0.3], 30.0, (10, 40, 40))
+        hs.append(h)
+    A, B = hs
+    rng = np.random.default_rng(5)
+    Fa, Ta, Fb, Tb = (np.zeros(6) for _ in range(4))
+    tol = 1e-11 if precision == 64 else 1e-5
+
+    def close(a, b):
+        d = float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-30))
+        observe("step_io", d)
+        return d <= tol
+
+    for n, set_forces in ((1, True), (3, False), (2, True), (1, True)):
+        F = rng.normal(scale=1e-3, size=6)
+        T = rng.normal(scale=1e-3, size=6)
+        if set_forces:
+            A.lb_set_external_forces(F, T)
+        A.lb_step(n)
+        A.lb_forces_all(Fa, Ta)
+        B.lb_step_io(F if set_forces else None, T if set_forces else None, Fb, Tb, n)
+        assert close(Fa, Fb) and close(Ta, Tb), n
+    B.lb_step_io(None, None, None, None, 2)
+    A.lb_step(2)
+    fa, fb = A.lb_get_populations(), B.lb_get_populations()
+    assert float((np.abs(fa - fb).max(axis=1) / W19).max()) <= tol
+    for b in range(2):
+        sa, sb = A.lb_get_body(b), B.lb_get_body(b)
+        assert all(close(sa[k], sb[k]) for k in ("X", "q")), b
+    with pytest.raises(ValueError):
+        B.lb_step_io(np.zeros(5), None, Fb, Tb)
+    with pytest.raises(ValueError):
+        B.lb_step_io(None, None, np.zeros(6, dtype=np.float32), Tb)
+    A.close()
+    B.close()
 
 
 @pytest.mark.parametrize("precision", [64, 32])
