@@ -72,7 +72,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: b
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    # --no-undefined: a declaration without a matching definition fails here
+    # rather than when the library is loaded
+    cmd = [nv, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -648,7 +648,9 @@ namespace {
 // The body prologue of step h->step + k (k-th of a group; the device step
 // counter is advanced once per group, so kernels read *step_dev + k): the
 // previous step's second half kick if finish_prev, this step's kick and
-// drift, the clearing of its spread-force tiles. On stream `st`.
+// drift, the clearing of its spread-force tiles. On stream `st`. The first
+// step of a group (k = 0) has no fluid kernel of this group beside it, so its
+// clearing takes a full-GPU grid.
 lb_status launch_step_prologue(lb_ctx *h, int k, bool finish_prev, cudaStream_t st) {
     const int nb = (int)h->hb.size();
     const bool coupled = nb > 0 && !h->hbody_of.empty();
@@ -658,7 +660,8 @@ lb_status launch_step_prologue(lb_ctx *h, int k, bool finish_prev, cudaStream_t 
     const lbk::Recorder rec{nsub == 1 ? h->rec : nullptr, h->rec_every, h->rec_cap, h->step_dev, (uint32_t)k};
     cudaError_t e = lbk::launch_step_pre(h->db, nb, finish_prev, coupled ? h->Fbuf[cur] : nullptr, h->fp32,
                                          coupled ? h->tiles[cur] : nullptr, h->tlist[cur], h->tcount[cur],
-                                         h->list_cap, h->g, h->ntx, h->nty, rec, st, 1.0 / nsub, h->io_dmap);
+                                         h->list_cap, h->g, h->ntx, h->nty, rec, st, 1.0 / nsub, h->io_dmap,
+                                         k == 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "step_pre launch");
     // the list of this buffer restarts empty for this step's coupling
     if (coupled) LB_CUDA(h, cudaMemsetAsync(h->tcount[cur], 0, sizeof(int), st));

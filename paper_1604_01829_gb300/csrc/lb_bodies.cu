@@ -114,14 +114,24 @@ __global__ void __launch_bounds__(128) __maxnreg__(sizeof(T) == 4 ? LB_COUPLE_RE
 
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
                             const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
-                            cudaStream_t s, double dt, const double *ext) {
+                            cudaStream_t s, double dt, const double *ext, bool alone) {
     // one block per body, and for the tile clearing (grid-stride) at most a
-    // quarter of the SMs' worth of blocks: the kernel runs beside the fluid
-    // kernel of the previous step, whose blocks it would otherwise displace
-    // (measured on GB300 at 256^3 with 64 bodies: fluid kernel 0.4372 ms
-    // against 0.4392 with a full-GPU grid, the step 0.4620 against 0.4641)
+    // quarter of the SMs' worth of blocks when the kernel runs beside the
+    // fluid kernel of the previous step, whose blocks it would otherwise
+    // displace (measured on GB300 at 256^3 with 64 bodies: fluid kernel
+    // 0.4372 ms against 0.4392 with a full-GPU grid, the step 0.4620 against
+    // 0.4641); 8 blocks per SM when nothing runs beside it (the first step of
+    // a group, e.g. every step of a one-step-per-call control loop)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms <= 0)
+            sms = 152;
+    }
     long long n = 64LL * list_cap;
-    if (n > 38LL * 256) n = 38LL * 256;
+    const long long cap = (alone ? 8LL * sms : (long long)(sms + 3) / 4) * 256;
+    if (n > cap) n = cap;
     unsigned grid = (unsigned)((n + 255) / 256);
     if (grid < (unsigned)nbodies) grid = (unsigned)nbodies;
     if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);

@@ -162,7 +162,7 @@ struct Recorder {
 // dt: the MD (sub)step, 1 without substeps
 cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, bool fp32, int *tiles, const int *tlist,
                             const int *tcount, int list_cap, const Geom &g, int ntx, int nty, const Recorder &rec,
-                            cudaStream_t s, double dt = 1.0, const double *ext = nullptr);
+                            cudaStream_t s, double dt = 1.0, const double *ext = nullptr, bool alone = false);
 
 // The valid records of body `id` in a recorder ring, oldest first (host
 // arrays; lb_traj.cu).
