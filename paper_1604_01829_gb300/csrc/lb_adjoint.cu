@@ -557,11 +557,12 @@ struct Snapshot {
 };
 
 // What the reverse pass of one step reads, taped by the two-level schedule.
-// The first step of a segment reads its populations and previous spread
-// force from the segment's snapshot, every later one from the entry before
-// it (its Fnew), so entry 0 holds no populations.
+// Entry 0 receives the segment's snapshot populations; every step reads its
+// entry and writes the next one's populations itself. The first step's
+// previous spread force is the snapshot's, every later one's the Fnew of the
+// entry before.
 struct Tape {
-    void *f = nullptr;        // populations before the step (entries >= 1)
+    void *f = nullptr;        // populations before the step
     void *Fnew = nullptr;     // spread force the step writes
     Body *bodies = nullptr;   // bodies before the step
 };
@@ -668,7 +669,7 @@ lb_status ensure_work(lb_ctx *h, int nsnap, int ntape, int nsteps, double *alloc
     }
     for (size_t k = 0; k < w->tape.size(); ++k) {
         Tape &T = w->tape[k];
-        if (k > 0 && e == cudaSuccess) {
+        if (e == cudaSuccess) {
             // out-of-place steps write the slots of fluid nodes only: the
             // wall-node slots (never read) start as zeros, not garbage
             e = walloc(*w, &T.f, z.fbytes);
@@ -907,35 +908,81 @@ lb_status run_two_level(Run &R, int c) {
     cudaError_t e = R.save(w->snaps[nseg]);
     if (e != cudaSuccess) return R.fail_cuda(e, "snapshot");
     R.mark_first();
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-        const Snapshot &Sg = w->snaps[sg];
-        if ((e = R.restore(Sg)) != cudaSuccess) return R.fail_cuda(e, "restore");
-        const int a0 = sg * K, a1 = std::min(T, a0 + K);
-        R.recompute_steps += a1 - a0;
-        // each step reads the populations where the one before left them (the
-        // snapshot, then tape entries) and leaves its own in the next entry:
-        // the tape is written by the steps themselves, not copied
+    // The re-run of steps [a0, a1) from the state in tape entry 0: each step
+    // reads the populations where the one before left them and stores its own
+    // into the next entry (the last into the handle's array), so the tape is
+    // written by the steps themselves.
+    auto rerun = [&](int a0, int a1) -> lb_status {
         for (int n = a0; n < a1; ++n) {
             Tape &Tp = w->tape[n - a0];
             const int curb = (int)((R.n0 + n) & 1);
-            e = cudaMemcpyAsync(Tp.bodies, h->db, R.z.bbytes, cudaMemcpyDeviceToDevice, R.s);
-            if (e != cudaSuccess) return R.fail_cuda(e, "tape");
+            cudaError_t ce = cudaMemcpyAsync(Tp.bodies, h->db, R.z.bbytes, cudaMemcpyDeviceToDevice, R.s);
+            if (ce != cudaSuccess) return R.fail_cuda(ce, "tape");
             void *dst = n + 1 < a1 ? w->tape[n + 1 - a0].f : h->f;
-            lb_status st = lbk::ctx_step_oop(h, R.pops(), dst);
+            lb_status st = lbk::ctx_step_oop(h, Tp.f, dst);
             if (st != LB_OK) return st;
-            R.cf = dst != h->f ? dst : nullptr;
-            e = cudaMemcpyAsync(Tp.Fnew, h->Fbuf[curb], R.z.Fbytes, cudaMemcpyDeviceToDevice, R.s);
-            if (e != cudaSuccess) return R.fail_cuda(e, "tape");
+            ce = cudaMemcpyAsync(Tp.Fnew, h->Fbuf[curb], R.z.Fbytes, cudaMemcpyDeviceToDevice, R.s);
+            if (ce != cudaSuccess) return R.fail_cuda(ce, "tape");
         }
-        const int prev0 = (int)((R.n0 + a0) & 1) ^ 1;
+        return LB_OK;
+    };
+    // A full segment re-runs the same steps on the same buffers whatever its
+    // snapshot (entry 0 receives the snapshot's populations), so its launches
+    // are captured once per starting parity as a CUDA graph and replayed:
+    // host launch cost would otherwise exceed the segment's device time.
+    cudaGraphExec_t gx[2] = {nullptr, nullptr};
+    bool graphs = K > 1 && !h->timing;      // per-kernel timing events stay eager
+    auto drop = [&]() {
+        for (auto &g : gx)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    };
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const Snapshot &Sg = w->snaps[sg];
+        if ((e = R.restore(Sg)) != cudaSuccess) return drop(), R.fail_cuda(e, "restore");
+        if ((e = cudaMemcpyAsync(w->tape[0].f, Sg.f, R.z.fbytes, cudaMemcpyDeviceToDevice, R.s)) != cudaSuccess)
+            return drop(), R.fail_cuda(e, "tape");
+        const int a0 = sg * K, a1 = std::min(T, a0 + K);
+        R.recompute_steps += a1 - a0;
+        lb_status st = LB_OK;
+        const int p = (int)((R.n0 + a0) & 1);
+        if (graphs && a1 - a0 == K && !gx[p]) {
+            // capture (nothing runs; the host step mirror is put back after)
+            const long long step0 = h->step;
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamBeginCapture(R.s, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                st = rerun(a0, a1);
+                e = cudaStreamEndCapture(R.s, &gr);
+                if (st == LB_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gx[p], gr, 0);
+                if (gr) cudaGraphDestroy(gr);
+            }
+            h->step = step0;
+            if (st != LB_OK) return drop(), st;
+            if (e != cudaSuccess) {           // not capturable here: step eagerly from now on
+                cudaGetLastError();
+                gx[p] = nullptr;
+                graphs = false;
+            }
+        }
+        if (graphs && a1 - a0 == K && gx[p]) {
+            if ((e = cudaGraphLaunch(gx[p], R.s)) != cudaSuccess) return drop(), R.fail_cuda(e, "re-run graph");
+            h->step += K;
+        } else if ((st = rerun(a0, a1)) != LB_OK) {
+            return drop(), st;
+        }
+        R.cf = nullptr;
+        const int prev0 = p ^ 1;
         for (int n = a1 - 1; n >= a0; --n) {
             const Tape &Tp = w->tape[n - a0];
-            const void *fn = n == a0 ? Sg.f : Tp.f;
             const void *Fprev = n == a0 ? Sg.F[prev0] : w->tape[n - 1 - a0].Fnew;
-            lb_status st = R.reverse_step(n, fn, Fprev, Tp.Fnew, Tp.bodies);
-            if (st != LB_OK) return st;
+            st = R.reverse_step(n, Tp.f, Fprev, Tp.Fnew, Tp.bodies);
+            if (st != LB_OK) return drop(), st;
         }
     }
+    drop();
     // leave the handle where the forward sweep ended
     if ((e = R.restore(w->snaps[nseg], true)) != cudaSuccess) return R.fail_cuda(e, "restore");
     return LB_OK;
