@@ -536,6 +536,38 @@ __global__ void k_record_v(const Body *bodies, int jb, int axis, double *out, in
     out[idx] = bodies[jb].V[axis];
 }
 
+// Several device-to-device copies in one launch (a state save or restore):
+// segment k copies bytes (a multiple of 4) from src to dst, in 16-byte words
+// when both addresses allow it, else in 4-byte words.
+struct CopySeg {
+    const void *src;
+    void *dst;
+    unsigned long long bytes;
+};
+struct CopyList {
+    CopySeg seg[12];
+    int n;
+};
+
+__global__ void k_copy_segments(const CopyList L) {
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nt = (unsigned long long)gridDim.x * blockDim.x;
+    for (int k = 0; k < L.n; ++k) {
+        const CopySeg c = L.seg[k];
+        unsigned long long n16 = 0;
+        if ((((uintptr_t)c.src | (uintptr_t)c.dst) & 15u) == 0) {
+            n16 = c.bytes / 16;
+            const uint4 *s4 = static_cast<const uint4 *>(c.src);
+            uint4 *d4 = static_cast<uint4 *>(c.dst);
+            for (unsigned long long i = tid; i < n16; i += nt) d4[i] = s4[i];
+        }
+        const unsigned long long w0 = 4 * n16, nw = c.bytes / 4;   // 4-byte words left: [w0, nw)
+        const uint32_t *s1 = static_cast<const uint32_t *>(c.src);
+        uint32_t *d1 = static_cast<uint32_t *>(c.dst);
+        for (unsigned long long i = w0 + tid; i < nw; i += nt) d1[i] = s1[i];
+    }
+}
+
 }  // namespace
 }  // namespace lbk
 
@@ -736,43 +768,52 @@ struct Run {
     const void *cf = nullptr;
     const void *pops() const { return cf ? cf : h->f; }
 
-    cudaError_t save(Snapshot &S) {
-        cudaError_t e = cudaSuccess;
-        if (pops() != S.f) e = cudaMemcpyAsync(S.f, pops(), z.fbytes, cudaMemcpyDeviceToDevice, s);
-        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-            e = cudaMemcpyAsync(S.F[k], h->Fbuf[k], z.Fbytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S.tiles[k], h->tiles[k], z.tbytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S.tlist[k], h->tlist[k], z.lbytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync((char *)S.tlist[k] + z.lbytes, h->tcount[k], sizeof(int), cudaMemcpyDeviceToDevice, s);
+    // The state's parts as copy segments between a snapshot and the handle
+    // (to_snapshot: handle -> snapshot); the populations when with_f.
+    lbk::CopyList parts(const Snapshot &S, bool to_snapshot, bool with_f, const void *f_src) {
+        lbk::CopyList L{};
+        auto add = [&](void *snap, const void *hnd, size_t bytes) {
+            lbk::CopySeg &c = L.seg[L.n++];
+            c.src = to_snapshot ? hnd : snap;
+            c.dst = to_snapshot ? snap : const_cast<void *>(hnd);
+            c.bytes = bytes;
+        };
+        if (with_f) {
+            if (to_snapshot) add(S.f, f_src, z.fbytes);
+            else add(S.f, h->f, z.fbytes);
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(S.bodies, h->db, z.bbytes, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(S.dstep, h->step_dev, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+        for (int k = 0; k < 2; ++k) {
+            add(S.F[k], h->Fbuf[k], z.Fbytes);
+            add(S.tiles[k], h->tiles[k], z.tbytes);
+            add(S.tlist[k], h->tlist[k], z.lbytes);
+            add((char *)S.tlist[k] + z.lbytes, h->tcount[k], sizeof(int));
+        }
+        add(S.bodies, h->db, z.bbytes);
+        add(S.dstep, h->step_dev, sizeof(unsigned long long));
+        return L;
+    }
+    cudaError_t copy(const lbk::CopyList &L) {
+        unsigned long long words = 0;
+        for (int k = 0; k < L.n; ++k) words += (L.seg[k].bytes + 15) / 16;
+        const unsigned long long want = (words + 255) / 256;
+        const unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>(want, 4096));
+        lbk::k_copy_segments<<<grid, 256, 0, s>>>(L);
+        return cudaGetLastError();
+    }
+
+    // One launch for the whole state (the populations only if they are not
+    // already the snapshot's).
+    cudaError_t save(Snapshot &S) {
         S.step = h->step;
-        return e;
+        return copy(parts(S, true, pops() != S.f, pops()));
     }
     // Everything but the populations, which stay in the snapshot for the next
     // step or turn to read; whole: the populations too (the handle is left
     // holding the state).
     cudaError_t restore(const Snapshot &S, bool whole = false) {
-        cudaError_t e = cudaSuccess;
-        if (whole) {
-            e = cudaMemcpyAsync(h->f, S.f, z.fbytes, cudaMemcpyDeviceToDevice, s);
-            cf = nullptr;
-        } else {
-            cf = S.f;
-        }
-        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-            e = cudaMemcpyAsync(h->Fbuf[k], S.F[k], z.Fbytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(h->tiles[k], S.tiles[k], z.tbytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(h->tlist[k], S.tlist[k], z.lbytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(h->tcount[k], (char *)S.tlist[k] + z.lbytes, sizeof(int), cudaMemcpyDeviceToDevice, s);
-        }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->db, S.bodies, z.bbytes, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->step_dev, S.dstep, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+        cf = whole ? nullptr : S.f;
         h->step = S.step;
-        return e;
+        return copy(parts(S, false, whole, nullptr));
     }
 
     // Steps the handle from relative step a to b (its state is a), recording
