@@ -122,13 +122,13 @@ cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, boo
     // 0.4372 ms against 0.4392 with a full-GPU grid, the step 0.4620 against
     // 0.4641); 8 blocks per SM when nothing runs beside it (the first step of
     // a group, e.g. every step of a one-step-per-call control loop)
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess || sms <= 0)
-            sms = 152;
-    }
+    static const int sms = [] {     // initialised once, thread-safe
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || n <= 0)
+            n = 152;
+        return n;
+    }();
     long long n = 64LL * list_cap;
     const long long cap = (alone ? 8LL * sms : (long long)(sms + 3) / 4) * 256;
     if (n > cap) n = cap;
