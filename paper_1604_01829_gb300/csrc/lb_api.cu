@@ -680,6 +680,7 @@ lb_status launch_step_coupling(lb_ctx *h, int k, int sub) {
     c.fp32 = h->fp32;
     c.odd = odd;
     c.rho0 = h->p.rho0;
+    c.rho0_f = (float)h->p.rho0;
     c.gamma = h->p.gamma_bead;
     const double dt = 1.0 / h->p.md_substeps;
     // bead noise of variance 2 kT gamma / dt per substep (Philox call 4 + sub)

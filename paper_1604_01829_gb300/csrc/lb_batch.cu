@@ -59,6 +59,7 @@ struct BInst {
     uint32_t key0, key1, instance;
     double rho0, gamma, noise_amp;
     float gamma_f, noise_amp_f;
+    float noise_amp_sub_f;       // noise_amp x sqrt(MD substeps), rounded to FP32 (FP32 coupling)
     double pore_R;
     WallBeads wall;              // pore-wall beads
     double gd[3];                // uniform force density
@@ -268,6 +269,8 @@ struct BatchCouple {
     const float *sf;
     const int *bead_body;
     const int *bead_rng;          // bead index within its own lattice
+    const int *bead_inst;         // instance of each bead
+    int ninst;
     Body *bodies;
     double *F_bead;
     int nbeads;
@@ -276,6 +279,7 @@ struct BatchCouple {
     int *err;                     // index checks of checked builds, as BatchArgs
     int list_cap, nbodies;
     double dt, noise_scale;       // MD substep length 1/n; bead noise amplitude factor sqrt(n)
+    float dt_f;                  // dt rounded to FP32
     uint32_t call;                // Philox call word of the bead noise: 4 + substep
 };
 
@@ -289,16 +293,21 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? LB_BATCH_COUPLE_REGS : 255) k_batch
     const bool active = k < b.nbeads;
     // lanes of inactive groups borrow bead 0's instance (they do no work)
     const int kk = active ? k : 0;
-    const BInst &I = b.inst[b.bodies[chk(b.bead_body[kk], b.nbodies, b.err)].inst];
+    const BInst &I = b.inst[chk(b.bead_inst[kk], b.ninst, b.err)];
     CoupleArgs a{};
     a.g = I.g;
     a.g.N = I.fs;                 // force planes (and dense population planes): the padded node count
     a.f = static_cast<const T *>(b.pool) + I.off;
     a.fp32 = b.fp32;
     a.odd = b.odd;
-    a.rho0 = I.rho0;
-    a.gamma = I.gamma;
-    a.noise_amp = I.noise_amp * b.noise_scale;
+    // the FP32 coupling reads the FP32 copies only (no FP64 work per thread)
+    if constexpr (sizeof(T) == 8) {
+        a.rho0 = I.rho0;
+        a.gamma = I.gamma;
+        a.noise_amp = I.noise_amp * b.noise_scale;
+        a.dt = b.dt;
+    }
+    a.rho0_f = I.pf.rho0;
     a.gforce = I.gd;
     a.gforce_f = I.gf;
     a.Fprev = static_cast<const T *>(b.Fprev) + I.foff;
@@ -312,7 +321,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? LB_BATCH_COUPLE_REGS : 255) k_batch
     a.s = b.s;
     a.sf = b.sf;
     a.gamma_f = I.gamma_f;
-    a.noise_amp_f = (float)(I.noise_amp * b.noise_scale);
+    a.noise_amp_f = I.noise_amp_sub_f;
     a.bead_body = b.bead_body;
     a.bodies = b.bodies;
     a.F_bead = b.F_bead;
@@ -321,8 +330,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? LB_BATCH_COUPLE_REGS : 255) k_batch
     a.ntiles = (long long)I.ntx * I.nty * I.ntz;
     a.list_cap = b.list_cap;
     a.nbodies = b.nbodies;
-    a.dt = b.dt;
-    a.dt_f = (float)b.dt;
+    a.dt_f = b.dt_f;
     a.call = b.call;
     a.key0 = I.key0;
     a.key1 = I.key1;
@@ -467,7 +475,7 @@ struct lb_batch_ctx {
     // bodies
     std::vector<Body> hb;
     std::vector<double> hs;
-    std::vector<int> hbody_of, hbead_rng;
+    std::vector<int> hbody_of, hbead_rng, hbead_inst;
     std::vector<std::vector<int>> inst_bodies;     // body ids per instance
     std::vector<int> inst_beads;                   // beads per instance so far
     Body *db = nullptr;
@@ -475,6 +483,7 @@ struct lb_batch_ctx {
     float *dsf = nullptr;
     std::vector<float> hsf;
     int *dbody_of = nullptr, *dbead_rng = nullptr;
+    int *dbead_inst = nullptr;              // instance of each bead (the coupling's first lookup)
     double *dFbead = nullptr;
     bool uploaded = false;
     // schedule
@@ -789,6 +798,7 @@ lb_status upload(lb_batch_ctx *h) {
         if ((s = balloc(h, &h->dsf, sizeof(float) * 3 * (size_t)nbeads)) != LB_OK) return s;
         if ((s = balloc(h, &h->dbody_of, sizeof(int) * (size_t)nbeads)) != LB_OK) return s;
         if ((s = balloc(h, &h->dbead_rng, sizeof(int) * (size_t)nbeads)) != LB_OK) return s;
+        if ((s = balloc(h, &h->dbead_inst, sizeof(int) * (size_t)std::max(nbeads, 1))) != LB_OK) return s;
         if ((s = balloc(h, &h->dFbead, sizeof(double) * 3 * (size_t)nbeads)) != LB_OK) return s;
         BCUDA(h, cudaMemcpyAsync(h->db, h->hb.data(), sizeof(Body) * nb, cudaMemcpyHostToDevice, h->stream));
         if (nbeads > 0) {
@@ -797,6 +807,9 @@ lb_status upload(lb_batch_ctx *h) {
             BCUDA(h, cudaMemcpyAsync(h->dsf, h->hsf.data(), sizeof(float) * 3 * nbeads, cudaMemcpyHostToDevice, h->stream));
             BCUDA(h, cudaMemcpyAsync(h->dbody_of, h->hbody_of.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
             BCUDA(h, cudaMemcpyAsync(h->dbead_rng, h->hbead_rng.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
+            h->hbead_inst.resize(nbeads);
+            for (int j = 0; j < nbeads; ++j) h->hbead_inst[j] = h->hb[h->hbody_of[j]].inst;
+            BCUDA(h, cudaMemcpyAsync(h->dbead_inst, h->hbead_inst.data(), sizeof(int) * nbeads, cudaMemcpyHostToDevice, h->stream));
         }
         const size_t fb = (h->fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)h->Ftot;
         h->list_cap = (int)std::min<long long>(h->Ttot, 8LL * std::max(nbeads, 1));
@@ -873,6 +886,8 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record, boo
         c.sf = h->dsf;
         c.bead_body = h->dbody_of;
         c.bead_rng = h->dbead_rng;
+        c.bead_inst = h->dbead_inst;
+        c.ninst = h->n;
         c.bodies = h->db;
         c.F_bead = h->dFbead;
         c.nbeads = nbeads;
@@ -884,6 +899,7 @@ lb_status launch_step(lb_batch_ctx *h, int k, bool finish_prev, bool record, boo
         // bead noise of variance 2 kT gamma / dt per substep (Philox call 4 + substep)
         c.dt = dt;
         c.noise_scale = std::sqrt((double)nsub);
+        c.dt_f = (float)dt;
         const unsigned grid = (unsigned)((8LL * nbeads + 127) / 128);
         for (int sub = 0; sub < nsub; ++sub) {
             if (sub > 0) {   // bodies move by dt between the couplings of one LB step
@@ -1069,6 +1085,7 @@ lb_status lb_batch_create(const lb_params *params, int n, void *cuda_stream, lb_
         I.noise_amp = p.kT > 0.0 ? std::sqrt(2.0 * p.kT * p.gamma_bead) : 0.0;
         I.gamma_f = (float)I.gamma;
         I.noise_amp_f = (float)I.noise_amp;
+        I.noise_amp_sub_f = (float)(I.noise_amp * std::sqrt((double)h->nsub));
         fill_coll(p, I);
         I.mx = (uint32_t)((0x100000000ULL + p.nx - 1) / p.nx);
         I.my = (uint32_t)((0x100000000ULL + p.ny - 1) / p.ny);
@@ -1163,7 +1180,7 @@ lb_status lb_batch_destroy(lb_batch_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void *bufs[] = {h->pool, h->Fbuf[0], h->Fbuf[1], h->tiles[0], h->tiles[1], h->tlist[0], h->tlist[1], h->tcount[0],
                     h->tcount[1], h->dinst, h->dtile_start, h->dtile_inst,
-                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dFbead, h->rec, h->dcmap, h->dcnbr, h->dfluid,
+                    h->dflag_start, h->step_dev, h->db, h->ds, h->dsf, h->dbody_of, h->dbead_rng, h->dbead_inst, h->dFbead, h->rec, h->dcmap, h->dcnbr, h->dfluid,
                     h->derr};
     for (void *b : bufs)
         if (b) cudaFree(b);

@@ -162,7 +162,7 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
         for (int q = 0; q < 3; ++q) ub[q] = wt * (float)g.wchan[38 + 3 * ywall + q];
     if (fluid) {                         // wall nodes carry u = 0
         float rho, j[3];
-        node_rho_j<float>(A, g, xyz[0], xyz[1], xyz[2], chk(n, g.N, a.err), a.odd, (float)a.rho0, rho, j, a.err);
+        node_rho_j<float>(A, g, xyz[0], xyz[1], xyz[2], chk(n, g.N, a.err), a.odd, a.rho0_f, rho, j, a.err);
         const float ir = 1.f / rho;
         const float *Fp = static_cast<const float *>(a.Fprev);
         ub[0] = wt * ((j[0] + 0.5f * (a.gforce_f[0] + Fp[n])) * ir);

@@ -102,6 +102,7 @@ struct CoupleArgs {
     const double *s;             // body-frame bead offsets [3*nbeads]
     const float *sf;             // the same in FP32 (FP32 coupling)
     float gamma_f, noise_amp_f;  // gamma and noise_amp in FP32
+    float rho0_f;                // rho0 in FP32
     const int *bead_body;        // body index of each bead
     Body *bodies;
     double *F_bead;              // out: bead forces [3*nbeads]
