@@ -98,6 +98,11 @@ __global__ void k_wall_beads(const WallBeads w, Body *bodies, const double *s, c
     if (k < nbeads) wall_bead_body(w, bodies, s, bead_body, k);
 }
 
+// threads per block of the body prologue when it runs beside a fluid kernel
+#ifndef LB_PRE_BLOCK
+#define LB_PRE_BLOCK 256
+#endif
+
 // register cap of the FP32 coupling kernel (resident CTAs of 128 per SM:
 // 65536 / (128 x cap))
 #ifndef LB_COUPLE_REGS
@@ -130,12 +135,13 @@ cudaError_t launch_step_pre(Body *b, int nbodies, bool finish_prev, void *F, boo
         return n;
     }();
     long long n = 64LL * list_cap;
-    const long long cap = (alone ? 8LL * sms : (long long)(sms + 3) / 4) * 256;
+    const int bs = alone ? 256 : LB_PRE_BLOCK;
+    const long long cap = (alone ? 8LL * sms : (long long)(sms + 3) / 4) * bs;
     if (n > cap) n = cap;
-    unsigned grid = (unsigned)((n + 255) / 256);
+    unsigned grid = (unsigned)((n + bs - 1) / bs);
     if (grid < (unsigned)nbodies) grid = (unsigned)nbodies;
-    if (fp32) k_step_pre<float><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);
-    else k_step_pre<double><<<grid, 256, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);
+    if (fp32) k_step_pre<float><<<grid, bs, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (float *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);
+    else k_step_pre<double><<<grid, bs, 0, s>>>(b, nbodies, finish_prev ? 1 : 0, (double *)F, tiles, tlist, tcount, g, ntx, nty, rec, dt, ext);
     return cudaGetLastError();
 }
 
