@@ -4,7 +4,9 @@ ABI against closed forms of Stokes flow:
 * the Hasimoto finite-size law for the drag of a raspberry in a periodic box
   (Sec. 2.4, Eq. (hasimoto)), with the protocol of the oracle pin;
 * the drag anisotropy of a prolate raspberry, xi_perp / xi_par = F / E of
-  the Happel-Brenner factors (SI, Eqs. (happelbrenner_e), (happelbrenner_f));
+  the Happel-Brenner factors (SI, Eqs. (happelbrenner_e), (happelbrenner_f)),
+  and its rotational drag anisotropy against Perrin's spheroid factors
+  (SI, Eqs. (dr_bf_i), (dr_bf_j));
 * the drag of a sphere on the axis of a cylindrical pore (Sec. 2.8, the
   confinement geometry) against the centreline wall-correction series of
   Bohlin (1960) / Haberman & Sayre (1958), K(lambda) = 1 / (1 - 2.10444
@@ -105,6 +107,24 @@ def test_prolate_drag_anisotropy_matches_happel_brenner():
     expect = Fc.happel_brenner_F(3.0) / Fc.happel_brenner_E(3.0)
     assert perp > par
     assert abs(perp / par / expect - 1) < 0.04, (par, perp, perp / par, expect)
+
+
+def test_prolate_rotational_drag_anisotropy_matches_perrin():
+    """The same 3:1 prolate raspberry held in place and spinning about its
+    long axis and about a short one (L = 64; the rotational drag changes by
+    < 0.3 % from L = 48 to 80): xi_r,perp / xi_r,par within 4 % of Perrin's
+    spheroid value J / I = 3.129 (SI, Eqs. (dr_bf_i), (dr_bf_j); measured
+    3.169), and the two short axes agree (rotational symmetry of the bead
+    shell about the long axis)."""
+    from paper_1604_01829_gb300 import drag as D
+    beads = Wl.ellipsoid_raspberry(9.0, 3.0, 3.0)
+    par = D.spin_drag(64, beads, axis=0)
+    perp_y = D.spin_drag(64, beads, axis=1)
+    perp_z = D.spin_drag(64, beads, axis=2)
+    I, J = Fc.perrin_rotation(3.0)
+    observe("rot_anisotropy_vs_perrin", abs(perp_y / par / (J / I) - 1))
+    assert abs(perp_y / perp_z - 1) < 1e-3, (perp_y, perp_z)
+    assert abs(perp_y / par / (J / I) - 1) < 0.04, (par, perp_y, perp_y / par, J / I)
 
 
 def test_pore_drag_enhancement_across_radial_offsets():
