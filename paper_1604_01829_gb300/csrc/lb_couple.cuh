@@ -110,6 +110,22 @@ __device__ __forceinline__ void wall_bead_body(const WallBeads &w, Body *bodies,
     }
 }
 
+// Flags `tile` in the tile flags of this step's force buffer when this lane
+// spread a force onto one of its nodes (fluid) and, the first time a tile is
+// flagged, appends it to the list of flagged tiles (cleared two steps later);
+// the appends of a warp take one atomic on the list's counter. Every lane of
+// the warp calls it (ballot).
+__device__ __forceinline__ void flag_tile(const CoupleArgs &a, bool fluid, int tile, int lane) {
+    const bool first = fluid && a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0;
+    const unsigned m = __ballot_sync(0xffffffffu, first);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(a.tcount, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (first) a.tlist[chk(base + __popc(m & ((1u << lane) - 1u)), a.list_cap, a.err)] = a.tile_base + tile;
+}
+
 // FP32 storage: the same coupling with every per-bead quantity in FP32
 // (GB300's FP64 pipe is narrow and one bead's FP64 work, done by one lane,
 // would bound the kernel). The virtual site is formed relative to the body:
@@ -188,16 +204,16 @@ __device__ __forceinline__ void couple_bead_f32(const CoupleArgs &a, int k, int 
     }
     for (int q = 0; q < 3; ++q) Fb[q] = __shfl_sync(0xffffffffu, Fb[q], 0, 8);
 
+    int tile = 0;
     if (fluid) {
         float *Fc = static_cast<float *>(a.Fcur);
         const float wdt = wt * a.dt_f;
         atomicAdd(&Fc[n], -wdt * Fb[0]);
         atomicAdd(&Fc[g.N + n], -wdt * Fb[1]);
         atomicAdd(&Fc[2 * g.N + n], -wdt * Fb[2]);
-        const int tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
-        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0)
-            a.tlist[chk(atomicAdd(a.tcount, 1), a.list_cap, a.err)] = a.tile_base + tile;
+        tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
     }
+    flag_tile(a, fluid, tile, lane);
 
     // force and torque: FP32 sums over the (up to 4) beads of the warp's first
     // body, FP64 accumulation on the body
@@ -313,16 +329,15 @@ __device__ __forceinline__ void couple_bead(const CoupleArgs &a, int k, int k_rn
     for (int q = 0; q < 3; ++q) Fb[q] = __shfl_sync(0xffffffffu, Fb[q], 0, 8);
 
     // spread -w F_b onto this lane's node; a wall node takes nothing
+    int tile = 0;
     if (fluid) {
         T *Fc = static_cast<T *>(a.Fcur);
         atomicAdd(&Fc[n], -wt * (T)(a.dt * Fb[0]));
         atomicAdd(&Fc[g.N + n], -wt * (T)(a.dt * Fb[1]));
         atomicAdd(&Fc[2 * g.N + n], -wt * (T)(a.dt * Fb[2]));
-        const int tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
-        // first flag of a tile also records it for clearing two steps later
-        if (a.tiles_cur[tile] == 0 && atomicExch(&a.tiles_cur[tile], 1) == 0)
-            a.tlist[chk(atomicAdd(a.tcount, 1), a.list_cap, a.err)] = a.tile_base + tile;
+        tile = chk((int)tile_of(xyz[0], xyz[1], xyz[2], a.ntx, a.nty), a.ntiles, a.err);
     }
+    flag_tile(a, fluid, tile, lane);
 
     // force and torque on the body: sum the (up to 4) beads of this warp
     // that belong to the warp's first body, atomics for the others
