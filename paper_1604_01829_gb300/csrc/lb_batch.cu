@@ -283,6 +283,12 @@ struct BatchCouple {
     uint32_t call;                // Philox call word of the bead noise: 4 + substep
 };
 
+// 1: lb_batch_step launches every step eagerly instead of replaying the
+// captured two-step graph
+#ifndef LB_BATCH_EAGER
+#define LB_BATCH_EAGER 0
+#endif
+
 #ifndef LB_BATCH_COUPLE_REGS
 #define LB_BATCH_COUPLE_REGS 64
 #endif
@@ -1283,7 +1289,7 @@ lb_status lb_batch_step(lb_batch_handle h, int nsteps) {
     if (nsteps == 0) return LB_OK;
     lb_status s = upload(h);
     if (s != LB_OK) return s;
-    if (h->timing) return eager_steps(h, nsteps);
+    if (h->timing || LB_BATCH_EAGER) return eager_steps(h, nsteps);
     if (h->step & 1) {
         if ((s = eager_steps(h, 1)) != LB_OK) return s;
         --nsteps;

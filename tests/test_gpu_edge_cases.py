@@ -165,6 +165,41 @@ def _upstream(nodes, dims):
     return ux + nx * (uy + ny * uz)
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_long_calls_on_large_lattices_equal_single_steps(precision):
+    """From 2^20 nodes on, lb_step calls of four or more steps launch every
+    step eagerly instead of replaying captured graphs; shorter calls replay
+    one-step graphs. A 128 x 128 x 64 lattice (2^20 nodes) with two
+    raspberries and thermal noise, stepped once by lb_step(7) and once by
+    seven lb_step(1), ends in the same state to the rounding of the atomics
+    that spread bead forces in no fixed order (FP64 1e-11, FP32 1e-5 of
+    w_i rho0; bodies to the same relative bound)."""
+    from paper_1604_01829_gb300 import lb
+    params = dict(collision=1, gamma_shear=-0.45, gamma_bulk=-0.2, gamma_odd=0.3, gamma_even=-0.1, kT=1e-4,
+                  seed=9, gamma_bead=Wl.paper_gamma_to_lattice(50.0), compensate_force=1)
+    sph = Wl.sphere_raspberry(3.0)
+    ell = Wl.ellipsoid_raspberry(6.0, 2.5, 2.5, seed=4)
+    hs = []
+    for _ in range(2):
+        h = lb.LB(128, 128, 64, precision=precision, **params)
+        h.lb_add_raspberry(sph, [30.2, 60.7, 20.1], mass=113.0, inertia=(400, 400, 400), F_ext=(1e-3, 0, 0))
+        h.lb_add_raspberry(ell, [90.6, 40.3, 44.9], [0.9, 0.1, -0.2, 0.3], 160.0, (500, 1500, 1500))
+        hs.append(h)
+    A, B = hs
+    A.lb_step(7)
+    for _ in range(7):
+        B.lb_step(1)
+    tol = 1e-11 if precision == 64 else 1e-5
+    d = float((np.abs(A.lb_get_populations() - B.lb_get_populations()).max(axis=1) / W19).max())
+    assert d <= tol, d
+    for b in range(2):
+        sa, sb = A.lb_get_body(b), B.lb_get_body(b)
+        for k in ("X", "V", "q"):
+            assert np.abs(sa[k] - sb[k]).max() <= tol * max(np.abs(sa[k]).max(), 1e-3), (b, k)
+    A.close()
+    B.close()
+
+
 def test_largest_lattice_on_sampled_nodes():
     import torch
     from paper_1604_01829_gb300 import lb
