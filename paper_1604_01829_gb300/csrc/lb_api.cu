@@ -739,16 +739,16 @@ lb_status launch_step_coupling(lb_ctx *h, int k, int sub) {
 // coupling of step k waits for it.
 lb_status launch_steps(lb_ctx *h, int n) {
     const bool bodies = !h->hb.empty();
+    lb_status s;
     if (bodies) {
         LB_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
         LB_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        if ((s = launch_step_prologue(h, 0, false, h->side)) != LB_OK) return s;
     }
     for (int k = 0; k < n; ++k) {
         const long long t = h->step + k;
         const int cur = (int)(t & 1);
-        lb_status s;
         if (bodies) {
-            if ((s = launch_step_prologue(h, k, k > 0, h->side)) != LB_OK) return s;
             LB_CUDA(h, cudaEventRecord(h->ev_join, h->side));
             LB_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
             if (!h->hbody_of.empty()) {
@@ -767,6 +767,10 @@ lb_status launch_steps(lb_ctx *h, int n) {
             if (k + 1 < n) {                  // the next prologue may start now
                 LB_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
                 LB_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                // enqueued before this step's fluid kernel (graph replay at
+                // 256^3: 0.4675 against 0.4685 ms enqueued after it; eager
+                // launches 0.4635 either way)
+                if ((s = launch_step_prologue(h, k + 1, true, h->side)) != LB_OK) return s;
             }
         }
         if ((s = timed_collide(h, fluid_args(h, cur, (uint32_t)k), (t & 1) != 0)) != LB_OK) return s;
